@@ -1,0 +1,401 @@
+/*
+ * md_oracle.c - plain, slow FP64 CPU oracle for the short-range MD hot path.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may link, load or
+ * call this file: only the test suite, the package smoke check and the
+ * benchmark's CPU-baseline leg use it.  It shares no code, header, table or
+ * constant with the CUDA library; it is compiled with -ffp-contract=off so
+ * every expression below is evaluated exactly in the order written.
+ *
+ * What it computes (Meyer 2013, arXiv:1305.4196, and textbook MD):
+ *   - the problem statement of Sec. I: N particles in a periodic box whose
+ *     interactions vanish beyond a cutoff r_cut;
+ *   - the linked-cell technique of Sec. II.A (cells at least as wide as the
+ *     search radius, a particle interacts only with particles in its own or
+ *     the 26 surrounding cells) - used here only to enumerate the pairs of
+ *     the plain definition faster; a brute-force O(N^2) enumerator gives the
+ *     same pair set bit for bit;
+ *   - neighbour (Verlet) lists of Sec. II.A: all pairs closer than
+ *     r_list = r_cut + skin at the build positions;
+ *   - each pair counted once (Newton's third law, Sec. II.D.3);
+ *   - Lennard-Jones pair energy u(r) = 4 eps [(s/r)^12 - (s/r)^6], force
+ *     -du/dr along the pair vector, cut (unshifted) at r_cut;
+ *   - per-pair virial W_ab = sum over pairs of d_a f_b;
+ *   - velocity-Verlet integration (the paper only says "integration of the
+ *     equations of motion", Sec. II.A) with a neighbour rebuild whenever some
+ *     particle moved more than skin/2 since the last build (or every k steps,
+ *     the paper's own protocol, Sec. III);
+ *   - serial execution, as the paper's single-thread scheduler (Sec. II.C).
+ *
+ * Readings where the paper is silent (potential, integrator, rebuild rule,
+ * strict '<' at both cutoffs, minimum image by rint) are the ones listed in
+ * the repository's design notes.  All parity of this file is pinned by the
+ * CPU tests (closed forms, finite differences, brute force, lattice sums).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ---------------------------------------------------------------- helpers */
+
+/* Minimum-image displacement component: d - L * rint(d / L). */
+static double mic(double d, double L)
+{
+    return d - L * nearbyint(d / L);
+}
+
+/* x_i - x_j under minimum image; returns |d|^2 summed in x, y, z order. */
+static double pair_disp(const double *x, int64_t i, int64_t j, const double *box, double d[3])
+{
+    d[0] = mic(x[3 * i + 0] - x[3 * j + 0], box[0]);
+    d[1] = mic(x[3 * i + 1] - x[3 * j + 1], box[1]);
+    d[2] = mic(x[3 * i + 2] - x[3 * j + 2], box[2]);
+    return d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+}
+
+typedef void (*pair_fn)(void *ctx, int64_t i, int64_t j, const double d[3], double r2);
+
+/*
+ * Call fn(i, j, d, r2) once for every unordered pair i < j with r2 < r*r.
+ * brute != 0 forces the O(N^2) loop; otherwise linked cells of width >= r
+ * are used when every dimension holds at least 3 of them.
+ */
+static void for_each_pair(int64_t n, const double *x, const double *box, double r,
+                          int brute, pair_fn fn, void *ctx)
+{
+    const double r2max = r * r;
+    int nc[3];
+    for (int k = 0; k < 3; ++k) {
+        nc[k] = (int)floor(box[k] / r);
+        if (nc[k] < 1) nc[k] = 1;
+    }
+    if (brute || nc[0] < 3 || nc[1] < 3 || nc[2] < 3) {
+        double d[3];
+        for (int64_t i = 0; i < n; ++i)
+            for (int64_t j = i + 1; j < n; ++j) {
+                double r2 = pair_disp(x, i, j, box, d);
+                if (r2 < r2max) fn(ctx, i, j, d, r2);
+            }
+        return;
+    }
+    /* linked cells: head[c] is the first particle of cell c, next[i] the one after i */
+    const int64_t ncell = (int64_t)nc[0] * nc[1] * nc[2];
+    int64_t *head = (int64_t *)malloc(sizeof(int64_t) * ncell);
+    int64_t *next = (int64_t *)malloc(sizeof(int64_t) * (n > 0 ? n : 1));
+    int32_t *cell = (int32_t *)malloc(sizeof(int32_t) * 3 * (n > 0 ? n : 1));
+    for (int64_t c = 0; c < ncell; ++c) head[c] = -1;
+    for (int64_t i = n - 1; i >= 0; --i) {
+        int cc[3];
+        for (int k = 0; k < 3; ++k) {
+            double w = box[k] / nc[k];
+            double xk = x[3 * i + k] - box[k] * floor(x[3 * i + k] / box[k]);
+            int c = (int)floor(xk / w);
+            if (c < 0) c = 0;
+            if (c >= nc[k]) c = nc[k] - 1;
+            cc[k] = c;
+            cell[3 * i + k] = c;
+        }
+        int64_t c = ((int64_t)cc[2] * nc[1] + cc[1]) * nc[0] + cc[0];
+        next[i] = head[c];
+        head[c] = i;
+    }
+    double d[3];
+    for (int64_t i = 0; i < n; ++i) {
+        for (int oz = -1; oz <= 1; ++oz)
+            for (int oy = -1; oy <= 1; ++oy)
+                for (int ox = -1; ox <= 1; ++ox) {
+                    int cx = (cell[3 * i + 0] + ox + nc[0]) % nc[0];
+                    int cy = (cell[3 * i + 1] + oy + nc[1]) % nc[1];
+                    int cz = (cell[3 * i + 2] + oz + nc[2]) % nc[2];
+                    int64_t c = ((int64_t)cz * nc[1] + cy) * nc[0] + cx;
+                    for (int64_t j = head[c]; j >= 0; j = next[j]) {
+                        if (j <= i) continue;
+                        double r2 = pair_disp(x, i, j, box, d);
+                        if (r2 < r2max) fn(ctx, i, j, d, r2);
+                    }
+                }
+    }
+    free(head);
+    free(next);
+    free(cell);
+}
+
+/* ------------------------------------------------------- neighbour pairs */
+
+typedef struct {
+    int64_t count, cap;
+    int32_t *pairs; /* nullable: 2 x cap */
+} pair_sink;
+
+static void collect_pair(void *ctx, int64_t i, int64_t j, const double d[3], double r2)
+{
+    (void)d;
+    (void)r2;
+    pair_sink *s = (pair_sink *)ctx;
+    if (s->pairs && s->count < s->cap) {
+        s->pairs[2 * s->count + 0] = (int32_t)i;
+        s->pairs[2 * s->count + 1] = (int32_t)j;
+    }
+    s->count++;
+}
+
+static int cmp_pair(const void *a, const void *b)
+{
+    const int32_t *p = (const int32_t *)a, *q = (const int32_t *)b;
+    if (p[0] != q[0]) return p[0] < q[0] ? -1 : 1;
+    if (p[1] != q[1]) return p[1] < q[1] ? -1 : 1;
+    return 0;
+}
+
+/*
+ * Neighbour set at positions x: all pairs (i, j), i < j, with minimum-image
+ * |x_i - x_j|^2 < r_list^2 (strict).  Returns the number of pairs; if pairs is
+ * non-null and cap is large enough they are written sorted by (i, j).
+ */
+int64_t orc_neighbor_pairs(int64_t n, const double *x, const double *box, double r_list,
+                           int brute, int64_t cap, int32_t *pairs)
+{
+    pair_sink s = {0, cap, pairs};
+    for_each_pair(n, x, box, r_list, brute, collect_pair, &s);
+    if (pairs && s.count <= cap) qsort(pairs, (size_t)s.count, 2 * sizeof(int32_t), cmp_pair);
+    return s.count;
+}
+
+/* ------------------------------------------------------- Lennard-Jones */
+
+typedef struct {
+    int32_t nsp;
+    const double *eps, *sig, *rc; /* nsp x nsp, row-major, symmetric */
+    const int32_t *species;       /* nullable: all species 0 */
+    double *f;                    /* N x 3, accumulated */
+    double *pe_atom;              /* nullable: N, half of each pair energy */
+    double pe, vir[6];
+} lj_acc;
+
+/* One pair: energy, force on i (= -force on j) and virial, if r < r_cut(a,b). */
+static void lj_pair(void *ctx, int64_t i, int64_t j, const double d[3], double r2)
+{
+    lj_acc *a = (lj_acc *)ctx;
+    int32_t si = a->species ? a->species[i] : 0;
+    int32_t sj = a->species ? a->species[j] : 0;
+    int32_t t = si * a->nsp + sj;
+    double rc = a->rc[t];
+    if (!(r2 < rc * rc)) return;
+    double s = a->sig[t];
+    double e = a->eps[t];
+    double sr2 = (s * s) / r2;
+    double s6 = sr2 * sr2 * sr2;
+    double u = 4.0 * e * (s6 * s6 - s6);
+    double fr = 24.0 * e * (2.0 * s6 * s6 - s6) / r2; /* |f| / r, positive = repulsive */
+    for (int k = 0; k < 3; ++k) {
+        a->f[3 * i + k] += fr * d[k];
+        a->f[3 * j + k] -= fr * d[k];
+    }
+    a->pe += u;
+    if (a->pe_atom) {
+        a->pe_atom[i] += 0.5 * u;
+        a->pe_atom[j] += 0.5 * u;
+    }
+    a->vir[0] += d[0] * (fr * d[0]);
+    a->vir[1] += d[1] * (fr * d[1]);
+    a->vir[2] += d[2] * (fr * d[2]);
+    a->vir[3] += d[0] * (fr * d[1]);
+    a->vir[4] += d[0] * (fr * d[2]);
+    a->vir[5] += d[1] * (fr * d[2]);
+}
+
+static double max_cut(int32_t nsp, const double *rc)
+{
+    double m = 0.0;
+    for (int32_t t = 0; t < nsp * nsp; ++t)
+        if (rc[t] > m) m = rc[t];
+    return m;
+}
+
+/*
+ * Forces, total potential energy and virial of the whole system at x: the
+ * plain definition, every pair closer than its cutoff counted once.
+ * f (N x 3) is overwritten; pe_atom (nullable) receives half of each pair energy.
+ */
+void orc_lj_forces(int64_t n, const double *x, const double *box, const int32_t *species,
+                   int32_t nsp, const double *eps, const double *sig, const double *rc,
+                   int brute, double *f, double *pe_atom, double *pe, double *vir)
+{
+    memset(f, 0, sizeof(double) * 3 * (size_t)n);
+    if (pe_atom) memset(pe_atom, 0, sizeof(double) * (size_t)n);
+    lj_acc a;
+    memset(&a, 0, sizeof(a));
+    a.nsp = nsp;
+    a.eps = eps;
+    a.sig = sig;
+    a.rc = rc;
+    a.species = species;
+    a.f = f;
+    a.pe_atom = pe_atom;
+    for_each_pair(n, x, box, max_cut(nsp, rc), brute, lj_pair, &a);
+    if (pe) *pe = a.pe;
+    if (vir)
+        for (int k = 0; k < 6; ++k) vir[k] = a.vir[k];
+}
+
+/*
+ * Forces restricted to a given pair set (each unordered pair once), as a
+ * neighbour list is used between rebuilds: only listed pairs closer than
+ * their cutoff contribute.
+ */
+void orc_lj_forces_pairs(int64_t n, const double *x, const double *box, const int32_t *species,
+                         int32_t nsp, const double *eps, const double *sig, const double *rc,
+                         int64_t npairs, const int32_t *pairs, double *f, double *pe, double *vir)
+{
+    memset(f, 0, sizeof(double) * 3 * (size_t)n);
+    lj_acc a;
+    memset(&a, 0, sizeof(a));
+    a.nsp = nsp;
+    a.eps = eps;
+    a.sig = sig;
+    a.rc = rc;
+    a.species = species;
+    a.f = f;
+    double d[3];
+    for (int64_t p = 0; p < npairs; ++p) {
+        int64_t i = pairs[2 * p], j = pairs[2 * p + 1];
+        double r2 = pair_disp(x, i, j, box, d);
+        lj_pair(&a, i, j, d, r2);
+    }
+    if (pe) *pe = a.pe;
+    if (vir)
+        for (int k = 0; k < 6; ++k) vir[k] = a.vir[k];
+}
+
+/*
+ * Force, energy share and virial share on each of m sampled atoms, by a
+ * direct loop over all N partners (O(m N)).  Used to check single atoms of
+ * systems too large for a whole-system oracle run.  vir_out is m x 6.
+ */
+void orc_lj_forces_subset(int64_t n, const double *x, const double *box, const int32_t *species,
+                          int32_t nsp, const double *eps, const double *sig, const double *rc,
+                          int64_t m, const int64_t *idx, double *f_out, double *pe_out, double *vir_out)
+{
+    double d[3];
+    for (int64_t q = 0; q < m; ++q) {
+        int64_t i = idx[q];
+        int32_t si = species ? species[i] : 0;
+        double f[3] = {0.0, 0.0, 0.0}, pe = 0.0, w[6] = {0, 0, 0, 0, 0, 0};
+        for (int64_t j = 0; j < n; ++j) {
+            if (j == i) continue;
+            int32_t sj = species ? species[j] : 0;
+            int32_t t = si * nsp + sj;
+            double r2 = pair_disp(x, i, j, box, d);
+            double rcut = rc[t];
+            if (!(r2 < rcut * rcut)) continue;
+            double s = sig[t], e = eps[t];
+            double sr2 = (s * s) / r2;
+            double s6 = sr2 * sr2 * sr2;
+            double u = 4.0 * e * (s6 * s6 - s6);
+            double fr = 24.0 * e * (2.0 * s6 * s6 - s6) / r2;
+            for (int k = 0; k < 3; ++k) f[k] += fr * d[k];
+            pe += 0.5 * u;
+            w[0] += 0.5 * (d[0] * (fr * d[0]));
+            w[1] += 0.5 * (d[1] * (fr * d[1]));
+            w[2] += 0.5 * (d[2] * (fr * d[2]));
+            w[3] += 0.5 * (d[0] * (fr * d[1]));
+            w[4] += 0.5 * (d[0] * (fr * d[2]));
+            w[5] += 0.5 * (d[1] * (fr * d[2]));
+        }
+        for (int k = 0; k < 3; ++k) f_out[3 * q + k] = f[k];
+        if (pe_out) pe_out[q] = pe;
+        if (vir_out)
+            for (int k = 0; k < 6; ++k) vir_out[6 * q + k] = w[k];
+    }
+}
+
+/* ------------------------------------------------------- integration */
+
+/* Kinetic energy 1/2 sum m v^2 (mass per species). */
+double orc_kinetic(int64_t n, const double *v, const int32_t *species, const double *mass)
+{
+    double ke = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        double m = mass[species ? species[i] : 0];
+        ke += 0.5 * m * (v[3 * i] * v[3 * i] + v[3 * i + 1] * v[3 * i + 1] + v[3 * i + 2] * v[3 * i + 2]);
+    }
+    return ke;
+}
+
+/*
+ * Velocity-Verlet run of nsteps with neighbour rebuilds.
+ *
+ * Per step: v += (dt/2m) F;  x += dt v;  rebuild test;  F = F(x);
+ * v += (dt/2m) F.  The rebuild test (policy 0) fires when some particle's
+ * squared displacement since the last build exceeds (skin/2)^2; policy 1
+ * fires every k-th step.  A rebuild maps positions back into [0, L) (one
+ * box length at most, counted in the image array) and records them as the
+ * new reference positions.  Forces are the plain definition at every step.
+ *
+ * x, v, image (N x 3) are updated in place.  Optional per-step outputs
+ * (length nsteps): pe_hist, ke_hist.  Returns the number of rebuilds.
+ */
+int64_t orc_run_nve(int64_t n, double *x, double *v, int32_t *image, const double *box,
+                    const int32_t *species, int32_t nsp, const double *eps, const double *sig,
+                    const double *rc, const double *mass, double dt, double skin,
+                    int32_t policy, int32_t every_k, int64_t nsteps,
+                    double *pe_hist, double *ke_hist)
+{
+    double *f = (double *)malloc(sizeof(double) * 3 * (size_t)n);
+    double *xref = (double *)malloc(sizeof(double) * 3 * (size_t)n);
+    double *hdtm = (double *)malloc(sizeof(double) * (size_t)nsp);
+    for (int32_t s = 0; s < nsp; ++s) hdtm[s] = (0.5 * dt) / mass[s];
+    memcpy(xref, x, sizeof(double) * 3 * (size_t)n);
+    const double half_skin = 0.5 * skin;
+    const double lim2 = half_skin * half_skin;
+    double pe = 0.0, vir[6];
+    int64_t rebuilds = 0;
+    orc_lj_forces(n, x, box, species, nsp, eps, sig, rc, 0, f, NULL, &pe, vir);
+    for (int64_t step = 0; step < nsteps; ++step) {
+        for (int64_t i = 0; i < n; ++i) {
+            double h = hdtm[species ? species[i] : 0];
+            for (int k = 0; k < 3; ++k) {
+                v[3 * i + k] = v[3 * i + k] + h * f[3 * i + k];
+                x[3 * i + k] = x[3 * i + k] + dt * v[3 * i + k];
+            }
+        }
+        int rebuild = 0;
+        if (policy == 1) {
+            rebuild = every_k > 0 && ((step + 1) % every_k) == 0;
+        } else {
+            for (int64_t i = 0; i < n && !rebuild; ++i) {
+                double dx = x[3 * i] - xref[3 * i];
+                double dy = x[3 * i + 1] - xref[3 * i + 1];
+                double dz = x[3 * i + 2] - xref[3 * i + 2];
+                if (dx * dx + dy * dy + dz * dz > lim2) rebuild = 1;
+            }
+        }
+        if (rebuild) {
+            for (int64_t i = 0; i < n; ++i)
+                for (int k = 0; k < 3; ++k) {
+                    double L = box[k];
+                    if (x[3 * i + k] >= L) {
+                        x[3 * i + k] -= L;
+                        image[3 * i + k] += 1;
+                    } else if (x[3 * i + k] < 0.0) {
+                        x[3 * i + k] += L;
+                        image[3 * i + k] -= 1;
+                    }
+                }
+            memcpy(xref, x, sizeof(double) * 3 * (size_t)n);
+            rebuilds++;
+        }
+        orc_lj_forces(n, x, box, species, nsp, eps, sig, rc, 0, f, NULL, &pe, vir);
+        for (int64_t i = 0; i < n; ++i) {
+            double h = hdtm[species ? species[i] : 0];
+            for (int k = 0; k < 3; ++k) v[3 * i + k] = v[3 * i + k] + h * f[3 * i + k];
+        }
+        if (pe_hist) pe_hist[step] = pe;
+        if (ke_hist) ke_hist[step] = orc_kinetic(n, v, species, mass);
+    }
+    free(f);
+    free(xref);
+    free(hdtm);
+    return rebuilds;
+}
