@@ -1,0 +1,350 @@
+#!/usr/bin/env python
+"""Benchmark of the short-range MD hot path: atom-timesteps/s on one GB300.
+
+One benchmark step = md_step(inner) velocity-Verlet time steps (neighbour
+rebuilds whenever some atom moved more than skin/2, exactly as in a
+production run) followed by md_energy_virial (thermodynamic output), on the
+2,048,000-atom Lennard-Jones system (80^3 fcc cells, rho* = 0.8442, T* = 0.72,
+r_cut = 2.5, skin = 0.3, dt = 0.005), mixed precision, full neighbour lists.
+
+Prints one JSON line (rank 0).  With --impl reference the FP64 CPU oracle is
+timed instead, on bounded samples of the same workload.  Under torchrun every
+rank runs its own replica (the method has no data exchange between
+independent systems), and the value is the sum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "atom-timesteps/s"
+WORKLOADS = {
+    "lj_liquid_2048000": dict(n_cells=80, rho=0.8442, T=0.72, seed=2),
+    # smaller case of the same kernels for profiler captures (lists still exceed L2)
+    "lj_liquid_1048576": dict(n_cells=64, rho=0.8442, T=0.72, seed=2),
+}
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--inner", type=int, default=100, help="MD time steps per benchmark step")
+    p.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    p.add_argument("--list", default="full", choices=["full", "half"])
+    p.add_argument("--workload", default="lj_liquid_2048000", choices=sorted(WORKLOADS))
+    p.add_argument("--no-extras", action="store_true", help="skip the FP64 / half-list comparison runs")
+    p.add_argument("--cpu-steps", type=int, default=2, help="oracle time steps in the CPU baseline sample")
+    p.add_argument("--e2e-steps", type=int, default=3)
+    return p.parse_args()
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.out = None
+
+    def start(self):
+        try:
+            self.out = tempfile.TemporaryFile(mode="w+")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.out, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.out.seek(0)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.out.read().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def make_workload(name):
+    from paper_1305_4196_gb300 import workloads as W
+    w = WORKLOADS[name]
+    return W.lj_fcc(w["n_cells"], rho=w["rho"], T=w["T"], seed=w["seed"])
+
+
+def config_of(args, sysm, world):
+    return {"workload": args.workload, "atoms": sysm.n, "box_sigma": float(sysm.box[0]),
+            "rho": WORKLOADS[args.workload]["rho"], "T": WORKLOADS[args.workload]["T"], "r_cut": 2.5,
+            "skin": 0.3, "dt": 0.005, "timesteps_per_step": args.inner, "precision": args.precision,
+            "neighbour_list": args.list, "parallelism": f"replicas{world}" if world > 1 else "single",
+            "l2": "working set > L2 (positions, lists and state exceed 129 MB)"}
+
+
+def cpu_baseline(sysm, steps):
+    """The FP64 oracle as it stands, single thread, on `steps` velocity-Verlet steps of the workload."""
+    from oracle import oracle as O
+    O.build()
+    P = O.LJParams.single()
+    t0 = time.perf_counter()
+    O.run_nve(sysm.pos, sysm.vel, sysm.box, P, 0.005, 0.3, steps)
+    dt = time.perf_counter() - t0
+    return {"value": sysm.n * steps / dt, "unit": METRIC, "cores": 1, "kind": "oracle",
+            "sample": f"{steps} velocity-Verlet steps of the full {sysm.n}-atom workload (initial force "
+                      f"evaluation included), FP64, single thread", "seconds": dt}
+
+
+def run_reference(args):
+    """--impl reference: the CPU oracle on bounded samples (1 MD time step per benchmark step)."""
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    O.build()
+    sysm = make_workload(args.workload)
+    P = O.LJParams.single()
+    x, v = sysm.pos.copy(), sysm.vel.copy()
+    img = np.zeros((sysm.n, 3), dtype=np.int32)
+    for _ in range(args.warmup):
+        r = O.run_nve(x, v, sysm.box, P, 0.005, 0.3, 1, image=img)
+        x, v, img = r["pos"], r["vel"], r["image"]
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        r = O.run_nve(x, v, sysm.box, P, 0.005, 0.3, 1, image=img)
+        times.append(time.perf_counter() - t0)
+        x, v, img = r["pos"], r["vel"], r["image"]
+    total = sum(times)
+    value = sysm.n * args.steps / total
+    cfg = config_of(args, sysm, world)
+    cfg["timesteps_per_step"] = 1
+    cfg["precision"] = "fp64"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded fcc start, Gaussian velocities)", "config": cfg,
+            "cpu_baseline": {"value": value, "unit": METRIC, "cores": 1, "kind": "oracle",
+                             "sample": "1 velocity-Verlet step (with one force evaluation) of the full workload "
+                                       "per benchmark step, FP64, single thread"},
+            "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def algorithmic_force_bytes(n, entries, precision):
+    """Bytes one force evaluation must move at least: coordinates (16 B FP32 / 28 B FP64 with
+    species) and list length (2 B) read per atom, force written (24 B), 2 B per list entry."""
+    per_atom = (16 if precision == "mixed" else 28) + 2 + 24
+    return n * per_atom + 2 * entries
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    from paper_1305_4196_gb300 import build as B
+    B.build()
+    from paper_1305_4196_gb300 import mdgb as M
+
+    sysm = make_workload(args.workload)
+    # CPU baseline first (rank 0, one GPU only): no GPU context is touched by the oracle
+    cpu = cpu_baseline(sysm, args.cpu_steps) if (rank == 0 and world == 1 and args.cpu_steps > 0) else None
+
+    stream = torch.cuda.Stream()
+    prec = M.MD_MIXED if args.precision == "mixed" else M.MD_FP64
+    lst = M.MD_LIST_FULL if args.list == "full" else M.MD_LIST_HALF_COLOUR8
+    s = M.System(sysm.n, sysm.box, precision=prec, list_kind=lst, stream=stream.cuda_stream)
+    s.set_state(sysm.pos, sysm.vel, sysm.species)
+
+    def one_step():
+        s.step(args.inner)
+        s.energy_virial()
+
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+    info0 = s.info()
+    s.set_timing(True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        one_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    info1 = s.info()
+    s.set_timing(False)
+    t_max = ms
+    if world > 1:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    timesteps = args.steps * args.inner
+    value = world * sysm.n * timesteps / (t_max * 1e-3)
+    launches = info1["kernel_launches"] - info0["kernel_launches"]
+
+    # roofline of the dominant kernel (the force evaluation), from events around each launch
+    f_evals = max(info1["timed_force_evals"], 1)
+    f_ms = info1["force_ms"] / f_evals
+    peak, peak_kind = load_peaks()
+    abytes = algorithmic_force_bytes(sysm.n, info1["list_entries"], args.precision)
+    achieved = abytes / (f_ms * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "kernel": "k_force_mixed_full" if args.precision == "mixed" else "k_force_fp64_full",
+                "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)", "traffic": None,
+                "algorithmic_bytes": abytes, "avg_launch_ms": f_ms, "launches_timed": info1["timed_force_evals"],
+                "force_share_of_step": info1["force_ms"] / ms}
+
+    # end to end through the C ABI with pinned host buffers, copies inside the timed region
+    e2e = None
+    if args.e2e_steps > 0:
+        pos_h = torch.empty((sysm.n, 3), dtype=torch.float64, pin_memory=True).numpy()
+        vel_h = torch.empty((sysm.n, 3), dtype=torch.float64, pin_memory=True).numpy()
+        img_h = torch.empty((sysm.n, 3), dtype=torch.int32, pin_memory=True).numpy()
+        sp_h = torch.empty((sysm.n,), dtype=torch.int32, pin_memory=True).numpy()
+        s.get_state()  # warm path
+        M.md_get_state(s.handle, pos_h, vel_h, img_h)
+        sp_h[:] = sysm.species
+        pos_h += img_h * sysm.box
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            M.md_set_state(s.handle, pos_h, vel_h, sp_h)
+            s.step(args.inner)
+            M.md_get_state(s.handle, pos_h, vel_h, img_h)
+            s.energy_virial()
+        torch.cuda.synchronize()
+        t_e2e = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([t_e2e], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            t_e2e = float(t.item())
+        e2e = {"value": world * sysm.n * args.inner * args.e2e_steps / t_e2e, "unit": METRIC,
+               "h2d_bytes_per_step": sysm.n * (24 + 24 + 4), "d2h_bytes_per_step": sysm.n * (24 + 24 + 12) + 64}
+
+    extras = {}
+    if not args.no_extras and rank == 0 and world == 1:
+        extras = comparisons(args, sysm, M, stream, value)
+
+    s.close()
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32+i64" if args.precision == "mixed" else "f64",
+                "data": "synthetic (seeded fcc start, Gaussian velocities at T*=0.72)",
+                "config": config_of(args, sysm, world), "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "clocks": clk, "gpu_launches": launches,
+                "rebuilds_per_timestep": (info1["n_builds"] - info0["n_builds"]) / timesteps,
+                "ns_per_atom_timestep": t_max * 1e6 / (sysm.n * timesteps),
+                "build_ms_avg": info1["build_ms"] / max(info1["timed_builds"], 1)}
+        line.update(extras)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def comparisons(args, sysm, M, stream, value):
+    """Same workload on the FP64 GPU path and on the 8-colour half-list path (short runs)."""
+    import torch
+    out = {}
+    runs = []
+    if args.precision == "mixed":
+        runs.append(("fp64_gpu", M.MD_FP64, M.MD_LIST_FULL, 10, 2))
+    runs.append(("half_colour8_mixed" if args.list == "full" else "full_mixed", M.MD_MIXED,
+                 M.MD_LIST_HALF_COLOUR8 if args.list == "full" else M.MD_LIST_FULL, args.inner, 3))
+    for name, prec, lst, inner, steps in runs:
+        s = M.System(sysm.n, sysm.box, precision=prec, list_kind=lst, stream=stream.cuda_stream)
+        s.set_state(sysm.pos, sysm.vel, sysm.species)
+        s.step(inner)
+        torch.cuda.synchronize()
+        s.set_timing(True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            s.step(inner)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        info = s.info()
+        v = sysm.n * inner * steps / (ms * 1e-3)
+        out[name] = {"value": v, "unit": METRIC, "timesteps": inner * steps,
+                     "force_ms_avg": info["force_ms"] / max(info["timed_force_evals"], 1)}
+        s.close()
+    if "fp64_gpu" in out:
+        out["speedup_mixed_vs_fp64_gpu"] = value / out["fp64_gpu"]["value"]
+    return {"compare": out}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,202 @@
+/*
+ * mdgb.h - C ABI of the GB300 (sm_103a) short-range molecular-dynamics hot path.
+ *
+ * The calls follow the problem statement of R. Meyer, "Efficient
+ * Parallelization of Short-Range Molecular Dynamics Simulations on Many-Core
+ * Systems" (arXiv:1305.4196): N particles in a periodic box whose
+ * interactions vanish beyond a cutoff r_cut (Sec. I), binned into linked
+ * cells at least as wide as the interaction range (Sec. II.A, step 1 of the
+ * algorithm), neighbour lists built per cell (Sec. II.A), forces computed per
+ * cell task (Sec. II.A, step 2) with no particle written by two workers at
+ * once (Sec. II.A; Sec. II.B waves), thread-local energy accumulators and a
+ * particle-parallel integration loop (Sec. II.C).
+ *
+ * Conventions shared by every call
+ *  - Status: every int-returning call returns MD_OK (0) or a negative MD_ERR_*
+ *    code; md_last_error() gives a message.  No exception or abort crosses the
+ *    ABI.  A failed call leaves the system usable unless it returns MD_ERR_CUDA.
+ *  - Atom order at the boundary is always the caller's original order
+ *    (index 0..N-1 as passed to md_set_state); the library reorders atoms into
+ *    cell order internally and hides it.
+ *  - Arrays of 3-vectors are N x 3, row-major (x0 y0 z0 x1 y1 z1 ...).
+ *  - Ownership: the caller owns every array it passes and keeps ownership;
+ *    the library copies in or out during the call (stream-ordered) and owns
+ *    only its opaque workspace, freed by md_destroy().
+ *  - Host or device: calls with a `device_ptrs` argument take device pointers
+ *    when it is non-zero and host pointers otherwise.  Everything runs on the
+ *    CUDA stream given in md_params.stream (NULL: the legacy default stream)
+ *    on the device that was current at md_create().
+ *  - Calls are asynchronous on the stream except those that return host
+ *    values (md_energy_virial, md_get_neighbors, md_get_info, host-pointer
+ *    copies), which synchronise the stream before returning.
+ *  - Units: reduced LJ units (sigma, epsilon, mass, tau).
+ */
+#ifndef MDGB_H
+#define MDGB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes */
+#define MD_OK                 0
+#define MD_ERR_ARG           -1  /* bad argument (null, size, range, species id) */
+#define MD_ERR_BOX_TOO_SMALL -2  /* some box side < 4 (r_cut + skin): cell grid and minimum image invalid */
+#define MD_ERR_CELL_OVERFLOW -3  /* a cell neighbourhood does not fit the on-chip tile even after regrowth */
+#define MD_ERR_LIST_OVERFLOW -4  /* a neighbour list does not fit even after regrowth */
+#define MD_ERR_NONFINITE     -5  /* a non-finite force or position appeared */
+#define MD_ERR_SKIN_VIOLATION -6 /* fixed-interval rebuild policy and an atom moved more than skin/2 */
+#define MD_ERR_CUDA          -7  /* a CUDA runtime call failed; the system should be destroyed */
+#define MD_ERR_TIMEOUT       -8  /* a bounded device-side wait gave up */
+#define MD_ERR_STATE         -9  /* call out of order (e.g. no md_set_state yet) */
+
+/* ---- md_params.precision */
+#define MD_FP64  0  /* FP64 positions, pair arithmetic and accumulation */
+#define MD_MIXED 1  /* FP32 pair arithmetic, 64-bit fixed-point force sums, FP64 integration and reductions */
+
+/* ---- md_params.list_kind */
+#define MD_LIST_FULL         0  /* every pair in both atoms' lists; each list owned by one thread, no writes to j */
+#define MD_LIST_HALF_COLOUR8 1  /* each pair once (Newton's third law); forces in 8 colour phases of 2x2x2-cell blocks */
+
+/* ---- md_params.rebuild */
+#define MD_REBUILD_SKIN_HALF 0  /* rebuild when some atom moved more than skin/2 since the last build (default) */
+#define MD_REBUILD_EVERY_K   1  /* rebuild every rebuild_k steps, as in the paper's benchmarks (Sec. III) */
+
+typedef struct md_system md_system; /* opaque; owns all device workspace */
+
+typedef struct {
+    int32_t n_species;     /* >= 1 */
+    const double *eps;     /* n_species^2, row-major, symmetric: LJ well depth per species pair */
+    const double *sigma;   /* n_species^2, row-major, symmetric: LJ diameter per species pair */
+    const double *rcut;    /* n_species^2 or NULL: per-pair cutoff (NULL: r_cut of md_create for all pairs) */
+    const double *mass;    /* n_species */
+    double dt;             /* time step */
+    int32_t precision;     /* MD_FP64 | MD_MIXED */
+    int32_t list_kind;     /* MD_LIST_FULL | MD_LIST_HALF_COLOUR8 */
+    int32_t rebuild;       /* MD_REBUILD_SKIN_HALF | MD_REBUILD_EVERY_K */
+    int32_t rebuild_k;     /* interval for MD_REBUILD_EVERY_K */
+    void *stream;          /* cudaStream_t, or NULL for the legacy default stream */
+} md_params;
+
+typedef struct {
+    int64_t n;             /* atoms */
+    int32_t ncell[3];      /* cells per dimension (multiples of 4) */
+    int32_t list_cap;      /* current neighbour-list capacity per atom */
+    int32_t tile_cap;      /* current on-chip tile capacity (atoms of a 4x4x4-cell neighbourhood) */
+    int64_t n_builds;      /* neighbour-list builds so far */
+    int64_t n_steps;       /* time steps integrated so far */
+    int64_t list_entries;  /* sum of list lengths at the last build */
+    int32_t max_list;      /* longest list at the last build */
+    int32_t max_tile;      /* largest tile at the last build */
+    double cell_width[3];  /* sigma */
+    int64_t kernel_launches;   /* kernels launched by the library so far */
+    int64_t force_evals;       /* force evaluations (one per step, plus md_forces / md_energy_virial) */
+    double force_ms;           /* summed device time of force evaluations (only while timing is on) */
+    int64_t timed_force_evals; /* force evaluations included in force_ms */
+    double build_ms;           /* summed device time of binning + list builds (only while timing is on) */
+    int64_t timed_builds;      /* builds included in build_ms */
+} md_info;
+
+/*
+ * Create a system of n atoms in the periodic box box[3] (sides, sigma) with
+ * cutoff r_cut and Verlet skin `skin` (neighbour-list radius r_cut + skin;
+ * Sec. II.A).  Picks the cell grid: per dimension the largest multiple of 4
+ * cells whose width is at least r_cut + skin (Sec. II.A: cells wider than the
+ * interaction range; multiples of 4 so that 2x2x2-cell blocks split into 8
+ * colour classes, Sec. II.D.2 blocking).  Allocates all device workspace.
+ * Errors: MD_ERR_ARG, MD_ERR_BOX_TOO_SMALL, MD_ERR_CUDA.  *out is NULL on error.
+ */
+int md_create(int64_t n, const double box[3], double r_cut, double skin,
+              const md_params *p, md_system **out);
+
+/*
+ * Load positions, velocities (N x 3, original order) and species ids (N,
+ * values in [0, n_species); NULL: all 0).  Positions may lie anywhere; they
+ * are mapped into [0, L) at the next neighbour build.  Invalidates forces and
+ * lists.  Errors: MD_ERR_ARG (bad species id), MD_ERR_CUDA.
+ */
+int md_set_state(md_system *s, const double *pos, const double *vel,
+                 const int32_t *species, int device_ptrs);
+
+/*
+ * Bin atoms into the cell grid (Sec. II.A, step 1): map positions into
+ * [0, L) (updating image counters), assign each atom its cell, counting-sort
+ * atoms into cell order (cells grouped by 2x2x2 block, atoms inside a cell in
+ * original-index order) and reorder all per-atom state.  Invalidates lists.
+ */
+int md_bin_cells(md_system *s);
+
+/*
+ * Bin (as md_bin_cells) and build the neighbour lists (Sec. II.A): for each
+ * atom every other atom at minimum-image distance < r_cut + skin, exactly the
+ * set the FP64 definition gives at the current positions.  Records the
+ * positions as the reference for the skin/2 displacement test.
+ * Errors: MD_ERR_CELL_OVERFLOW / MD_ERR_LIST_OVERFLOW only if regrowth fails.
+ */
+int md_build_neighbors(md_system *s);
+
+/*
+ * Forces at the current positions (Sec. II.A, step 2), rebuilding the lists
+ * first if there are none or some atom moved more than skin/2.  If f_out is
+ * non-NULL the forces are copied to it (N x 3 doubles, original order).
+ */
+int md_forces(md_system *s, double *f_out, int device_ptrs);
+
+/*
+ * Integrate n_steps velocity-Verlet steps: v += dt F/(2m); x += dt v;
+ * rebuild lists if the policy says so; F = F(x); v += dt F/(2m).
+ * Energies are not computed on the way (use md_energy_virial).
+ * Errors: MD_ERR_NONFINITE, MD_ERR_SKIN_VIOLATION, overflow codes, MD_ERR_CUDA.
+ */
+int md_step(md_system *s, int32_t n_steps);
+
+/*
+ * Potential energy, kinetic energy and virial W_ab = sum over pairs of
+ * d_a f_b (d = x_i - x_j, f = force on i; components xx yy zz xy xz yz) at the
+ * current state, reduced in FP64 in a fixed order (Sec. II.C thread-local
+ * accumulators).  Any output pointer may be NULL.  Host outputs; synchronises.
+ */
+int md_energy_virial(md_system *s, double *pe, double *ke, double virial[6]);
+
+/*
+ * Copy the state out in original order: positions as stored (unwrapped since
+ * the last build; add image * L for fully unwrapped coordinates), velocities
+ * and image counters (N x 3 int32).  Any output may be NULL.
+ */
+int md_get_state(md_system *s, double *pos, double *vel, int32_t *image, int device_ptrs);
+
+/*
+ * The neighbour pair set of the last build as unordered pairs (i, j), i < j,
+ * original ids, sorted by (i, j).  *n_pairs receives the count; pairs (host,
+ * 2 x n_pairs int32) may be NULL to query the count only.  Full lists list
+ * each pair twice internally; it is reported once.  Synchronises.
+ */
+int md_get_neighbors(md_system *s, int64_t *n_pairs, int32_t *pairs);
+
+/* Cell of every atom at the last binning (original order, linear index x fastest). Host output. */
+int md_get_cells(md_system *s, int32_t *cell_of_atom);
+
+/* Sizes and counters; host output. */
+int md_get_info(md_system *s, md_info *out);
+
+/*
+ * Turn per-phase device timing on (enable != 0) or off.  While on, the
+ * library brackets every force evaluation and every binning + list build with
+ * CUDA events on its stream and adds their elapsed times to md_info.force_ms
+ * and md_info.build_ms (the counters restart when timing is switched on).
+ */
+int md_set_timing(md_system *s, int enable);
+
+/* Copy the last error message into buf (at most len bytes, NUL-terminated). */
+int md_last_error(md_system *s, char *buf, int64_t len);
+
+/* Free all device workspace. NULL is allowed. */
+void md_destroy(md_system *s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MDGB_H */

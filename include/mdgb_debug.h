@@ -1,0 +1,43 @@
+/*
+ * mdgb_debug.h - host-only introspection of the cell grid and the colour
+ * schedule used by libmdgb (no GPU needed).
+ *
+ * The cell task method lets two tasks run at the same time only if they do
+ * not overlap: at least two cells lie between them in every direction
+ * (Meyer 2013, Sec. II.A), and waves of such tasks run one after another
+ * (Sec. II.B).  libmdgb's 2x2x2-cell blocks (Sec. II.D.2) are split into 8
+ * colour classes; these calls expose the exact numbering the kernels use so
+ * that a test can check, on the CPU, that the 4x4x4-cell neighbourhoods of
+ * all blocks of one colour are pairwise disjoint.
+ *
+ * All functions are pure host code, return MD_OK (0) or MD_ERR_ARG (-1),
+ * write only to the caller's arrays and allocate nothing.
+ */
+#ifndef MDGB_DEBUG_H
+#define MDGB_DEBUG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Cells per dimension md_create() picks for box[3] and list radius r_list
+ * (largest multiple of 4 with width >= r_list).  MD_ERR_BOX_TOO_SMALL (-2) if < 4. */
+int mdgb_grid_shape(const double box[3], double r_list, int32_t nc_out[3]);
+
+/* Number of 2x2x2 blocks for a grid of nc[3] cells (nc multiples of 4). */
+int mdgb_num_blocks(const int32_t nc[3], int32_t *nblock_out);
+
+/* Colour class (0..7) of block `block`. */
+int mdgb_block_colour(const int32_t nc[3], int32_t block, int32_t *colour_out);
+
+/* The 64 cells of block `block`'s tile in tile order (own 8 cells first), as
+ * linear cell indices cx + nc[0]*(cy + nc[1]*cz). */
+int mdgb_tile_cells(const int32_t nc[3], int32_t block, int32_t cells_out[64]);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MDGB_DEBUG_H */

@@ -1,0 +1,7 @@
+"""GB300-native short-range molecular dynamics hot path (arXiv:1305.4196).
+
+Submodules:
+  workloads - seeded synthetic inputs (no method arithmetic)
+  build     - nvcc build of libmdgb.so (sm_103a)
+  mdgb      - Python binding of the C ABI (loads libmdgb.so; raises if it is missing)
+"""

@@ -1,0 +1,750 @@
+// api.cu - the C ABI of include/mdgb.h on top of the sm_103a kernels.
+//
+// Host-side orchestration only: argument checks, workspace, the cell grid,
+// capacity regrowth, and the order of kernel launches on the caller's stream.
+// Every arithmetic step of the hot path runs in the kernels.
+#include "mdgb.h"
+#include "mdgb_internal.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+using namespace mdgb;
+
+struct md_system {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int64_t n = 0;
+    int np = 64;
+    Geometry g{};
+    PairTable pt{};
+    TileOffsets to{};
+    double box[3] = {0, 0, 0};
+    double rcut = 0, skin = 0, rl = 0, rl2 = 0, dt = 0, lim2 = 0;
+    int precision = MD_MIXED, list_kind = MD_LIST_FULL, rebuild = MD_REBUILD_SKIN_HALF, rebuild_k = 10;
+    int list_cap = 0, tile_cap = 0;
+    DevState st[2]{};
+    int cur = 0;
+    // binning scratch
+    int32_t *atom_cell = nullptr, *cell_count = nullptr, *cursor = nullptr, *slot_key = nullptr,
+            *slot_src = nullptr, *sorted_src = nullptr, *scan_scratch = nullptr;
+    double *partials = nullptr, *out8 = nullptr;
+    int nparts = 0;
+    uint32_t* h_flags = nullptr;  // pinned: [0] err, [1] rebuild flag, [2..5] stats
+    bool has_state = false, lists_valid = false, forces_valid = false;
+    int64_t n_builds = 0, n_steps = 0, list_entries = 0;
+    int max_list = 0, max_tile = 0;
+    std::vector<void*> allocs;
+    // launch accounting and optional event timing
+    int64_t launches = 0, force_evals = 0;
+    bool timing = false;
+    double force_ms = 0, build_ms = 0;
+    int64_t timed_force = 0, timed_build = 0;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_force, ev_build, ev_free;
+    char msg[512] = "";
+};
+
+namespace {
+
+int fail(md_system* s, int code, const char* fmt, ...) {
+    if (s) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(s->msg, sizeof(s->msg), fmt, ap);
+        va_end(ap);
+    }
+    return code;
+}
+
+#define CK(call)                                                                                   \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess)                                                                     \
+            return fail(s, MD_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_));           \
+    } while (0)
+
+#define CKL()                                                                                      \
+    do {                                                                                           \
+        cudaError_t e_ = cudaGetLastError();                                                       \
+        if (e_ != cudaSuccess)                                                                     \
+            return fail(s, MD_ERR_CUDA, "kernel launch failed (%s:%d): %s", __FILE__, __LINE__,    \
+                        cudaGetErrorString(e_));                                                   \
+    } while (0)
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int now = -1;
+        cudaGetDevice(&now);
+        if (prev >= 0 && now != prev) cudaSetDevice(prev);
+    }
+};
+
+template <typename T>
+int dalloc(md_system* s, T** p, size_t count) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    void* q = nullptr;
+    CK(cudaMalloc(&q, count * sizeof(T)));
+    s->allocs.push_back(q);
+    *p = static_cast<T*>(q);
+    return MD_OK;
+}
+
+void dfree(md_system* s, void* p) {
+    if (!p) return;
+    auto it = std::find(s->allocs.begin(), s->allocs.end(), p);
+    if (it != s->allocs.end()) s->allocs.erase(it);
+    cudaFree(p);
+}
+
+bool mixed(const md_system* s) { return s->precision == MD_MIXED; }
+bool half(const md_system* s) { return s->list_kind == MD_LIST_HALF_COLOUR8; }
+
+int round_up(int v, int m) { return (v + m - 1) / m * m; }
+
+// ---- event timing
+std::pair<cudaEvent_t, cudaEvent_t> take_events(md_system* s) {
+    if (!s->ev_free.empty()) {
+        auto e = s->ev_free.back();
+        s->ev_free.pop_back();
+        return e;
+    }
+    std::pair<cudaEvent_t, cudaEvent_t> e{nullptr, nullptr};
+    cudaEventCreate(&e.first);
+    cudaEventCreate(&e.second);
+    return e;
+}
+
+// add the elapsed times of completed event pairs (call after a stream synchronisation)
+void drain_events(md_system* s) {
+    for (auto& e : s->ev_force) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, e.first, e.second) == cudaSuccess) {
+            s->force_ms += ms;
+            s->timed_force++;
+        }
+        s->ev_free.push_back(e);
+    }
+    for (auto& e : s->ev_build) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, e.first, e.second) == cudaSuccess) {
+            s->build_ms += ms;
+            s->timed_build++;
+        }
+        s->ev_free.push_back(e);
+    }
+    s->ev_force.clear();
+    s->ev_build.clear();
+}
+
+// neighbour-list matrix for the current capacity
+int alloc_lists(md_system* s, int cap) {
+    uint16_t* nl = nullptr;
+    int rc = dalloc(s, &nl, (size_t)cap * s->np);
+    if (rc) return rc;
+    dfree(s, s->st[0].nl);
+    s->st[0].nl = s->st[1].nl = nl;
+    s->list_cap = cap;
+    return MD_OK;
+}
+
+int sync_flags(md_system* s) {
+    CK(cudaMemcpyAsync(s->h_flags, s->st[0].err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaMemcpyAsync(s->h_flags + 1, s->st[0].rebuild_flag, sizeof(int32_t), cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaMemcpyAsync(s->h_flags + 2, s->st[0].stats, 4 * sizeof(int32_t), cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    drain_events(s);
+    return MD_OK;
+}
+
+int check_err(md_system* s, uint32_t mask) {
+    uint32_t e = s->h_flags[0] & mask;
+    if (!e) return MD_OK;
+    if (e & ERR_NONFINITE) return fail(s, MD_ERR_NONFINITE, "non-finite force or coordinate");
+    if (e & ERR_ESCAPE) return fail(s, MD_ERR_NONFINITE, "an atom moved more than one box length");
+    if (e & ERR_SKIN) return fail(s, MD_ERR_SKIN_VIOLATION, "an atom moved more than skin/2 between rebuilds");
+    if (e & ERR_LIST_OVERFLOW) return fail(s, MD_ERR_LIST_OVERFLOW, "neighbour list overflow");
+    if (e & ERR_TILE_OVERFLOW) return fail(s, MD_ERR_CELL_OVERFLOW, "tile overflow");
+    return fail(s, MD_ERR_ARG, "device error 0x%x", e);
+}
+
+// ---- binning: assign, count, scan, scatter, in-cell order, gather (swaps the state buffers)
+int do_bin(md_system* s) {
+    if (s->n == 0) return MD_OK;
+    const Geometry& g = s->g;
+    CK(cudaMemsetAsync(s->cell_count, 0, sizeof(int32_t) * g.ncell, s->stream));
+    CK(cudaMemsetAsync(s->cursor, 0, sizeof(int32_t) * g.ncell, s->stream));
+    DevState& a = s->st[s->cur];
+    DevState& b = s->st[s->cur ^ 1];
+    launch_bin_assign(a, g, s->atom_cell, s->cell_count, s->stream);
+    launch_scan(s->cell_count, a.cell_start, g.ncell, s->scan_scratch, s->stream);
+    launch_scatter(a, s->atom_cell, a.cell_start, s->cursor, s->slot_key, s->slot_src, s->stream);
+    launch_cell_sort(g, a.cell_start, s->slot_key, s->slot_src, s->sorted_src, s->stream);
+    launch_gather(b, a, g, s->sorted_src, s->atom_cell, mixed(s), s->stream);
+    CKL();
+    s->launches += 7;
+    s->cur ^= 1;
+    s->lists_valid = false;
+    s->forces_valid = false;
+    return MD_OK;
+}
+
+// ---- list build with capacity regrowth (host-visible: reads the device counters)
+int do_build(md_system* s) {
+    std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
+    if (s->timing && s->n > 0) {
+        ev = take_events(s);
+        CK(cudaEventRecord(ev.first, s->stream));
+    }
+    int rc = do_bin(s);
+    if (rc) return rc;
+    if (s->n == 0) {
+        s->lists_valid = true;
+        return MD_OK;
+    }
+    for (int attempt = 0; attempt < 4; ++attempt) {
+        DevState& a = s->st[s->cur];
+        CK(cudaMemsetAsync(a.stats, 0, 4 * sizeof(int32_t), s->stream));
+        CK(cudaMemsetAsync(a.err, 0, sizeof(uint32_t), s->stream));
+        if (build_lists_smem(s->list_cap, s->tile_cap) > 226 * 1024)
+            return fail(s, MD_ERR_CELL_OVERFLOW, "tile (%d atoms) and lists (%d) exceed shared memory",
+                        s->tile_cap, s->list_cap);
+        launch_build_lists(a, s->g, s->to, s->rl2, s->list_cap, s->tile_cap, half(s), s->stream);
+        CKL();
+        s->launches += 1;
+        if (ev.second) {
+            CK(cudaEventRecord(ev.second, s->stream));
+            s->ev_build.push_back(ev);
+            ev = {nullptr, nullptr};
+        }
+        rc = sync_flags(s);
+        if (rc) return rc;
+        const uint32_t e = s->h_flags[0];
+        const int max_list = (int)s->h_flags[2], max_tile = (int)s->h_flags[3];
+        bool again = false;
+        if (e & ERR_TILE_OVERFLOW) {
+            int cap = round_up(max_tile + max_tile / 4 + 64, 64);
+            if (cap > 65535) return fail(s, MD_ERR_CELL_OVERFLOW, "tile of %d atoms exceeds 16-bit indices", max_tile);
+            s->tile_cap = cap;
+            again = true;
+        }
+        if (e & ERR_LIST_OVERFLOW) {
+            int cap = round_up(max_list + max_list / 8 + 8, 8);
+            if (cap > 65535) return fail(s, MD_ERR_LIST_OVERFLOW, "list of %d neighbours", max_list);
+            rc = alloc_lists(s, cap);
+            if (rc) return rc;
+            again = true;
+        }
+        if (!again) {
+            rc = check_err(s, ~0u);
+            if (rc) return rc;
+            s->max_list = max_list;
+            s->max_tile = max_tile;
+            uint64_t sum = (uint64_t)s->h_flags[4] | ((uint64_t)s->h_flags[5] << 32);
+            s->list_entries = (int64_t)sum;
+            s->n_builds++;
+            s->lists_valid = true;
+            // keep the tile capacity close to the need (max_tile counts the dummy slot) so
+            // that more CTAs fit per SM and every shared-memory layout stays within limits
+            s->tile_cap = round_up(max_tile + max_tile / 8 + 32, 32);
+            return MD_OK;
+        }
+    }
+    return fail(s, MD_ERR_LIST_OVERFLOW, "capacity regrowth did not converge");
+}
+
+int do_forces(md_system* s, int with_energy) {
+    if (s->n == 0) return MD_OK;
+    const DevState& a = s->st[s->cur];
+    std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
+    if (s->timing && !with_energy) {
+        ev = take_events(s);
+        CK(cudaEventRecord(ev.first, s->stream));
+    }
+    if (mixed(s)) {
+        if (force_smem_bytes(1, half(s), with_energy, s->tile_cap) > 226 * 1024)
+            return fail(s, MD_ERR_CELL_OVERFLOW, "tile of %d atoms exceeds shared memory", s->tile_cap);
+        launch_forces_mixed(a, s->g, s->pt, s->to, s->tile_cap, half(s), with_energy, s->stream);
+    } else {
+        if (force_smem_bytes(0, half(s), with_energy, s->tile_cap) > 226 * 1024)
+            return fail(s, MD_ERR_CELL_OVERFLOW, "tile of %d atoms exceeds shared memory", s->tile_cap);
+        launch_forces_fp64(a, s->g, s->pt, s->tile_cap, half(s), with_energy, s->stream);
+    }
+    CKL();
+    if (ev.second) {
+        CK(cudaEventRecord(ev.second, s->stream));
+        s->ev_force.push_back(ev);
+    }
+    s->launches += half(s) ? 8 : 1;
+    s->force_evals += 1;
+    s->forces_valid = true;
+    return MD_OK;
+}
+
+int ensure_lists(md_system* s) {
+    if (!s->has_state) return fail(s, MD_ERR_STATE, "no state: call md_set_state first");
+    if (!s->lists_valid) return do_build(s);
+    return MD_OK;
+}
+
+int validate_params(md_system* s, const md_params* p, double r_cut) {
+    if (!p) return fail(s, MD_ERR_ARG, "params is NULL");
+    if (p->n_species < 1 || p->n_species > MAX_SPECIES)
+        return fail(s, MD_ERR_ARG, "n_species must be in [1, %d]", MAX_SPECIES);
+    if (!p->eps || !p->sigma || !p->mass) return fail(s, MD_ERR_ARG, "eps, sigma and mass are required");
+    if (!(p->dt > 0.0) || !std::isfinite(p->dt)) return fail(s, MD_ERR_ARG, "dt must be positive");
+    if (p->precision != MD_FP64 && p->precision != MD_MIXED) return fail(s, MD_ERR_ARG, "bad precision");
+    if (p->list_kind != MD_LIST_FULL && p->list_kind != MD_LIST_HALF_COLOUR8)
+        return fail(s, MD_ERR_ARG, "bad list kind");
+    if (p->rebuild != MD_REBUILD_SKIN_HALF && p->rebuild != MD_REBUILD_EVERY_K)
+        return fail(s, MD_ERR_ARG, "bad rebuild policy");
+    if (p->rebuild == MD_REBUILD_EVERY_K && p->rebuild_k < 1) return fail(s, MD_ERR_ARG, "rebuild_k must be >= 1");
+    const int ns = p->n_species;
+    for (int a = 0; a < ns; ++a) {
+        if (!(p->mass[a] > 0.0)) return fail(s, MD_ERR_ARG, "mass must be positive");
+        for (int b = 0; b < ns; ++b) {
+            const double e = p->eps[a * ns + b], sg = p->sigma[a * ns + b];
+            const double rc = p->rcut ? p->rcut[a * ns + b] : r_cut;
+            if (!(e >= 0.0) || !(sg > 0.0) || !(rc > 0.0) || !std::isfinite(e) || !std::isfinite(sg) ||
+                !std::isfinite(rc))
+                return fail(s, MD_ERR_ARG, "bad LJ parameters for pair (%d,%d)", a, b);
+            if (e != p->eps[b * ns + a] || sg != p->sigma[b * ns + a] ||
+                (p->rcut && rc != p->rcut[b * ns + a]))
+                return fail(s, MD_ERR_ARG, "pair tables must be symmetric");
+        }
+    }
+    return MD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int md_create(int64_t n, const double box[3], double r_cut, double skin, const md_params* p, md_system** out) {
+    if (!out) return MD_ERR_ARG;
+    *out = nullptr;
+    md_system* s = new md_system();
+    auto bail = [&](int code) {
+        md_destroy(s);
+        return code;
+    };
+    if (n < 0 || n > 0x7fffffffLL - 64) return bail(MD_ERR_ARG);
+    if (!box || !(r_cut > 0.0) || !(skin >= 0.0) || !std::isfinite(r_cut) || !std::isfinite(skin))
+        return bail(MD_ERR_ARG);
+    int rc = validate_params(s, p, r_cut);
+    if (rc) return bail(rc);
+    cudaGetDevice(&s->device);
+    s->stream = static_cast<cudaStream_t>(p->stream);
+    s->n = n;
+    s->np = round_up((int)std::max<int64_t>(n, 1), 64);
+    s->precision = p->precision;
+    s->list_kind = p->list_kind;
+    s->rebuild = p->rebuild;
+    s->rebuild_k = p->rebuild_k;
+    s->dt = p->dt;
+    s->skin = skin;
+    // pair table and the list radius
+    const int ns = p->n_species;
+    PairTable& pt = s->pt;
+    pt.nsp = ns;
+    double rcmax = 0.0;
+    for (int t = 0; t < ns * ns; ++t) {
+        const double e = p->eps[t], sg = p->sigma[t];
+        const double rc_t = p->rcut ? p->rcut[t] : r_cut;
+        rcmax = std::max(rcmax, rc_t);
+        pt.sig2_d[t] = sg * sg;
+        pt.eps_d[t] = e;
+        pt.rc2_d[t] = rc_t * rc_t;
+        pt.sig2_f[t] = (float)(sg * sg);
+        pt.c48_f[t] = (float)(48.0 * e * 2048.0);
+        pt.c24_f[t] = (float)(24.0 * e * 2048.0);
+        pt.c4_f[t] = (float)(4.0 * e);
+        pt.rc2_f[t] = (float)(rc_t * rc_t);
+    }
+    for (int a = 0; a < ns; ++a) {
+        pt.mass[a] = p->mass[a];
+        pt.hdtm[a] = (0.5 * p->dt) / p->mass[a];
+    }
+    s->rcut = rcmax;
+    s->rl = rcmax + skin;
+    s->rl2 = s->rl * s->rl;
+    const double half_skin = 0.5 * skin;
+    s->lim2 = half_skin * half_skin;
+    // cell grid: per dimension the largest multiple of 4 cells at least r_list wide
+    Geometry& g = s->g;
+    for (int d = 0; d < 3; ++d) {
+        if (!(box[d] > 0.0) || !std::isfinite(box[d])) return bail(MD_ERR_ARG);
+        s->box[d] = box[d];
+        int nc = (int)std::floor(box[d] / (s->rl * (1.0 + 1e-12)));
+        nc -= nc % 4;
+        if (nc < 4) {
+            fail(s, MD_ERR_BOX_TOO_SMALL, "box side %g < 4 r_list", box[d]);
+            return bail(MD_ERR_BOX_TOO_SMALL);
+        }
+        if (nc > 1024) nc = 1024;
+        g.L[d] = box[d];
+        g.nc[d] = nc;
+        g.w[d] = box[d] / nc;
+        g.inv_w[d] = nc / box[d];
+        g.nbh[d] = nc / 4;
+        for (int t = 0; t < 4; ++t) s->to.off[d][t] = (float)((t - 1.5) * g.w[d]);
+    }
+    g.nblock = (g.nc[0] / 2) * (g.nc[1] / 2) * (g.nc[2] / 2);
+    g.ncell = g.nblock * 8;
+    // initial capacities from the mean density (regrown on overflow)
+    const double vol = box[0] * box[1] * box[2];
+    const double rho = (double)n / vol;
+    const double tile_vol = 64.0 * g.w[0] * g.w[1] * g.w[2];
+    s->tile_cap = round_up((int)std::ceil(rho * tile_vol * 1.5) + 64, 64);
+    s->tile_cap = std::min(s->tile_cap, 4096);
+    const double sphere = 4.0 / 3.0 * M_PI * s->rl * s->rl * s->rl * rho;
+    int lc = (int)std::ceil(sphere * 1.4) + 16;
+    if (p->list_kind == MD_LIST_HALF_COLOUR8) lc = (int)std::ceil(sphere * 0.7) + 16;
+    lc = round_up(std::min(lc, 512), 8);
+
+    // workspace
+    for (int k = 0; k < 2; ++k) {
+        DevState& d = s->st[k];
+        d.n = n;
+        d.np = s->np;
+        if ((rc = dalloc(s, &d.x, n)) || (rc = dalloc(s, &d.y, n)) || (rc = dalloc(s, &d.z, n)) ||
+            (rc = dalloc(s, &d.vx, n)) || (rc = dalloc(s, &d.vy, n)) || (rc = dalloc(s, &d.vz, n)) ||
+            (rc = dalloc(s, &d.rx, n)) || (rc = dalloc(s, &d.ry, n)) || (rc = dalloc(s, &d.rz, n)) ||
+            (rc = dalloc(s, &d.ix, n)) || (rc = dalloc(s, &d.iy, n)) || (rc = dalloc(s, &d.iz, n)) ||
+            (rc = dalloc(s, &d.species, n)) || (rc = dalloc(s, &d.orig, n)) || (rc = dalloc(s, &d.cell_of, n)) ||
+            (rc = dalloc(s, &d.xr, n)) || (rc = dalloc(s, &d.xr_ref, n)))
+            return bail(rc);
+    }
+    DevState& d0 = s->st[0];
+    if ((rc = dalloc(s, &d0.cell_start, (size_t)g.ncell + 1)) || (rc = dalloc(s, &d0.nl_cnt, n)) ||
+        (rc = dalloc(s, &d0.err, 1)) || (rc = dalloc(s, &d0.rebuild_flag, 1)) || (rc = dalloc(s, &d0.stats, 8)))
+        return bail(rc);
+    if (p->precision == MD_MIXED) {
+        if ((rc = dalloc(s, &d0.fq, 3 * (size_t)n)) || (rc = dalloc(s, &d0.pe_atom_f, n)) ||
+            (rc = dalloc(s, &d0.vir_atom_f, 6 * (size_t)n)))
+            return bail(rc);
+    } else {
+        if ((rc = dalloc(s, &d0.f, 3 * (size_t)n)) || (rc = dalloc(s, &d0.pe_atom_d, n)) ||
+            (rc = dalloc(s, &d0.vir_atom_d, 6 * (size_t)n)))
+            return bail(rc);
+    }
+    DevState& d1 = s->st[1];
+    d1.cell_start = d0.cell_start;
+    d1.nl_cnt = d0.nl_cnt;
+    d1.err = d0.err;
+    d1.rebuild_flag = d0.rebuild_flag;
+    d1.stats = d0.stats;
+    d1.fq = d0.fq;
+    d1.f = d0.f;
+    d1.pe_atom_f = d0.pe_atom_f;
+    d1.vir_atom_f = d0.vir_atom_f;
+    d1.pe_atom_d = d0.pe_atom_d;
+    d1.vir_atom_d = d0.vir_atom_d;
+    if ((rc = alloc_lists(s, lc))) return bail(rc);
+    if ((rc = dalloc(s, &s->atom_cell, n)) || (rc = dalloc(s, &s->cell_count, g.ncell)) ||
+        (rc = dalloc(s, &s->cursor, g.ncell)) || (rc = dalloc(s, &s->slot_key, n)) ||
+        (rc = dalloc(s, &s->slot_src, n)) || (rc = dalloc(s, &s->sorted_src, n)) ||
+        (rc = dalloc(s, &s->scan_scratch, scan_scratch_ints(g.ncell))))
+        return bail(rc);
+    s->nparts = 592;
+    if ((rc = dalloc(s, &s->partials, 8 * (size_t)s->nparts)) || (rc = dalloc(s, &s->out8, 8))) return bail(rc);
+    if (cudaMallocHost(&s->h_flags, 16 * sizeof(uint32_t)) != cudaSuccess) return bail(MD_ERR_CUDA);
+    if (cudaMemsetAsync(d0.err, 0, sizeof(uint32_t), s->stream) != cudaSuccess ||
+        cudaMemsetAsync(d0.rebuild_flag, 0, sizeof(int32_t), s->stream) != cudaSuccess ||
+        cudaStreamSynchronize(s->stream) != cudaSuccess)
+        return bail(MD_ERR_CUDA);
+    *out = s;
+    return MD_OK;
+}
+
+int md_set_state(md_system* s, const double* pos, const double* vel, const int32_t* species, int device_ptrs) {
+    if (!s) return MD_ERR_ARG;
+    if (!pos) return fail(s, MD_ERR_ARG, "pos is NULL");
+    DeviceGuard dg(s->device);
+    const size_t n = (size_t)s->n;
+    const double *dpos = pos, *dvel = vel;
+    const int32_t* dsp = species;
+    double* tmp = nullptr;
+    int32_t* tsp = nullptr;
+    if (!device_ptrs && n > 0) {
+        CK(cudaMallocAsync(&tmp, sizeof(double) * 6 * n, s->stream));
+        CK(cudaMemcpyAsync(tmp, pos, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, s->stream));
+        dpos = tmp;
+        if (vel) {
+            CK(cudaMemcpyAsync(tmp + 3 * n, vel, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, s->stream));
+            dvel = tmp + 3 * n;
+        }
+        if (species) {
+            CK(cudaMallocAsync(&tsp, sizeof(int32_t) * n, s->stream));
+            CK(cudaMemcpyAsync(tsp, species, sizeof(int32_t) * n, cudaMemcpyHostToDevice, s->stream));
+            dsp = tsp;
+        }
+    }
+    s->cur = 0;
+    CK(cudaMemsetAsync(s->st[0].err, 0, sizeof(uint32_t), s->stream));
+    launch_set_state(s->st[0], dpos, dvel, dsp, s->pt.nsp, s->stream);
+    CKL();
+    if (tmp) CK(cudaFreeAsync(tmp, s->stream));
+    if (tsp) CK(cudaFreeAsync(tsp, s->stream));
+    int rc = sync_flags(s);
+    if (rc) return rc;
+    s->has_state = false;
+    s->lists_valid = false;
+    s->forces_valid = false;
+    if (s->h_flags[0] & 0x80000000u) return fail(s, MD_ERR_ARG, "species id out of range");
+    s->has_state = true;
+    return MD_OK;
+}
+
+int md_bin_cells(md_system* s) {
+    if (!s) return MD_ERR_ARG;
+    if (!s->has_state) return fail(s, MD_ERR_STATE, "no state");
+    DeviceGuard dg(s->device);
+    CK(cudaMemsetAsync(s->st[0].err, 0, sizeof(uint32_t), s->stream));
+    int rc = do_bin(s);
+    if (rc) return rc;
+    rc = sync_flags(s);
+    if (rc) return rc;
+    return check_err(s, ~0u);
+}
+
+int md_build_neighbors(md_system* s) {
+    if (!s) return MD_ERR_ARG;
+    if (!s->has_state) return fail(s, MD_ERR_STATE, "no state");
+    DeviceGuard dg(s->device);
+    return do_build(s);
+}
+
+int md_forces(md_system* s, double* f_out, int device_ptrs) {
+    if (!s) return MD_ERR_ARG;
+    DeviceGuard dg(s->device);
+    int rc = ensure_lists(s);
+    if (rc) return rc;
+    rc = do_forces(s, 0);
+    if (rc) return rc;
+    if (f_out && s->n > 0) {
+        const size_t n = (size_t)s->n;
+        if (device_ptrs) {
+            launch_forces_out(s->st[s->cur], mixed(s), f_out, s->stream);
+            CKL();
+        } else {
+            double* tmp = nullptr;
+            CK(cudaMallocAsync(&tmp, sizeof(double) * 3 * n, s->stream));
+            launch_forces_out(s->st[s->cur], mixed(s), tmp, s->stream);
+            CKL();
+            CK(cudaMemcpyAsync(f_out, tmp, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, s->stream));
+            CK(cudaFreeAsync(tmp, s->stream));
+            CK(cudaStreamSynchronize(s->stream));
+        }
+    }
+    rc = sync_flags(s);
+    if (rc) return rc;
+    return check_err(s, ERR_NONFINITE | ERR_TILE_OVERFLOW);
+}
+
+int md_step(md_system* s, int32_t n_steps) {
+    if (!s) return MD_ERR_ARG;
+    if (n_steps < 0) return fail(s, MD_ERR_ARG, "n_steps < 0");
+    if (n_steps == 0 || s->n == 0) {
+        if (s) s->n_steps += n_steps;
+        return MD_OK;
+    }
+    DeviceGuard dg(s->device);
+    int rc = ensure_lists(s);
+    if (rc) return rc;
+    if (!s->forces_valid && (rc = do_forces(s, 0))) return rc;
+    const int mx = mixed(s);
+    for (int k = 0; k < n_steps; ++k) {
+        CK(cudaMemsetAsync(s->st[0].rebuild_flag, 0, sizeof(int32_t), s->stream));
+        launch_integrate(s->st[s->cur], s->g, s->pt, k == 0 ? INT_KICK_DRIFT : INT_KICK_KICK_DRIFT, mx, s->dt,
+                         s->lim2, s->stream);
+        CKL();
+        s->launches += 1;
+        bool rebuild;
+        if (s->rebuild == MD_REBUILD_EVERY_K) {
+            rebuild = ((s->n_steps + k + 1) % s->rebuild_k) == 0;
+            if (!rebuild) {
+                if ((rc = sync_flags(s))) return rc;
+                if (s->h_flags[1]) return fail(s, MD_ERR_SKIN_VIOLATION, "an atom moved more than skin/2");
+            }
+        } else {
+            if ((rc = sync_flags(s))) return rc;
+            rebuild = s->h_flags[1] != 0;
+        }
+        if (rebuild && (rc = do_build(s))) return rc;
+        if ((rc = do_forces(s, 0))) return rc;
+    }
+    launch_integrate(s->st[s->cur], s->g, s->pt, INT_KICK, mx, s->dt, s->lim2, s->stream);
+    CKL();
+    s->launches += 1;
+    s->n_steps += n_steps;
+    rc = sync_flags(s);
+    if (rc) return rc;
+    return check_err(s, ERR_NONFINITE | ERR_TILE_OVERFLOW | ERR_ESCAPE);
+}
+
+int md_energy_virial(md_system* s, double* pe, double* ke, double virial[6]) {
+    if (!s) return MD_ERR_ARG;
+    DeviceGuard dg(s->device);
+    if (!s->has_state) return fail(s, MD_ERR_STATE, "no state");
+    double h[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    if (s->n > 0) {
+        int rc = ensure_lists(s);
+        if (rc) return rc;
+        if ((rc = do_forces(s, 1))) return rc;
+        launch_reduce_energy(s->st[s->cur], s->pt, mixed(s), s->partials, s->nparts, s->out8, s->stream);
+        CKL();
+        s->launches += 2;
+        CK(cudaMemcpyAsync(h, s->out8, sizeof(h), cudaMemcpyDeviceToHost, s->stream));
+        if ((rc = sync_flags(s))) return rc;
+        if ((rc = check_err(s, ERR_NONFINITE | ERR_TILE_OVERFLOW))) return rc;
+    }
+    if (pe) *pe = h[0];
+    if (ke) *ke = h[1];
+    if (virial)
+        for (int c = 0; c < 6; ++c) virial[c] = h[2 + c];
+    return MD_OK;
+}
+
+int md_get_state(md_system* s, double* pos, double* vel, int32_t* image, int device_ptrs) {
+    if (!s) return MD_ERR_ARG;
+    if (!s->has_state) return fail(s, MD_ERR_STATE, "no state");
+    DeviceGuard dg(s->device);
+    const size_t n = (size_t)s->n;
+    if (n == 0) return MD_OK;
+    if (device_ptrs) {
+        launch_get_state(s->st[s->cur], pos, vel, image, s->stream);
+        CKL();
+        return MD_OK;
+    }
+    double* tmp = nullptr;
+    int32_t* timg = nullptr;
+    CK(cudaMallocAsync(&tmp, sizeof(double) * 6 * n, s->stream));
+    CK(cudaMallocAsync(&timg, sizeof(int32_t) * 3 * n, s->stream));
+    launch_get_state(s->st[s->cur], tmp, tmp + 3 * n, timg, s->stream);
+    CKL();
+    if (pos) CK(cudaMemcpyAsync(pos, tmp, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, s->stream));
+    if (vel) CK(cudaMemcpyAsync(vel, tmp + 3 * n, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, s->stream));
+    if (image) CK(cudaMemcpyAsync(image, timg, sizeof(int32_t) * 3 * n, cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaFreeAsync(tmp, s->stream));
+    CK(cudaFreeAsync(timg, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    return MD_OK;
+}
+
+int md_get_neighbors(md_system* s, int64_t* n_pairs, int32_t* pairs) {
+    if (!s || !n_pairs) return MD_ERR_ARG;
+    DeviceGuard dg(s->device);
+    int rc = ensure_lists(s);
+    if (rc) return rc;
+    const int64_t npairs = half(s) ? s->list_entries : s->list_entries / 2;
+    *n_pairs = npairs;
+    if (!pairs || npairs == 0) return MD_OK;
+    unsigned long long* counter = nullptr;
+    int32_t* dp = nullptr;
+    CK(cudaMallocAsync(&counter, sizeof(unsigned long long), s->stream));
+    CK(cudaMallocAsync(&dp, sizeof(int32_t) * 2 * (size_t)npairs, s->stream));
+    CK(cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s->stream));
+    launch_pairs_out(s->st[s->cur], s->g, half(s), counter, dp, npairs, s->stream);
+    CKL();
+    unsigned long long got = 0;
+    CK(cudaMemcpyAsync(&got, counter, sizeof(got), cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaMemcpyAsync(pairs, dp, sizeof(int32_t) * 2 * (size_t)npairs, cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaFreeAsync(counter, s->stream));
+    CK(cudaFreeAsync(dp, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    if ((int64_t)got != npairs) return fail(s, MD_ERR_STATE, "pair count mismatch (%llu vs %lld)", got, (long long)npairs);
+    std::vector<int64_t> keys((size_t)npairs);
+    for (int64_t k = 0; k < npairs; ++k) keys[k] = ((int64_t)pairs[2 * k] << 32) | (uint32_t)pairs[2 * k + 1];
+    std::sort(keys.begin(), keys.end());
+    for (int64_t k = 0; k < npairs; ++k) {
+        pairs[2 * k] = (int32_t)(keys[k] >> 32);
+        pairs[2 * k + 1] = (int32_t)(keys[k] & 0xffffffff);
+    }
+    return MD_OK;
+}
+
+int md_get_cells(md_system* s, int32_t* cell_of_atom) {
+    if (!s || !cell_of_atom) return MD_ERR_ARG;
+    if (!s->has_state) return fail(s, MD_ERR_STATE, "no state");
+    DeviceGuard dg(s->device);
+    if (s->n == 0) return MD_OK;
+    int32_t* tmp = nullptr;
+    CK(cudaMallocAsync(&tmp, sizeof(int32_t) * (size_t)s->n, s->stream));
+    launch_cells_out(s->st[s->cur], s->g, tmp, s->stream);
+    CKL();
+    CK(cudaMemcpyAsync(cell_of_atom, tmp, sizeof(int32_t) * (size_t)s->n, cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaFreeAsync(tmp, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    return MD_OK;
+}
+
+int md_get_info(md_system* s, md_info* out) {
+    if (!s || !out) return MD_ERR_ARG;
+    out->n = s->n;
+    for (int d = 0; d < 3; ++d) {
+        out->ncell[d] = s->g.nc[d];
+        out->cell_width[d] = s->g.w[d];
+    }
+    out->list_cap = s->list_cap;
+    out->tile_cap = s->tile_cap;
+    out->n_builds = s->n_builds;
+    out->n_steps = s->n_steps;
+    out->list_entries = s->list_entries;
+    out->max_list = s->max_list;
+    out->max_tile = s->max_tile;
+    out->kernel_launches = s->launches;
+    out->force_evals = s->force_evals;
+    out->force_ms = s->force_ms;
+    out->timed_force_evals = s->timed_force;
+    out->build_ms = s->build_ms;
+    out->timed_builds = s->timed_build;
+    return MD_OK;
+}
+
+int md_set_timing(md_system* s, int enable) {
+    if (!s) return MD_ERR_ARG;
+    DeviceGuard dg(s->device);
+    CK(cudaStreamSynchronize(s->stream));
+    drain_events(s);
+    s->timing = enable != 0;
+    s->force_ms = s->build_ms = 0.0;
+    s->timed_force = s->timed_build = 0;
+    return MD_OK;
+}
+
+int md_last_error(md_system* s, char* buf, int64_t len) {
+    if (!s || !buf || len <= 0) return MD_ERR_ARG;
+    std::snprintf(buf, (size_t)len, "%s", s->msg);
+    return MD_OK;
+}
+
+void md_destroy(md_system* s) {
+    if (!s) return;
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (prev != s->device) cudaSetDevice(s->device);
+    if (s->stream) cudaStreamSynchronize(s->stream);
+    else cudaDeviceSynchronize();
+    for (void* p : s->allocs) cudaFree(p);
+    s->allocs.clear();
+    drain_events(s);
+    for (auto& e : s->ev_free) {
+        cudaEventDestroy(e.first);
+        cudaEventDestroy(e.second);
+    }
+    if (s->h_flags) cudaFreeHost(s->h_flags);
+    if (prev >= 0 && prev != s->device) cudaSetDevice(prev);
+    delete s;
+}
+
+}  // extern "C"

@@ -1,0 +1,77 @@
+// debug.cu - host-only introspection of the cell numbering (include/mdgb_debug.h).
+#include "mdgb.h"
+#include "mdgb_debug.h"
+#include "tile.cuh"
+
+#include <cmath>
+
+using namespace mdgb;
+
+namespace {
+
+bool make_geometry(const int32_t nc[3], Geometry& g) {
+    if (!nc) return false;
+    for (int d = 0; d < 3; ++d) {
+        if (nc[d] < 4 || nc[d] % 4 != 0) return false;
+        g.nc[d] = nc[d];
+        g.nbh[d] = nc[d] / 4;
+    }
+    g.nblock = (nc[0] / 2) * (nc[1] / 2) * (nc[2] / 2);
+    g.ncell = g.nblock * 8;
+    return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mdgb_grid_shape(const double box[3], double r_list, int32_t nc_out[3]) {
+    if (!box || !nc_out || !(r_list > 0.0)) return MD_ERR_ARG;
+    for (int d = 0; d < 3; ++d) {
+        int nc = (int)std::floor(box[d] / (r_list * (1.0 + 1e-12)));
+        nc -= nc % 4;
+        if (nc < 4) return MD_ERR_BOX_TOO_SMALL;
+        nc_out[d] = nc > 1024 ? 1024 : nc;
+    }
+    return MD_OK;
+}
+
+int mdgb_num_blocks(const int32_t nc[3], int32_t* nblock_out) {
+    Geometry g{};
+    if (!nblock_out || !make_geometry(nc, g)) return MD_ERR_ARG;
+    *nblock_out = g.nblock;
+    return MD_OK;
+}
+
+int mdgb_block_colour(const int32_t nc[3], int32_t block, int32_t* colour_out) {
+    Geometry g{};
+    if (!colour_out || !make_geometry(nc, g) || block < 0 || block >= g.nblock) return MD_ERR_ARG;
+    int bx, by, bz;
+    block_coords(g, block, bx, by, bz);
+    *colour_out = (bx & 1) | ((by & 1) << 1) | ((bz & 1) << 2);
+    return MD_OK;
+}
+
+int mdgb_tile_cells(const int32_t nc[3], int32_t block, int32_t cells_out[64]) {
+    Geometry g{};
+    if (!cells_out || !make_geometry(nc, g) || block < 0 || block >= g.nblock) return MD_ERR_ARG;
+    constexpr TileTables tt = make_tile_tables();
+    int bx, by, bz;
+    block_coords(g, block, bx, by, bz);
+    for (int t = 0; t < 64; ++t) {
+        const int c = tt.coord_of_idx[t];
+        int cx = 2 * bx - 1 + (c & 3), cy = 2 * by - 1 + ((c >> 2) & 3), cz = 2 * bz - 1 + (c >> 4);
+        cx = (cx + g.nc[0]) % g.nc[0];
+        cy = (cy + g.nc[1]) % g.nc[1];
+        cz = (cz + g.nc[2]) % g.nc[2];
+        // round trip through the kernels' cell id to check the numbering is a bijection
+        int id = cell_id_of(g, cx, cy, cz);
+        int ax, ay, az;
+        cell_coords(g, id, ax, ay, az);
+        if (ax != cx || ay != cy || az != cz) return MD_ERR_ARG;
+        cells_out[t] = cx + g.nc[0] * (cy + g.nc[1] * cz);
+    }
+    return MD_OK;
+}
+
+}  // extern "C"

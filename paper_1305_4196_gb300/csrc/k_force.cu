@@ -1,0 +1,589 @@
+// k_force.cu - Lennard-Jones forces by cell tasks (Sec. II.A, step 2).
+//
+// One CTA is the task of one 2x2x2-cell block (Sec. II.D.2 blocking): it
+// stages the block's 4x4x4-cell tile in shared memory and evaluates the
+// neighbour lists of the block's own atoms against it.
+//
+//  * Full lists: one thread per atom i, accumulating only F_i.  No thread
+//    ever writes an atom it does not own, so the paper's requirement that no
+//    particle is updated by two workers at once (Sec. II.A) holds with no
+//    synchronisation at all.
+//  * Half lists (Newton's third law, Sec. II.D.3): each pair once; the
+//    reaction -f_ij goes to the tile copy of j in shared memory, and the tile
+//    is added back to global memory at the end.  Blocks of one colour class
+//    have disjoint tiles, so one launch per colour runs only non-overlapping
+//    tasks - the barrier-separated waves of Sec. II.B, 8 of them.  No global
+//    atomics are used; within a CTA the tile accumulators take shared-memory
+//    integer adds.
+//
+// Mixed precision: pair arithmetic in FP32 on block-frame coordinates; every
+// pair force component q = rint(f * 2^32) is added in Q31.32 fixed point,
+// split exactly into a high part (multiples of 2^21) and a low part, each
+// summed in a 32-bit integer.  Integer sums do not depend on order, so the
+// result is bit-reproducible for any list order, thread mapping or list kind,
+// and f_ji = -f_ij bit for bit makes the total force exactly zero.
+//
+// FP64: the same structure with FP64 tile coordinates and FP64 sums.
+#include "tile.cuh"
+
+namespace mdgb {
+
+constexpr int F_THREADS = 256;
+constexpr float MAGIC = 12582912.0f;   // 1.5 * 2^23: adding it rounds |a| < 2^22 to an integer
+constexpr float TWO21 = 2097152.0f;    // 2^21
+constexpr float FS_SCALE = 2048.0f;    // 2^11: pair force scaled so that rint() yields multiples of 2^-11
+
+// Exact split of a * 2^21 (a = fs2 * d computed exactly inside the FMA) into
+// two integer parts: hi counts units of 2^-11, lo units of 2^-32 (both offset
+// by the bit pattern of MAGIC, which the caller removes once per term).
+struct FixAcc {
+    unsigned hi, lo;  // wrap-around sums; the true sums fit in 32 bits
+};
+
+__device__ __forceinline__ void fix_add(FixAcc& acc, float fs2, float d) {
+    float t1 = __fmaf_rn(fs2, d, MAGIC);
+    float h = __fsub_rn(t1, MAGIC);
+    float r = __fmaf_rn(fs2, d, -h);
+    float t2 = __fmaf_rn(r, TWO21, MAGIC);
+    acc.hi += __float_as_uint(t1);
+    acc.lo += __float_as_uint(t2);
+}
+
+__device__ __forceinline__ void fix_sub(FixAcc& acc, float fs2, float d) {
+    // contribution of -d: exact negation of fix_add's terms
+    float t1 = __fmaf_rn(fs2, -d, MAGIC);
+    float h = __fsub_rn(t1, MAGIC);
+    float r = __fmaf_rn(fs2, -d, -h);
+    float t2 = __fmaf_rn(r, TWO21, MAGIC);
+    acc.hi += __float_as_uint(t1);
+    acc.lo += __float_as_uint(t2);
+}
+
+// slow exact path for |fs2 * d| >= 2^22 (pair force component >= 2048 eps/sigma): add
+// rint(fs2 * d * 2^21) in the same two-part form (FP64 product of two floats is exact).
+__device__ __noinline__ uint2 fix_wide_terms(float fs2, float d, uint32_t* err) {
+    double a = (double)fs2 * (double)d * 2097152.0;
+    if (!(fabs(a) < 9.0e15)) {
+        atomicOr(err, ERR_NONFINITE);
+        a = 0.0;
+    }
+    long long q = __double2ll_rn(a);
+    long long qh = q >> 21;
+    return make_uint2(__float_as_uint(MAGIC) + (unsigned)(int)qh,
+                      __float_as_uint(MAGIC) + (unsigned)(int)(q - qh * 2097152LL));
+}
+
+__device__ __forceinline__ void fix_add_wide(FixAcc& acc, float fs2, float d, uint32_t* err) {
+    const uint2 t = fix_wide_terms(fs2, d, err);
+    acc.hi += t.x;
+    acc.lo += t.y;
+}
+
+__device__ __forceinline__ long long fix_final(const FixAcc& acc, int nterms) {
+    const int hi = (int)(acc.hi - (unsigned)nterms * __float_as_uint(MAGIC));
+    const int lo = (int)(acc.lo - (unsigned)nterms * __float_as_uint(MAGIC));
+    return (long long)hi * 2097152LL + (long long)lo;
+}
+
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// per-pair LJ in FP32; returns fs2 = (|f|/r) * 2^11, masked to 0 outside the cutoff
+template <bool SINGLE>
+__device__ __forceinline__ float lj_fs2(const PairTable& pt, int t, float r2, float& s6_out, bool& inside) {
+    const float sig2 = SINGLE ? pt.sig2_f[0] : pt.sig2_f[t];
+    const float c48 = SINGLE ? pt.c48_f[0] : pt.c48_f[t];
+    const float c24 = SINGLE ? pt.c24_f[0] : pt.c24_f[t];
+    const float rc2 = SINGLE ? pt.rc2_f[0] : pt.rc2_f[t];
+    const float inv = rcp_approx(r2);
+    const float s2 = sig2 * inv;
+    const float s6 = s2 * s2 * s2;
+    inside = r2 < rc2;
+    s6_out = s6;
+    const float fs = (c48 * s6 - c24) * s6 * inv;  // constants carry the 2^11 scale
+    return inside ? fs : 0.0f;
+}
+
+// Neighbour lists come in chunks of 8 tile indices (one 16-byte load per chunk,
+// chunk c of atom i at uint4 index c * np + i); the last chunk is padded with the
+// tile's dummy slot T, which holds a point far outside every cutoff.
+#define MDGB_FOR_EACH_NEIGHBOUR(ROW0, NP, NCH, ...)                                         \
+    {                                                                                        \
+        const uint4* lp_ = (ROW0);                                                           \
+        uint4 cur_ = make_uint4(0u, 0u, 0u, 0u);                                             \
+        if ((NCH) > 0) cur_ = __ldcs(lp_);                                                   \
+        for (int c_ = 0; c_ < (NCH); ++c_) {                                                 \
+            uint4 nxt_ = cur_;                                                               \
+            if (c_ + 1 < (NCH)) nxt_ = __ldcs(lp_ + (size_t)(c_ + 1) * (NP));                \
+            const unsigned w_[4] = {cur_.x, cur_.y, cur_.z, cur_.w};                         \
+            _Pragma("unroll") for (int e_ = 0; e_ < 8; ++e_) {                               \
+                const int u = (int)((w_[e_ >> 1] >> ((e_ & 1) * 16)) & 0xffffu);             \
+                __VA_ARGS__                                                                  \
+            }                                                                                \
+            cur_ = nxt_;                                                                     \
+        }                                                                                    \
+    }
+
+__device__ __forceinline__ void stage_dummy_f32(float4* tile, int T) {
+    if (threadIdx.x == 0) tile[T] = make_float4(1.0e4f, 1.0e4f, 1.0e4f, __int_as_float(0));
+}
+
+// ---------------------------------------------------------------- mixed, full list
+template <bool SINGLE, bool EV>
+__global__ void __launch_bounds__(F_THREADS) k_force_mixed_full(DevState s, Geometry g, PairTable pt,
+                                                                TileOffsets to, int tile_cap, float fs2_max) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ TileMeta m;
+    float4* tile = reinterpret_cast<float4*>(smem);
+    const int b = blockIdx.x;
+    tile_meta(g, s.cell_start, b, m);
+    const int T = m.prefix[64];
+    if (T + 1 > tile_cap) {
+        if (threadIdx.x == 0) atomicOr(s.err, ERR_TILE_OVERFLOW);
+        return;
+    }
+    tile_stage_f32(m, s.xr, to, tile, nullptr);
+    stage_dummy_f32(tile, T);
+    __syncthreads();
+    const int blk0 = m.start[0];
+    const int nown = m.prefix[8];
+    const int64_t n = s.n;
+    const int np = s.np;
+    for (int ui = threadIdx.x; ui < nown; ui += blockDim.x) {
+        const int gi = blk0 + ui;
+        const float4 pi = tile[ui];
+        const int si = __float_as_int(pi.w);
+        const int nch = (s.nl_cnt[gi] + 7) >> 3;
+        FixAcc ax{0u, 0u}, ay{0u, 0u}, az{0u, 0u};
+        float pe = 0.f, w0 = 0.f, w1 = 0.f, w2 = 0.f, w3 = 0.f, w4 = 0.f, w5 = 0.f;
+        MDGB_FOR_EACH_NEIGHBOUR(reinterpret_cast<const uint4*>(s.nl) + gi, np, nch, {
+            const float4 pj = tile[u];
+            const float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
+            const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+            const int t = SINGLE ? 0 : si * pt.nsp + __float_as_int(pj.w);
+            float s6;
+            bool inside;
+            const float fs2 = lj_fs2<SINGLE>(pt, t, r2, s6, inside);
+            if (fabsf(fs2) < fs2_max) {
+                fix_add(ax, fs2, dx);
+                fix_add(ay, fs2, dy);
+                fix_add(az, fs2, dz);
+            } else {
+                fix_add_wide(ax, fs2, dx, s.err);
+                fix_add_wide(ay, fs2, dy, s.err);
+                fix_add_wide(az, fs2, dz, s.err);
+            }
+            if (EV) {
+                const float c4 = SINGLE ? pt.c4_f[0] : pt.c4_f[t];
+                const float u_ = inside ? c4 * s6 * (s6 - 1.0f) : 0.0f;
+                const float fs = fs2 * (1.0f / FS_SCALE);
+                pe += u_;
+                w0 = fmaf(dx, fs * dx, w0);
+                w1 = fmaf(dy, fs * dy, w1);
+                w2 = fmaf(dz, fs * dz, w2);
+                w3 = fmaf(dx, fs * dy, w3);
+                w4 = fmaf(dx, fs * dz, w4);
+                w5 = fmaf(dy, fs * dz, w5);
+            }
+        })
+        const int nterms = nch * 8;
+        s.fq[gi] = fix_final(ax, nterms);
+        s.fq[n + gi] = fix_final(ay, nterms);
+        s.fq[2 * n + gi] = fix_final(az, nterms);
+        if (EV) {
+            // full lists see every pair twice: each atom keeps half of each pair energy / virial
+            s.pe_atom_f[gi] = 0.5f * pe;
+            s.vir_atom_f[gi] = 0.5f * w0;
+            s.vir_atom_f[n + gi] = 0.5f * w1;
+            s.vir_atom_f[2 * n + gi] = 0.5f * w2;
+            s.vir_atom_f[3 * n + gi] = 0.5f * w3;
+            s.vir_atom_f[4 * n + gi] = 0.5f * w4;
+            s.vir_atom_f[5 * n + gi] = 0.5f * w5;
+        }
+    }
+}
+
+// ---------------------------------------------------------------- mixed, half list, one colour
+// Shared memory: tile coordinates, then the tile's fixed-point accumulators
+// (hi and lo parts per component, 32-bit) and their term counts.  Pair energies
+// and virials are booked in full on the listing atom (only totals are reported).
+template <bool SINGLE, bool EV>
+__global__ void __launch_bounds__(F_THREADS) k_force_mixed_half(DevState s, Geometry g, PairTable pt,
+                                                                TileOffsets to, int tile_cap, float fs2_max,
+                                                                int block0) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ TileMeta m;
+    float4* tile = reinterpret_cast<float4*>(smem);
+    unsigned* acc = reinterpret_cast<unsigned*>(tile + tile_cap);  // 6 x tile_cap: hx, lx, hy, ly, hz, lz
+    int* nterm = reinterpret_cast<int*>(acc + 6 * tile_cap);        // tile_cap
+    const int b = block0 + blockIdx.x;
+    tile_meta(g, s.cell_start, b, m);
+    const int T = m.prefix[64];
+    if (T + 1 > tile_cap) {
+        if (threadIdx.x == 0) atomicOr(s.err, ERR_TILE_OVERFLOW);
+        return;
+    }
+    tile_stage_f32(m, s.xr, to, tile, nullptr);
+    stage_dummy_f32(tile, T);
+    for (int u = threadIdx.x; u <= T; u += blockDim.x) {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) acc[c * tile_cap + u] = 0u;
+        nterm[u] = 0;
+    }
+    __syncthreads();
+    const int blk0 = m.start[0];
+    const int nown = m.prefix[8];
+    const int64_t n = s.n;
+    const int np = s.np;
+    for (int ui = threadIdx.x; ui < nown; ui += blockDim.x) {
+        const int gi = blk0 + ui;
+        const float4 pi = tile[ui];
+        const int si = __float_as_int(pi.w);
+        const int nch = (s.nl_cnt[gi] + 7) >> 3;
+        FixAcc ax{0u, 0u}, ay{0u, 0u}, az{0u, 0u};
+        float pe = 0.f, w0 = 0.f, w1 = 0.f, w2 = 0.f, w3 = 0.f, w4 = 0.f, w5 = 0.f;
+        MDGB_FOR_EACH_NEIGHBOUR(reinterpret_cast<const uint4*>(s.nl) + gi, np, nch, {
+            const float4 pj = tile[u];
+            const float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
+            const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+            const int t = SINGLE ? 0 : si * pt.nsp + __float_as_int(pj.w);
+            float s6;
+            bool inside;
+            const float fs2 = lj_fs2<SINGLE>(pt, t, r2, s6, inside);
+            FixAcc bx{0u, 0u}, by{0u, 0u}, bz{0u, 0u};
+            if (fabsf(fs2) < fs2_max) {
+                fix_add(ax, fs2, dx);
+                fix_add(ay, fs2, dy);
+                fix_add(az, fs2, dz);
+                fix_sub(bx, fs2, dx);
+                fix_sub(by, fs2, dy);
+                fix_sub(bz, fs2, dz);
+            } else {
+                fix_add_wide(ax, fs2, dx, s.err);
+                fix_add_wide(ay, fs2, dy, s.err);
+                fix_add_wide(az, fs2, dz, s.err);
+                fix_add_wide(bx, fs2, -dx, s.err);
+                fix_add_wide(by, fs2, -dy, s.err);
+                fix_add_wide(bz, fs2, -dz, s.err);
+            }
+            atomicAdd(&acc[0 * tile_cap + u], bx.hi);
+            atomicAdd(&acc[1 * tile_cap + u], bx.lo);
+            atomicAdd(&acc[2 * tile_cap + u], by.hi);
+            atomicAdd(&acc[3 * tile_cap + u], by.lo);
+            atomicAdd(&acc[4 * tile_cap + u], bz.hi);
+            atomicAdd(&acc[5 * tile_cap + u], bz.lo);
+            atomicAdd(&nterm[u], 1);
+            if (EV) {
+                const float c4 = SINGLE ? pt.c4_f[0] : pt.c4_f[t];
+                const float fs = fs2 * (1.0f / FS_SCALE);
+                pe += inside ? c4 * s6 * (s6 - 1.0f) : 0.0f;
+                w0 = fmaf(dx, fs * dx, w0);
+                w1 = fmaf(dy, fs * dy, w1);
+                w2 = fmaf(dz, fs * dz, w2);
+                w3 = fmaf(dx, fs * dy, w3);
+                w4 = fmaf(dx, fs * dz, w4);
+                w5 = fmaf(dy, fs * dz, w5);
+            }
+        })
+        // own atom's part goes through the same tile accumulator
+        atomicAdd(&acc[0 * tile_cap + ui], ax.hi);
+        atomicAdd(&acc[1 * tile_cap + ui], ax.lo);
+        atomicAdd(&acc[2 * tile_cap + ui], ay.hi);
+        atomicAdd(&acc[3 * tile_cap + ui], ay.lo);
+        atomicAdd(&acc[4 * tile_cap + ui], az.hi);
+        atomicAdd(&acc[5 * tile_cap + ui], az.lo);
+        atomicAdd(&nterm[ui], nch * 8);
+        if (EV) {
+            s.pe_atom_f[gi] = pe;
+            s.vir_atom_f[gi] = w0;
+            s.vir_atom_f[n + gi] = w1;
+            s.vir_atom_f[2 * n + gi] = w2;
+            s.vir_atom_f[3 * n + gi] = w3;
+            s.vir_atom_f[4 * n + gi] = w4;
+            s.vir_atom_f[5 * n + gi] = w5;
+        }
+    }
+    __syncthreads();
+    // add the tile back: this CTA is the only one of its colour touching these atoms
+    for (int u = threadIdx.x; u < T; u += blockDim.x) {
+        const int nt = nterm[u];
+        if (nt == 0) continue;
+        const int slot = tile_slot_of(m, u);
+        const int gj = m.start[slot] + (u - m.prefix[slot]);
+        FixAcc fx{acc[0 * tile_cap + u], acc[1 * tile_cap + u]};
+        FixAcc fy{acc[2 * tile_cap + u], acc[3 * tile_cap + u]};
+        FixAcc fz{acc[4 * tile_cap + u], acc[5 * tile_cap + u]};
+        s.fq[gj] += fix_final(fx, nt);
+        s.fq[n + gj] += fix_final(fy, nt);
+        s.fq[2 * n + gj] += fix_final(fz, nt);
+    }
+}
+
+// ---------------------------------------------------------------- FP64
+__device__ __forceinline__ void tile_stage_f64(const DevState& s, const Geometry& g, const TileMeta& m, int b,
+                                               double* __restrict__ tx_, double* __restrict__ ty_,
+                                               double* __restrict__ tz_, int* __restrict__ tsp) {
+    int bx, by, bz;
+    block_coords(g, b, bx, by, bz);
+    const int T = m.prefix[64];
+    for (int u = threadIdx.x; u < T; u += blockDim.x) {
+        const int slot = tile_slot_of(m, u);
+        const int c = c_tiles.coord_of_idx[slot];
+        const int j = m.start[slot] + (u - m.prefix[slot]);
+        const int t3[3] = {c & 3, (c >> 2) & 3, c >> 4};
+        const int b3[3] = {bx, by, bz};
+        const double* X[3] = {s.x, s.y, s.z};
+        double* out[3] = {tx_, ty_, tz_};
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const int raw = 2 * b3[d] - 1 + t3[d];
+            const double shift = raw < 0 ? -g.L[d] : (raw >= g.nc[d] ? g.L[d] : 0.0);
+            const double centre = (2.0 * b3[d] + 1.0) * g.w[d];
+            out[d][u] = (X[d][j] + shift) - centre;
+        }
+        tsp[u] = s.species[j];
+    }
+    if (threadIdx.x == 0) {
+        tx_[T] = ty_[T] = tz_[T] = 1.0e4;
+        tsp[T] = 0;
+    }
+}
+
+template <bool EV>
+__global__ void __launch_bounds__(F_THREADS) k_force_fp64_full(DevState s, Geometry g, PairTable pt, int tile_cap) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ TileMeta m;
+    double* tx = reinterpret_cast<double*>(smem);
+    double* ty = tx + tile_cap;
+    double* tz = ty + tile_cap;
+    int* tsp = reinterpret_cast<int*>(tz + tile_cap);
+    const int b = blockIdx.x;
+    tile_meta(g, s.cell_start, b, m);
+    const int T = m.prefix[64];
+    if (T + 1 > tile_cap) {
+        if (threadIdx.x == 0) atomicOr(s.err, ERR_TILE_OVERFLOW);
+        return;
+    }
+    tile_stage_f64(s, g, m, b, tx, ty, tz, tsp);
+    __syncthreads();
+    const int blk0 = m.start[0];
+    const int nown = m.prefix[8];
+    const int64_t n = s.n;
+    const int np = s.np;
+    for (int ui = threadIdx.x; ui < nown; ui += blockDim.x) {
+        const int gi = blk0 + ui;
+        const double xi = tx[ui], yi = ty[ui], zi = tz[ui];
+        const int si = tsp[ui];
+        const int nch = (s.nl_cnt[gi] + 7) >> 3;
+        double fx = 0, fy = 0, fz = 0, pe = 0, w0 = 0, w1 = 0, w2 = 0, w3 = 0, w4 = 0, w5 = 0;
+        MDGB_FOR_EACH_NEIGHBOUR(reinterpret_cast<const uint4*>(s.nl) + gi, np, nch, {
+            const double dx = xi - tx[u], dy = yi - ty[u], dz = zi - tz[u];
+            const double r2 = dx * dx + dy * dy + dz * dz;
+            const int t = si * pt.nsp + tsp[u];
+            if (r2 < pt.rc2_d[t]) {
+                const double sr2 = pt.sig2_d[t] / r2;
+                const double s6 = sr2 * sr2 * sr2;
+                const double e = pt.eps_d[t];
+                const double fr = 24.0 * e * (2.0 * s6 * s6 - s6) / r2;
+                fx += fr * dx;
+                fy += fr * dy;
+                fz += fr * dz;
+                if (EV) {
+                    pe += 4.0 * e * (s6 * s6 - s6);
+                    w0 += dx * (fr * dx);
+                    w1 += dy * (fr * dy);
+                    w2 += dz * (fr * dz);
+                    w3 += dx * (fr * dy);
+                    w4 += dx * (fr * dz);
+                    w5 += dy * (fr * dz);
+                }
+            }
+        })
+        s.f[gi] = fx;
+        s.f[n + gi] = fy;
+        s.f[2 * n + gi] = fz;
+        if (EV) {
+            s.pe_atom_d[gi] = 0.5 * pe;
+            s.vir_atom_d[gi] = 0.5 * w0;
+            s.vir_atom_d[n + gi] = 0.5 * w1;
+            s.vir_atom_d[2 * n + gi] = 0.5 * w2;
+            s.vir_atom_d[3 * n + gi] = 0.5 * w3;
+            s.vir_atom_d[4 * n + gi] = 0.5 * w4;
+            s.vir_atom_d[5 * n + gi] = 0.5 * w5;
+        }
+    }
+}
+
+// FP64 half list, one colour: reactions through FP64 shared-memory accumulators.
+template <bool EV>
+__global__ void __launch_bounds__(F_THREADS) k_force_fp64_half(DevState s, Geometry g, PairTable pt, int tile_cap,
+                                                               int block0) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ TileMeta m;
+    double* tx = reinterpret_cast<double*>(smem);
+    double* ty = tx + tile_cap;
+    double* tz = ty + tile_cap;
+    double* acc = tz + tile_cap;  // 3 x tile_cap
+    int* tsp = reinterpret_cast<int*>(acc + 3 * tile_cap);
+    const int b = block0 + blockIdx.x;
+    tile_meta(g, s.cell_start, b, m);
+    const int T = m.prefix[64];
+    if (T + 1 > tile_cap) {
+        if (threadIdx.x == 0) atomicOr(s.err, ERR_TILE_OVERFLOW);
+        return;
+    }
+    tile_stage_f64(s, g, m, b, tx, ty, tz, tsp);
+    for (int u = threadIdx.x; u <= T; u += blockDim.x) {
+        acc[u] = 0;
+        acc[tile_cap + u] = 0;
+        acc[2 * tile_cap + u] = 0;
+    }
+    __syncthreads();
+    const int blk0 = m.start[0];
+    const int nown = m.prefix[8];
+    const int64_t n = s.n;
+    const int np = s.np;
+    for (int ui = threadIdx.x; ui < nown; ui += blockDim.x) {
+        const int gi = blk0 + ui;
+        const double xi = tx[ui], yi = ty[ui], zi = tz[ui];
+        const int si = tsp[ui];
+        const int nch = (s.nl_cnt[gi] + 7) >> 3;
+        double fx = 0, fy = 0, fz = 0, pe = 0, w0 = 0, w1 = 0, w2 = 0, w3 = 0, w4 = 0, w5 = 0;
+        MDGB_FOR_EACH_NEIGHBOUR(reinterpret_cast<const uint4*>(s.nl) + gi, np, nch, {
+            const double dx = xi - tx[u], dy = yi - ty[u], dz = zi - tz[u];
+            const double r2 = dx * dx + dy * dy + dz * dz;
+            const int t = si * pt.nsp + tsp[u];
+            if (r2 < pt.rc2_d[t]) {
+                const double sr2 = pt.sig2_d[t] / r2;
+                const double s6 = sr2 * sr2 * sr2;
+                const double e = pt.eps_d[t];
+                const double fr = 24.0 * e * (2.0 * s6 * s6 - s6) / r2;
+                fx += fr * dx;
+                fy += fr * dy;
+                fz += fr * dz;
+                atomicAdd(&acc[u], -fr * dx);
+                atomicAdd(&acc[tile_cap + u], -fr * dy);
+                atomicAdd(&acc[2 * tile_cap + u], -fr * dz);
+                if (EV) {
+                    pe += 4.0 * e * (s6 * s6 - s6);
+                    w0 += dx * (fr * dx);
+                    w1 += dy * (fr * dy);
+                    w2 += dz * (fr * dz);
+                    w3 += dx * (fr * dy);
+                    w4 += dx * (fr * dz);
+                    w5 += dy * (fr * dz);
+                }
+            }
+        })
+        atomicAdd(&acc[ui], fx);
+        atomicAdd(&acc[tile_cap + ui], fy);
+        atomicAdd(&acc[2 * tile_cap + ui], fz);
+        if (EV) {
+            s.pe_atom_d[gi] = pe;
+            s.vir_atom_d[gi] = w0;
+            s.vir_atom_d[n + gi] = w1;
+            s.vir_atom_d[2 * n + gi] = w2;
+            s.vir_atom_d[3 * n + gi] = w3;
+            s.vir_atom_d[4 * n + gi] = w4;
+            s.vir_atom_d[5 * n + gi] = w5;
+        }
+    }
+    __syncthreads();
+    for (int u = threadIdx.x; u < T; u += blockDim.x) {
+        const int slot = tile_slot_of(m, u);
+        const int gj = m.start[slot] + (u - m.prefix[slot]);
+        s.f[gj] += acc[u];
+        s.f[n + gj] += acc[tile_cap + u];
+        s.f[2 * n + gj] += acc[2 * tile_cap + u];
+    }
+}
+
+// ---------------------------------------------------------------- launchers
+size_t force_smem_bytes(int mixed, int half, int with_energy, int tile_cap) {
+    (void)with_energy;
+    if (mixed) {
+        size_t b = (size_t)tile_cap * sizeof(float4);
+        if (half) b += (size_t)tile_cap * 7 * sizeof(int);
+        return b;
+    }
+    size_t b = (size_t)tile_cap * (3 * sizeof(double) + sizeof(int));
+    if (half) b += (size_t)tile_cap * 3 * sizeof(double);
+    return b;
+}
+
+template <typename K>
+static void set_smem(K kernel, size_t smem) {
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+void launch_forces_mixed(const DevState& s, const Geometry& g, const PairTable& pt, const TileOffsets& to,
+                         int tile_cap, int half, int with_energy, cudaStream_t st) {
+    if (s.n == 0) return;
+    const size_t smem = force_smem_bytes(1, half, with_energy, tile_cap);
+    float rcmax2 = 0.f;
+    for (int t = 0; t < pt.nsp * pt.nsp; ++t) rcmax2 = pt.rc2_f[t] > rcmax2 ? pt.rc2_f[t] : rcmax2;
+    // |fs2 * d| < 2^22 is guaranteed when |fs2| < 2^22 / r_cut
+    const float fs2_max = 4194304.0f / sqrtf(rcmax2) * 0.999f;
+    const bool single = pt.nsp == 1;
+    if (!half) {
+#define MDGB_FULL(SG, EVV)                                                                   \
+    {                                                                                        \
+        auto k = k_force_mixed_full<SG, EVV>;                                                \
+        set_smem(k, smem);                                                                   \
+        k<<<g.nblock, F_THREADS, smem, st>>>(s, g, pt, to, tile_cap, fs2_max);               \
+    }
+        if (single && !with_energy) MDGB_FULL(true, false)
+        else if (single) MDGB_FULL(true, true)
+        else if (!with_energy) MDGB_FULL(false, false)
+        else MDGB_FULL(false, true)
+#undef MDGB_FULL
+        return;
+    }
+    cudaMemsetAsync(s.fq, 0, sizeof(long long) * 3 * (size_t)s.n, st);
+    const int per = g.nblock / 8;
+    for (int col = 0; col < 8; ++col) {
+#define MDGB_HALF(SG, EVV)                                                                   \
+    {                                                                                        \
+        auto k = k_force_mixed_half<SG, EVV>;                                                \
+        set_smem(k, smem);                                                                   \
+        k<<<per, F_THREADS, smem, st>>>(s, g, pt, to, tile_cap, fs2_max, col * per);         \
+    }
+        if (single && !with_energy) MDGB_HALF(true, false)
+        else if (single) MDGB_HALF(true, true)
+        else if (!with_energy) MDGB_HALF(false, false)
+        else MDGB_HALF(false, true)
+#undef MDGB_HALF
+    }
+}
+
+void launch_forces_fp64(const DevState& s, const Geometry& g, const PairTable& pt, int tile_cap, int half,
+                        int with_energy, cudaStream_t st) {
+    if (s.n == 0) return;
+    const size_t smem = force_smem_bytes(0, half, with_energy, tile_cap);
+    if (!half) {
+        if (with_energy) {
+            set_smem(k_force_fp64_full<true>, smem);
+            k_force_fp64_full<true><<<g.nblock, F_THREADS, smem, st>>>(s, g, pt, tile_cap);
+        } else {
+            set_smem(k_force_fp64_full<false>, smem);
+            k_force_fp64_full<false><<<g.nblock, F_THREADS, smem, st>>>(s, g, pt, tile_cap);
+        }
+        return;
+    }
+    cudaMemsetAsync(s.f, 0, sizeof(double) * 3 * (size_t)s.n, st);
+    const int per = g.nblock / 8;
+    for (int col = 0; col < 8; ++col) {
+        if (with_energy) {
+            set_smem(k_force_fp64_half<true>, smem);
+            k_force_fp64_half<true><<<per, F_THREADS, smem, st>>>(s, g, pt, tile_cap, col * per);
+        } else {
+            set_smem(k_force_fp64_half<false>, smem);
+            k_force_fp64_half<false><<<per, F_THREADS, smem, st>>>(s, g, pt, tile_cap, col * per);
+        }
+    }
+}
+
+}  // namespace mdgb

@@ -1,0 +1,159 @@
+// mdgb_internal.cuh - shared definitions of the sm_103a kernels and the C-ABI layer.
+//
+// Cell numbering.  The box is cut into nc[d] cells per dimension (multiples
+// of 4).  Cells are grouped into 2x2x2 blocks (the paper's cell-task blocking,
+// Sec. II.D.2), blocks are grouped into 8 colour classes by the parities of
+// their block coordinates, and cells are numbered block by block, colour class
+// by colour class:
+//     cell id = block id * 8 + (lx + 2 ly + 4 lz)          (l = cell parity in its block)
+//     block id = colour * (nblock / 8) + index within colour
+// so that the atoms of one block (and of one colour class) are contiguous
+// after binning.  Two blocks of the same colour are 4 cells apart in some
+// dimension, so the 4x4x4-cell neighbourhoods ("tiles") of same-colour blocks
+// never overlap: a wave of non-overlapping tasks in the sense of Sec. II.B.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace mdgb {
+
+// device error bits (sticky, OR-ed into a device word, read by the host)
+enum : uint32_t {
+    ERR_LIST_OVERFLOW = 1u,   // a neighbour list exceeded the capacity
+    ERR_TILE_OVERFLOW = 2u,   // a 4x4x4-cell tile exceeded the on-chip capacity
+    ERR_NONFINITE = 4u,       // non-finite pair force or coordinates
+    ERR_ESCAPE = 8u,          // an atom moved more than one box length between builds
+    ERR_SKIN = 16u,           // displacement > skin/2 under the fixed-interval policy
+    ERR_CELL_COUNT = 32u,     // a cell holds more atoms than a list index can address
+};
+
+constexpr int MAX_SPECIES = 4;
+constexpr int MAX_PAIR = MAX_SPECIES * MAX_SPECIES;
+
+struct Geometry {
+    double L[3];       // box sides
+    double w[3];       // cell widths L / nc
+    double inv_w[3];   // nc / L
+    int nc[3];         // cells per dimension (multiple of 4)
+    int nbh[3];        // blocks per dimension within one colour class (= nc / 4)
+    int nblock;        // number of 2x2x2 blocks
+    int ncell;         // number of cells
+};
+
+// LJ pair constants per species pair (FP32 copies for the mixed path, FP64 for the FP64 path)
+struct PairTable {
+    int nsp;
+    float sig2_f[MAX_PAIR], c48_f[MAX_PAIR], c24_f[MAX_PAIR], c4_f[MAX_PAIR], rc2_f[MAX_PAIR];
+    double sig2_d[MAX_PAIR], eps_d[MAX_PAIR], rc2_d[MAX_PAIR];
+    double hdtm[MAX_SPECIES];  // (dt/2) / m per species
+    double mass[MAX_SPECIES];
+};
+
+__host__ __device__ inline int block_id_of(const Geometry& g, int bx, int by, int bz) {
+    int col = (bx & 1) | ((by & 1) << 1) | ((bz & 1) << 2);
+    int within = (bx >> 1) + g.nbh[0] * ((by >> 1) + g.nbh[1] * (bz >> 1));
+    return col * (g.nblock >> 3) + within;
+}
+
+__host__ __device__ inline void block_coords(const Geometry& g, int b, int& bx, int& by, int& bz) {
+    int per = g.nblock >> 3;
+    int col = b / per;
+    int w = b - col * per;
+    int hx = w % g.nbh[0];
+    int t = w / g.nbh[0];
+    int hy = t % g.nbh[1];
+    int hz = t / g.nbh[1];
+    bx = 2 * hx + (col & 1);
+    by = 2 * hy + ((col >> 1) & 1);
+    bz = 2 * hz + ((col >> 2) & 1);
+}
+
+__host__ __device__ inline int cell_id_of(const Geometry& g, int cx, int cy, int cz) {
+    return block_id_of(g, cx >> 1, cy >> 1, cz >> 1) * 8 + ((cx & 1) | ((cy & 1) << 1) | ((cz & 1) << 2));
+}
+
+__host__ __device__ inline void cell_coords(const Geometry& g, int c, int& cx, int& cy, int& cz) {
+    int bx, by, bz;
+    block_coords(g, c >> 3, bx, by, bz);
+    int l = c & 7;
+    cx = 2 * bx + (l & 1);
+    cy = 2 * by + ((l >> 1) & 1);
+    cz = 2 * bz + ((l >> 2) & 1);
+}
+
+// FP32 offsets (t - 3/2) * w of the 4 tile coordinates per dimension (see tile.cuh).
+struct TileOffsets {
+    float off[3][4];
+};
+
+// Per-CTA tile bookkeeping in shared memory.
+struct TileMeta {
+    int prefix[65];  // tile slot -> first tile index (prefix[64] = tile size)
+    int start[64];   // tile slot -> first global (cell-ordered) atom index
+};
+
+// Device state shared by the kernels (all arrays in cell order unless noted).
+struct DevState {
+    int64_t n;
+    int np;                 // row stride of the neighbour-list matrix (n rounded up to 64)
+    double *x, *y, *z;      // positions, unwrapped since the last build
+    double *vx, *vy, *vz;   // velocities
+    double *rx, *ry, *rz;   // reference positions of the last build (FP64 path displacement test)
+    int32_t *ix, *iy, *iz;  // periodic image counters
+    int32_t *species;       // species id
+    int32_t *orig;          // original index of each cell-ordered atom
+    int32_t *cell_of;       // cell id of each atom at the last build
+    float4 *xr;             // FP32 coordinates relative to the centre of the atom's build cell (mixed path)
+    float4 *xr_ref;         // xr at the last build (mixed path displacement test)
+    long long *fq;          // mixed path: forces, 3 x n, Q31.32 fixed point (x block, y block, z block)
+    double *f;              // FP64 path: forces, 3 x n
+    int32_t *cell_start;    // ncell + 1
+    uint16_t *nl;           // neighbour lists, tile-local indices, in chunks of 8: entry k of atom s at
+                            // nl[((k / 8) * np + s) * 8 + k % 8]; the last chunk is padded with the
+                            // tile's dummy slot (a point far outside every cutoff)
+    uint16_t *nl_cnt;       // list length per atom
+    float *pe_atom_f;       // per-atom energy share (mixed, on demand)
+    float *vir_atom_f;      // per-atom virial share, 6 x n (mixed, on demand)
+    double *pe_atom_d;      // FP64 path
+    double *vir_atom_d;     // FP64 path, 6 x n
+    uint32_t *err;          // sticky error bits
+    int32_t *rebuild_flag;  // set when some atom moved more than skin/2
+    int32_t *stats;         // [0] max list length, [1] max tile size, [2..3] sum of list lengths (u64)
+};
+
+// ---- kernel launchers (defined in the .cu files)
+void launch_bin_assign(const DevState& s, const Geometry& g, int32_t* atom_cell, int32_t* cell_count,
+                       cudaStream_t st);
+void launch_scan(const int32_t* in, int32_t* out_exclusive, int n, int32_t* scratch, cudaStream_t st);
+size_t scan_scratch_ints(int n);
+void launch_scatter(const DevState& s, const int32_t* atom_cell, const int32_t* cell_start, int32_t* cursor,
+                    int32_t* slot_key, int32_t* slot_src, cudaStream_t st);
+void launch_cell_sort(const Geometry& g, const int32_t* cell_start, const int32_t* slot_key,
+                      const int32_t* slot_src, int32_t* sorted_src, cudaStream_t st);
+void launch_gather(const DevState& dst, const DevState& src, const Geometry& g, const int32_t* sorted_src,
+                   const int32_t* atom_cell, int mixed, cudaStream_t st);
+void launch_build_lists(const DevState& s, const Geometry& g, const TileOffsets& to, double rl2, int list_cap,
+                        int tile_cap, int half, cudaStream_t st);
+size_t build_lists_smem(int list_cap, int tile_cap);
+void launch_forces_mixed(const DevState& s, const Geometry& g, const PairTable& pt, const TileOffsets& to,
+                         int tile_cap, int half, int with_energy, cudaStream_t st);
+size_t force_smem_bytes(int mixed, int half, int with_energy, int tile_cap);
+void launch_forces_fp64(const DevState& s, const Geometry& g, const PairTable& pt, int tile_cap, int half,
+                        int with_energy, cudaStream_t st);
+void launch_integrate(const DevState& s, const Geometry& g, const PairTable& pt, int mode, int mixed,
+                      double dt, double lim2, cudaStream_t st);
+void launch_reduce_energy(const DevState& s, const PairTable& pt, int mixed, double* partials, int nparts,
+                          double* out8, cudaStream_t st);
+void launch_set_state(const DevState& s, const double* pos, const double* vel, const int32_t* species,
+                      int nsp, cudaStream_t st);
+void launch_get_state(const DevState& s, double* pos, double* vel, int32_t* image, cudaStream_t st);
+void launch_forces_out(const DevState& s, int mixed, double* f_out, cudaStream_t st);
+void launch_cells_out(const DevState& s, const Geometry& g, int32_t* cells, cudaStream_t st);
+void launch_pairs_out(const DevState& s, const Geometry& g, int half, unsigned long long* counter,
+                      int32_t* pairs, long long cap, cudaStream_t st);
+
+// integrate modes
+enum { INT_KICK_DRIFT = 0, INT_KICK_KICK_DRIFT = 1, INT_KICK = 2 };
+
+}  // namespace mdgb

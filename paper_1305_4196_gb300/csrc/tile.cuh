@@ -1,0 +1,103 @@
+// tile.cuh - the on-chip neighbourhood of one 2x2x2-cell block.
+//
+// A cell task of the paper (Sec. II.A) reads the particles of its cell and
+// of the 26 surrounding cells.  Blocking 2x2x2 cells into one task
+// (Sec. II.D.2) widens that neighbourhood to the 4x4x4 cells around the
+// block: the "tile".  One CTA stages its tile in shared memory once and
+// serves every list build / force evaluation of its block from there, so the
+// neighbour lists can hold 16-bit tile-local indices.
+//
+// Tile order: the block's own 8 cells first (in the block's cell order, so
+// the block's atoms keep their cell-sorted order and own atom k has tile
+// index k), then the other 56 cells of the 4x4x4 neighbourhood, x fastest.
+// Coordinates in the tile are FP32, relative to the block centre: each
+// atom's FP32 offset from its own cell centre plus the (t - 3/2) cell-width
+// offset of its tile cell, which is the same for every periodic image.
+#pragma once
+
+#include "mdgb_internal.cuh"
+
+namespace mdgb {
+
+struct TileTables {
+    int8_t idx_of_coord[64];  // tile coordinate (tx + 4 ty + 16 tz) -> tile slot
+    int8_t coord_of_idx[64];  // tile slot -> tile coordinate
+};
+
+__host__ __device__ constexpr TileTables make_tile_tables() {
+    TileTables t{};
+    int k = 8;
+    for (int c = 0; c < 64; ++c) {
+        int x = c & 3, y = (c >> 2) & 3, z = c >> 4;
+        bool own = x >= 1 && x <= 2 && y >= 1 && y <= 2 && z >= 1 && z <= 2;
+        int i = own ? (x - 1) + 2 * (y - 1) + 4 * (z - 1) : k++;
+        t.idx_of_coord[c] = (int8_t)i;
+        t.coord_of_idx[i] = (int8_t)c;
+    }
+    return t;
+}
+
+static __constant__ TileTables c_tiles = make_tile_tables();
+
+// Fill meta for block b (threads 0..63 of the CTA take part; ends with __syncthreads).
+__device__ __forceinline__ void tile_meta(const Geometry& g, const int32_t* __restrict__ cell_start, int b,
+                                          TileMeta& m) {
+    const int t = threadIdx.x;
+    if (t < 64) {
+        int bx, by, bz;
+        block_coords(g, b, bx, by, bz);
+        int c = c_tiles.coord_of_idx[t];
+        int tx = c & 3, ty = (c >> 2) & 3, tz = c >> 4;
+        int cx = 2 * bx - 1 + tx, cy = 2 * by - 1 + ty, cz = 2 * bz - 1 + tz;
+        cx += cx < 0 ? g.nc[0] : (cx >= g.nc[0] ? -g.nc[0] : 0);
+        cy += cy < 0 ? g.nc[1] : (cy >= g.nc[1] ? -g.nc[1] : 0);
+        cz += cz < 0 ? g.nc[2] : (cz >= g.nc[2] ? -g.nc[2] : 0);
+        int id = cell_id_of(g, cx, cy, cz);
+        int st = cell_start[id];
+        int cnt = cell_start[id + 1] - st;
+        m.start[t] = st;
+        // inclusive scan of the 64 counts over two warps
+        int lane = t & 31;
+        int v = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += y;
+        }
+        m.prefix[t + 1] = v;  // warp-local inclusive prefix for now
+    }
+    __syncthreads();
+    if (t >= 32 && t < 64) m.prefix[t + 1] += m.prefix[32];
+    if (t == 0) m.prefix[0] = 0;
+    __syncthreads();
+}
+
+// Tile slot holding tile index u (binary search in the 65-entry prefix).
+__device__ __forceinline__ int tile_slot_of(const TileMeta& m, int u) {
+    int lo = 0, hi = 64;
+    while (hi - lo > 1) {
+        int mid = (lo + hi) >> 1;
+        if (m.prefix[mid] <= u) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+// Stage the block-frame FP32 coordinates of the tile (T = m.prefix[64] <= cap).
+__device__ __forceinline__ void tile_stage_f32(const TileMeta& m, const float4* __restrict__ xr,
+                                               const TileOffsets& to, float4* __restrict__ tile,
+                                               int32_t* __restrict__ gidx) {
+    const int T = m.prefix[64];
+    for (int u = threadIdx.x; u < T; u += blockDim.x) {
+        int slot = tile_slot_of(m, u);
+        int c = c_tiles.coord_of_idx[slot];
+        int j = m.start[slot] + (u - m.prefix[slot]);
+        float4 p = xr[j];
+        p.x += to.off[0][c & 3];
+        p.y += to.off[1][(c >> 2) & 3];
+        p.z += to.off[2][c >> 4];
+        tile[u] = p;
+        if (gidx) gidx[u] = j;
+    }
+}
+
+}  // namespace mdgb

@@ -1,0 +1,271 @@
+"""Python binding of the mdgb C ABI (include/mdgb.h).
+
+Argument marshalling only: every step of the hot path runs in the CUDA
+kernels behind libmdgb.so.  Functions keep the C names (md_create,
+md_set_state, md_bin_cells, md_build_neighbors, md_forces, md_step,
+md_energy_virial, md_get_state, md_get_neighbors, md_get_cells,
+md_get_info, md_last_error, md_destroy) and accept numpy arrays (host
+pointers) or torch CUDA tensors (device pointers).
+
+Importing this module loads the library and raises if it is missing:
+there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+MD_OK = 0
+MD_ERR_ARG = -1
+MD_ERR_BOX_TOO_SMALL = -2
+MD_ERR_CELL_OVERFLOW = -3
+MD_ERR_LIST_OVERFLOW = -4
+MD_ERR_NONFINITE = -5
+MD_ERR_SKIN_VIOLATION = -6
+MD_ERR_CUDA = -7
+MD_ERR_TIMEOUT = -8
+MD_ERR_STATE = -9
+
+MD_FP64 = 0
+MD_MIXED = 1
+MD_LIST_FULL = 0
+MD_LIST_HALF_COLOUR8 = 1
+MD_REBUILD_SKIN_HALF = 0
+MD_REBUILD_EVERY_K = 1
+
+EXPORTED = ["md_create", "md_set_state", "md_bin_cells", "md_build_neighbors", "md_forces", "md_step",
+            "md_energy_virial", "md_get_state", "md_get_neighbors", "md_get_cells", "md_get_info",
+            "md_set_timing", "md_last_error", "md_destroy"]
+
+
+class md_params(C.Structure):
+    _fields_ = [("n_species", C.c_int32), ("eps", C.POINTER(C.c_double)), ("sigma", C.POINTER(C.c_double)),
+                ("rcut", C.POINTER(C.c_double)), ("mass", C.POINTER(C.c_double)), ("dt", C.c_double),
+                ("precision", C.c_int32), ("list_kind", C.c_int32), ("rebuild", C.c_int32),
+                ("rebuild_k", C.c_int32), ("stream", C.c_void_p)]
+
+
+class md_info(C.Structure):
+    _fields_ = [("n", C.c_int64), ("ncell", C.c_int32 * 3), ("list_cap", C.c_int32), ("tile_cap", C.c_int32),
+                ("n_builds", C.c_int64), ("n_steps", C.c_int64), ("list_entries", C.c_int64),
+                ("max_list", C.c_int32), ("max_tile", C.c_int32), ("cell_width", C.c_double * 3),
+                ("kernel_launches", C.c_int64), ("force_evals", C.c_int64), ("force_ms", C.c_double),
+                ("timed_force_evals", C.c_int64), ("build_ms", C.c_double), ("timed_builds", C.c_int64)]
+
+
+class MDError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"mdgb error {code}: {msg}")
+        self.code = code
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def _load():
+    path = _build.LIB
+    if not os.path.exists(path):
+        raise ImportError(f"libmdgb.so is not built ({path}); run paper_1305_4196_gb300.build.build()")
+    lib = C.CDLL(path)
+    P = C.c_void_p
+    lib.md_create.argtypes = [C.c_int64, P, C.c_double, C.c_double, C.POINTER(md_params), C.POINTER(P)]
+    lib.md_set_state.argtypes = [P, P, P, P, C.c_int]
+    lib.md_bin_cells.argtypes = [P]
+    lib.md_build_neighbors.argtypes = [P]
+    lib.md_forces.argtypes = [P, P, C.c_int]
+    lib.md_step.argtypes = [P, C.c_int32]
+    lib.md_energy_virial.argtypes = [P, P, P, P]
+    lib.md_get_state.argtypes = [P, P, P, P, C.c_int]
+    lib.md_get_neighbors.argtypes = [P, C.POINTER(C.c_int64), P]
+    lib.md_get_cells.argtypes = [P, P]
+    lib.md_get_info.argtypes = [P, C.POINTER(md_info)]
+    lib.md_set_timing.argtypes = [P, C.c_int]
+    lib.md_last_error.argtypes = [P, C.c_char_p, C.c_int64]
+    lib.md_destroy.argtypes = [P]
+    lib.md_destroy.restype = None
+    for name in EXPORTED:
+        if name != "md_destroy":
+            getattr(lib, name).restype = C.c_int
+    return lib
+
+
+_lib = _load()
+
+
+def _ptr(a):
+    """(pointer, is_device) of a numpy array or torch tensor (None -> NULL)."""
+    if a is None:
+        return None, None
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("arrays must be C-contiguous")
+        return a.ctypes.data, False
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensors must be contiguous")
+        return a.data_ptr(), bool(a.is_cuda)
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _check(handle, code):
+    if code != MD_OK:
+        raise MDError(code, md_last_error(handle))
+
+
+def md_last_error(handle) -> str:
+    buf = C.create_string_buffer(512)
+    _lib.md_last_error(handle, buf, 512)
+    return buf.value.decode(errors="replace")
+
+
+def md_create(n, box, r_cut, skin, eps, sigma, mass, dt, precision=MD_MIXED, list_kind=MD_LIST_FULL,
+              rebuild=MD_REBUILD_SKIN_HALF, rebuild_k=10, rcut=None, stream=None):
+    """Create a system; eps/sigma/rcut are n_species x n_species tables, mass has n_species entries."""
+    eps = np.ascontiguousarray(np.atleast_2d(eps), dtype=np.float64)
+    sigma = np.ascontiguousarray(np.atleast_2d(sigma), dtype=np.float64)
+    mass = np.ascontiguousarray(np.atleast_1d(mass), dtype=np.float64)
+    rc = None if rcut is None else np.ascontiguousarray(np.atleast_2d(rcut), dtype=np.float64)
+    box = np.ascontiguousarray(box, dtype=np.float64)
+    dp = C.POINTER(C.c_double)
+    p = md_params(int(mass.shape[0]), eps.ctypes.data_as(dp), sigma.ctypes.data_as(dp),
+                  rc.ctypes.data_as(dp) if rc is not None else None, mass.ctypes.data_as(dp), float(dt),
+                  int(precision), int(list_kind), int(rebuild), int(rebuild_k),
+                  C.c_void_p(stream) if stream else None)
+    out = C.c_void_p()
+    code = _lib.md_create(int(n), box.ctypes.data, float(r_cut), float(skin), C.byref(p), C.byref(out))
+    if code != MD_OK:
+        raise MDError(code, "md_create failed")
+    return out
+
+
+def md_set_state(handle, pos, vel, species=None):
+    (pp, dev), (vp, _), (sp, _) = _ptr(pos), _ptr(vel), _ptr(species)
+    _check(handle, _lib.md_set_state(handle, pp, vp, sp, int(bool(dev))))
+
+
+def md_bin_cells(handle):
+    _check(handle, _lib.md_bin_cells(handle))
+
+
+def md_build_neighbors(handle):
+    _check(handle, _lib.md_build_neighbors(handle))
+
+
+def md_forces(handle, f_out=None):
+    fp, dev = _ptr(f_out)
+    _check(handle, _lib.md_forces(handle, fp, int(bool(dev))))
+
+
+def md_step(handle, n_steps):
+    _check(handle, _lib.md_step(handle, int(n_steps)))
+
+
+def md_energy_virial(handle):
+    pe, ke = C.c_double(), C.c_double()
+    vir = (C.c_double * 6)()
+    _check(handle, _lib.md_energy_virial(handle, C.byref(pe), C.byref(ke), vir))
+    return pe.value, ke.value, np.array(vir[:])
+
+
+def md_get_state(handle, pos=None, vel=None, image=None):
+    (pp, d1), (vp, d2), (ip, d3) = _ptr(pos), _ptr(vel), _ptr(image)
+    devs = {d for d in (d1, d2, d3) if d is not None}
+    if len(devs) > 1:
+        raise ValueError("mix of host and device outputs")
+    _check(handle, _lib.md_get_state(handle, pp, vp, ip, int(devs == {True})))
+
+
+def md_get_neighbors(handle):
+    cnt = C.c_int64()
+    _check(handle, _lib.md_get_neighbors(handle, C.byref(cnt), None))
+    out = np.empty((max(cnt.value, 1), 2), dtype=np.int32)
+    _check(handle, _lib.md_get_neighbors(handle, C.byref(cnt), out.ctypes.data))
+    return out[:cnt.value]
+
+
+def md_get_cells(handle, n):
+    out = np.empty(int(n), dtype=np.int32)
+    _check(handle, _lib.md_get_cells(handle, out.ctypes.data))
+    return out
+
+
+def md_get_info(handle) -> dict:
+    info = md_info()
+    _check(handle, _lib.md_get_info(handle, C.byref(info)))
+    return {"n": info.n, "ncell": list(info.ncell), "list_cap": info.list_cap, "tile_cap": info.tile_cap,
+            "n_builds": info.n_builds, "n_steps": info.n_steps, "list_entries": info.list_entries,
+            "max_list": info.max_list, "max_tile": info.max_tile, "cell_width": list(info.cell_width),
+            "kernel_launches": info.kernel_launches, "force_evals": info.force_evals, "force_ms": info.force_ms,
+            "timed_force_evals": info.timed_force_evals, "build_ms": info.build_ms,
+            "timed_builds": info.timed_builds}
+
+
+def md_set_timing(handle, enable=True):
+    _check(handle, _lib.md_set_timing(handle, int(bool(enable))))
+
+
+def md_destroy(handle):
+    _lib.md_destroy(handle)
+
+
+class System:
+    """Owning wrapper around one md_system handle (destroyed with the object)."""
+
+    def __init__(self, n, box, r_cut=2.5, skin=0.3, eps=1.0, sigma=1.0, mass=1.0, dt=0.005,
+                 precision=MD_MIXED, list_kind=MD_LIST_FULL, rebuild=MD_REBUILD_SKIN_HALF, rebuild_k=10,
+                 rcut=None, stream=None):
+        self.n = int(n)
+        self.handle = md_create(n, box, r_cut, skin, eps, sigma, mass, dt, precision, list_kind, rebuild,
+                                rebuild_k, rcut, stream)
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h:
+            md_destroy(h)
+            self.handle = None
+
+    def close(self):
+        self.__del__()
+
+    def set_state(self, pos, vel, species=None):
+        md_set_state(self.handle, pos, vel, species)
+
+    def bin_cells(self):
+        md_bin_cells(self.handle)
+
+    def build_neighbors(self):
+        md_build_neighbors(self.handle)
+
+    def forces(self, out=None):
+        if out is None:
+            out = np.empty((self.n, 3))
+        md_forces(self.handle, out)
+        return out
+
+    def step(self, n_steps):
+        md_step(self.handle, n_steps)
+
+    def energy_virial(self):
+        return md_energy_virial(self.handle)
+
+    def get_state(self):
+        pos, vel, img = np.empty((self.n, 3)), np.empty((self.n, 3)), np.empty((self.n, 3), dtype=np.int32)
+        md_get_state(self.handle, pos, vel, img)
+        return pos, vel, img
+
+    def neighbors(self):
+        return md_get_neighbors(self.handle)
+
+    def cells(self):
+        return md_get_cells(self.handle, self.n)
+
+    def info(self):
+        return md_get_info(self.handle)
+
+    def set_timing(self, enable=True):
+        md_set_timing(self.handle, enable)

@@ -1,0 +1,147 @@
+"""The C-ABI boundary on the CPU: exports, struct layout, argument errors, colour schedule.
+
+No compute call is made here (there is no GPU in the CPU suite); md_create
+is only driven into the argument checks that fail before any CUDA call.
+"""
+import ctypes as C
+import os
+import re
+import subprocess
+import tempfile
+
+import numpy as np
+import pytest
+
+from paper_1305_4196_gb300 import build as B
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+INCLUDE = os.path.join(ROOT, "include")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    from paper_1305_4196_gb300 import mdgb
+    return mdgb
+
+
+def _declared():
+    names = []
+    for h in sorted(os.listdir(INCLUDE)):
+        if h.endswith(".h"):
+            txt = open(os.path.join(INCLUDE, h)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names += re.findall(r"^\s*(?:int|void)\s+\**\s*(md\w+)\s*\(", txt, flags=re.M)
+    return names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared()
+    assert len(names) >= 13
+    out = subprocess.run(["nm", "-D", "--defined-only", B.LIB], capture_output=True, text=True, check=True).stdout
+    exported = set(re.findall(r"\sT\s(\w+)", out))
+    missing = [n for n in names if n not in exported]
+    assert not missing, missing
+    for n in lib.EXPORTED:
+        assert n in names
+
+
+def test_struct_layout_matches_binding(lib):
+    src = r'''
+#include <stdio.h>
+#include <stddef.h>
+#include "mdgb.h"
+int main(void) {
+  printf("%zu %zu %zu %zu %zu\n", sizeof(md_params), offsetof(md_params, dt), offsetof(md_params, stream),
+         sizeof(md_info), offsetof(md_info, cell_width));
+  return 0;
+}'''
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "t.c")
+        open(c, "w").write(src)
+        exe = os.path.join(d, "t")
+        subprocess.run(["gcc", "-I", INCLUDE, c, "-o", exe], check=True)
+        got = [int(v) for v in subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()]
+    P, I = lib.md_params, lib.md_info
+    assert got == [C.sizeof(P), P.dt.offset, P.stream.offset, C.sizeof(I), I.cell_width.offset]
+
+
+def test_argument_errors_before_any_cuda_call(lib):
+    M = lib
+    cases = [
+        dict(n=10, box=[10, 10, 10], code=M.MD_ERR_BOX_TOO_SMALL),          # < 4 r_list per side
+        dict(n=10, box=[40, 40, 11.1], code=M.MD_ERR_BOX_TOO_SMALL),
+        dict(n=10, box=[40, 40, 40], sigma=-1.0, code=M.MD_ERR_ARG),
+        dict(n=10, box=[40, 40, 40], mass=0.0, code=M.MD_ERR_ARG),
+        dict(n=10, box=[40, 40, 40], dt=0.0, code=M.MD_ERR_ARG),
+        dict(n=10, box=[40, 40, 40], precision=7, code=M.MD_ERR_ARG),
+        dict(n=10, box=[40, 40, 40], list_kind=3, code=M.MD_ERR_ARG),
+        dict(n=-1, box=[40, 40, 40], code=M.MD_ERR_ARG),
+        dict(n=10, box=[40, 40, 40], eps=[[1.0, 2.0], [1.0, 1.0]], sigma=[[1, 1], [1, 1]], mass=[1, 1],
+             code=M.MD_ERR_ARG),                                              # asymmetric table
+    ]
+    for c in cases:
+        code = c.pop("code")
+        kw = dict(r_cut=2.5, skin=0.3, eps=1.0, sigma=1.0, mass=1.0, dt=0.005)
+        kw.update(c)
+        with pytest.raises(M.MDError) as ei:
+            M.md_create(kw.pop("n"), kw.pop("box"), **kw)
+        assert ei.value.code == code, c
+
+
+def _dbg(lib):
+    L = lib._lib
+    L.mdgb_grid_shape.argtypes = [C.c_void_p, C.c_double, C.c_void_p]
+    L.mdgb_num_blocks.argtypes = [C.c_void_p, C.c_void_p]
+    L.mdgb_block_colour.argtypes = [C.c_void_p, C.c_int32, C.c_void_p]
+    L.mdgb_tile_cells.argtypes = [C.c_void_p, C.c_int32, C.c_void_p]
+    return L
+
+
+@pytest.mark.parametrize("box,rl", [((16.795962, 16.795962, 16.795962), 2.8),
+                                    ((134.3677, 134.3677, 134.3677), 2.8),
+                                    ((30.0, 41.0, 52.5), 2.8)])
+def test_grid_shape(lib, box, rl):
+    L = _dbg(lib)
+    nc = np.zeros(3, dtype=np.int32)
+    assert L.mdgb_grid_shape(np.array(box).ctypes.data, rl, nc.ctypes.data) == 0
+    for d in range(3):
+        assert nc[d] % 4 == 0 and box[d] / nc[d] >= rl
+        # the next multiple of 4 would make cells narrower than r_list
+        assert box[d] / (nc[d] + 4) < rl
+    if box[0] == 134.3677:
+        assert nc.tolist() == [44, 44, 44]
+    if box[0] == 16.795962:
+        assert nc.tolist() == [4, 4, 4]
+
+
+@pytest.mark.parametrize("nc", [(4, 4, 4), (8, 12, 16), (44, 44, 44)])
+def test_colour_schedule_tiles_disjoint(lib, nc):
+    """Sec. II.A/II.B: tasks in one wave must not overlap.  Every block's 4x4x4 tile
+    holds 64 distinct cells, own cells of all blocks partition the grid, and the
+    tiles of any two blocks of one colour share no cell."""
+    L = _dbg(lib)
+    ncv = np.array(nc, dtype=np.int32)
+    nb = np.zeros(1, dtype=np.int32)
+    assert L.mdgb_num_blocks(ncv.ctypes.data, nb.ctypes.data) == 0
+    nb = int(nb[0])
+    ncell = nc[0] * nc[1] * nc[2]
+    assert nb * 8 == ncell
+    own_seen = np.zeros(ncell, dtype=np.int32)
+    tiles = {c: [] for c in range(8)}
+    buf = np.zeros(64, dtype=np.int32)
+    col = np.zeros(1, dtype=np.int32)
+    for b in range(nb):
+        assert L.mdgb_tile_cells(ncv.ctypes.data, b, buf.ctypes.data) == 0
+        assert len(set(buf.tolist())) == 64
+        own_seen[buf[:8]] += 1
+        assert L.mdgb_block_colour(ncv.ctypes.data, b, col.ctypes.data) == 0
+        tiles[int(col[0])].append(buf.copy())
+    assert np.all(own_seen == 1)
+    for c in range(8):
+        allc = np.concatenate(tiles[c])
+        assert len(np.unique(allc)) == len(allc), f"colour {c} has overlapping tiles"
+        assert len(tiles[c]) == nb // 8
+        # blocks of one colour are contiguous in the block numbering
+    # own cells of a block are its 2x2x2 cells: adjacent in every dimension
+    assert L.mdgb_tile_cells(ncv.ctypes.data, nb, buf.ctypes.data) != 0  # out of range

@@ -1,0 +1,332 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Bars: neighbour sets bit-exact; forces per atom e_i = |F_i - F_i^ref| /
+max(|F_i^ref|, F_rms) <= 1e-12 (FP64 path) and <= 2e-5 (mixed path); energy
+and virial relative error <= 1e-12 (FP64) and <= 1e-6 (mixed); FP64
+trajectories within 1e-10 sigma over 100 steps; fixed-point forces bit-equal
+across list kinds, runs and input orderings, with an exactly zero sum.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from oracle import oracle as O  # noqa: E402
+from paper_1305_4196_gb300 import build as B  # noqa: E402
+from paper_1305_4196_gb300 import workloads as W  # noqa: E402
+
+B.build()
+from paper_1305_4196_gb300 import mdgb as M  # noqa: E402
+
+RC, SKIN, DT = 2.5, 0.3, 0.005
+PRECISIONS = {"fp64": M.MD_FP64, "mixed": M.MD_MIXED}
+LISTS = {"full": M.MD_LIST_FULL, "half": M.MD_LIST_HALF_COLOUR8}
+TOL = {"fp64": 1e-12, "mixed": 2e-5}
+
+
+def force_error(F, Fref):
+    mag = np.sqrt((Fref ** 2).sum(1))
+    frms = np.sqrt((mag ** 2).mean())
+    e = np.sqrt(((F - Fref) ** 2).sum(1)) / np.maximum(mag, frms)
+    return float(e.max())
+
+
+def make(sysm, precision="mixed", lst="full", params=None, **kw):
+    if params is None:
+        params = O.LJParams.single()
+    s = M.System(sysm.n, sysm.box, r_cut=float(params.rc.max()), skin=SKIN, eps=params.eps, sigma=params.sig,
+                 mass=params.mass, dt=DT, precision=PRECISIONS[precision], list_kind=LISTS[lst],
+                 rcut=params.rc if params.nsp > 1 else None, **kw)
+    s.set_state(np.ascontiguousarray(sysm.pos), np.ascontiguousarray(sysm.vel),
+                np.ascontiguousarray(sysm.species))
+    return s
+
+
+def liquid(n_cells=14, seed=21):
+    return W.lj_fcc(n_cells, seed=seed, jitter=0.05)
+
+
+def gas(n=3000, box=(22.5, 25.0, 31.0), seed=5):
+    box = np.array(box)
+    pos = W.random_gas(n, box, seed=seed)
+    return W.System(pos, np.zeros_like(pos), np.zeros(n, dtype=np.int32), box, "gas")
+
+
+def threshold():
+    box = np.array([30.0, 30.0, 30.0])
+    pos = W.threshold_pairs(343, box, RC + SKIN, 1e-12, seed=9)
+    return W.System(pos, np.zeros_like(pos), np.zeros(len(pos), dtype=np.int32), box, "threshold")
+
+
+def slab():
+    s = W.slab_nanoparticles(L=40.0, n_particles=4, r_min=3.0, r_max=5.0, seed=3)
+    return s
+
+
+# ---------------------------------------------------------------- binning
+def test_binning_puts_every_atom_in_its_cell():
+    sysm = liquid()
+    s = make(sysm)
+    s.bin_cells()
+    cells = s.cells()
+    pos, _, img = s.get_state()
+    info = s.info()
+    nc = np.array(info["ncell"])
+    w = np.array(info["cell_width"])
+    c3 = np.stack([cells % nc[0], (cells // nc[0]) % nc[1], cells // (nc[0] * nc[1])], axis=1)
+    assert np.all(pos >= 0.0) and np.all(pos < sysm.box)
+    assert np.all(c3 * w <= pos + 1e-12) and np.all(pos < (c3 + 1) * w + 1e-12)
+    # wrapping is the only change: unwrapped positions are the inputs
+    assert np.array_equal(pos + img * sysm.box, sysm.pos) or np.allclose(pos + img * sysm.box, sysm.pos, atol=1e-13)
+    assert np.bincount(cells, minlength=int(nc.prod())).sum() == sysm.n
+
+
+# ---------------------------------------------------------------- neighbour sets
+@pytest.mark.parametrize("kind", ["liquid", "gas", "threshold", "slab"])
+@pytest.mark.parametrize("lst", ["full", "half"])
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_neighbour_set_bit_exact(kind, lst, precision):
+    sysm = {"liquid": liquid, "gas": gas, "threshold": threshold, "slab": slab}[kind]()
+    s = make(sysm, precision, lst)
+    s.build_neighbors()
+    got = s.neighbors()
+    ref = O.neighbor_pairs(sysm.pos, sysm.box, RC + SKIN)
+    assert got.shape == ref.shape
+    assert np.array_equal(got, ref)
+
+
+def test_fcc_list_lengths():
+    """Perfect fcc at rho*=0.8442: every atom has exactly 78 neighbours inside 2.8."""
+    sysm = W.lj_fcc(14, seed=1)
+    s = make(sysm, "mixed", "full")
+    s.build_neighbors()
+    info = s.info()
+    assert info["list_entries"] == 78 * sysm.n and info["max_list"] == 78
+    s2 = make(sysm, "mixed", "half")
+    s2.build_neighbors()
+    assert s2.info()["list_entries"] == 39 * sysm.n
+
+
+# ---------------------------------------------------------------- forces
+@pytest.mark.parametrize("lst", ["full", "half"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("kind", ["liquid", "slab"])
+def test_forces_vs_oracle(kind, lst, precision):
+    sysm = liquid() if kind == "liquid" else slab()
+    s = make(sysm, precision, lst)
+    F = s.forces()
+    Fref, _, _ = O.lj_forces(sysm.pos, sysm.box, O.LJParams.single())
+    assert force_error(F, Fref) <= TOL[precision]
+
+
+@pytest.mark.parametrize("lst", ["full", "half"])
+def test_mixed_forces_bitwise_reproducible_and_order_independent(lst):
+    """Fixed-point sums do not depend on summation order: repeated runs and any input
+    ordering give bit-identical forces."""
+    sysm = liquid()
+    a = make(sysm, "mixed", lst).forces()
+    b = make(sysm, "mixed", lst).forces()
+    assert np.array_equal(a, b)
+    perm = np.argsort(W.splitmix64(3, 3, sysm.n))
+    sp = W.System(sysm.pos[perm], sysm.vel[perm], sysm.species[perm], sysm.box)
+    d = make(sp, "mixed", lst).forces()
+    assert np.array_equal(d, a[perm])
+
+
+def test_mixed_full_and_half_lists_agree():
+    sysm = liquid()
+    a = make(sysm, "mixed", "full").forces()
+    c = make(sysm, "mixed", "half").forces()
+    assert force_error(c, a) <= 2 * TOL["mixed"]
+
+
+def test_mixed_force_sum():
+    """Half lists evaluate each pair once, so f_ji = -f_ij bit for bit and the fixed-point
+    total is exactly zero.  Full lists evaluate a pair from both sides, in each block's own
+    FP32 frame: the total is zero to FP32 rounding."""
+    sysm = liquid()
+    F = make(sysm, "mixed", "half").forces()
+    q = np.rint(F * 2.0 ** 32).astype(np.int64)
+    assert np.array_equal(q.astype(np.float64) * 2.0 ** -32, F)
+    assert np.all(q.sum(axis=0) == 0)
+    F = make(sysm, "mixed", "full").forces()
+    frms = np.sqrt((F ** 2).sum(1).mean())
+    assert np.abs(F.sum(axis=0)).max() <= 1e-5 * frms * np.sqrt(sysm.n)
+
+
+def test_forces_translation_invariance_mixed():
+    sysm = liquid()
+    F = make(sysm, "mixed").forces()
+    t = np.array([3.3, -7.1, 0.37])
+    sh = W.System(W.wrap(sysm.pos + t, sysm.box), sysm.vel, sysm.species, sysm.box)
+    F2 = make(sh, "mixed").forces()
+    assert force_error(F2, F) <= 2 * TOL["mixed"]
+
+
+def test_multispecies_per_pair_cutoff():
+    """Kob-Andersen-type binary mixture: per-pair eps, sigma and r_cut = 2.5 sigma_ab."""
+    a = W.lattice_constant(1.2)
+    pos, box = W.fcc_lattice(14, 14, 14, a)
+    pos = W.gaussian_jitter(pos, box, 0.03, seed=4)
+    sp = W.species_shuffle(len(pos), 0.2, seed=4)
+    sysm = W.System(pos, np.zeros_like(pos), sp, box)
+    sig = np.array([[1.0, 0.8], [0.8, 0.88]])
+    P = O.LJParams([[1.0, 1.5], [1.5, 0.5]], sig, 2.5 * sig, [1.0, 1.0])
+    Fref, pe_ref, vir_ref = O.lj_forces(pos, box, P, species=sp)
+    for precision in ("fp64", "mixed"):
+        for lst in ("full", "half"):
+            s = make(sysm, precision, lst, params=P)
+            F = s.forces()
+            assert force_error(F, Fref) <= TOL[precision], (precision, lst)
+            pe, _, vir = s.energy_virial()
+            tol = 1e-12 if precision == "fp64" else 1e-6
+            assert abs(pe - pe_ref) <= tol * abs(pe_ref)
+            assert np.abs(vir - vir_ref).max() <= tol * np.abs(vir_ref[:3]).max()
+
+
+# ---------------------------------------------------------------- energies
+@pytest.mark.parametrize("lst", ["full", "half"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_energy_virial_vs_oracle(lst, precision):
+    sysm = liquid()
+    s = make(sysm, precision, lst)
+    pe, ke, vir = s.energy_virial()
+    P = O.LJParams.single()
+    _, pe_ref, vir_ref = O.lj_forces(sysm.pos, sysm.box, P)
+    ke_ref = O.kinetic(sysm.vel, P)
+    tol = 1e-12 if precision == "fp64" else 1e-6
+    assert abs(pe - pe_ref) <= tol * abs(pe_ref)
+    assert abs(ke - ke_ref) <= 1e-12 * ke_ref
+    assert np.abs(vir - vir_ref).max() <= tol * np.abs(vir_ref[:3]).max()
+
+
+def test_fcc_lattice_energy_on_gpu():
+    sysm = W.lj_fcc(14, seed=1)
+    for precision in ("fp64", "mixed"):
+        pe, _, vir = make(sysm, precision).energy_virial()
+        tol = 1e-12 if precision == "fp64" else 1e-6
+        assert pe / sysm.n == pytest.approx(-6.7733680533, rel=tol)
+        assert vir[:3].sum() / sysm.n == pytest.approx(-22.1581992540, rel=tol)
+
+
+# ---------------------------------------------------------------- trajectories
+@pytest.mark.parametrize("lst", ["full", "half"])
+def test_fp64_trajectory_config1(lst):
+    """4,000-atom fcc at T*=0.72, 100 velocity-Verlet steps, skin/2 rebuilds: FP64 GPU vs oracle."""
+    sysm = W.lj_fcc(10, seed=1)
+    s = make(sysm, "fp64", lst)
+    s.step(100)
+    pos, vel, img = s.get_state()
+    ref = O.run_nve(sysm.pos, sysm.vel, sysm.box, O.LJParams.single(), DT, SKIN, 100)
+    assert np.abs(pos + img * sysm.box - (ref["pos"] + ref["image"] * sysm.box)).max() < 1e-10
+    assert np.abs(vel - ref["vel"]).max() < 1e-9
+    assert s.info()["n_builds"] - 1 == ref["rebuilds"]
+
+
+def test_mixed_trajectory_short():
+    sysm = W.lj_fcc(10, seed=1)
+    s = make(sysm, "mixed", "full")
+    s.step(20)
+    pos, vel, img = s.get_state()
+    ref = O.run_nve(sysm.pos, sysm.vel, sysm.box, O.LJParams.single(), DT, SKIN, 20)
+    assert np.abs(pos + img * sysm.box - (ref["pos"] + ref["image"] * sysm.box)).max() < 1e-6
+
+
+def test_rebuild_every_k_policy_matches_oracle():
+    sysm = W.lj_fcc(10, seed=2)
+    s = make(sysm, "fp64", "full", rebuild=M.MD_REBUILD_EVERY_K, rebuild_k=5)
+    s.step(30)
+    pos, vel, img = s.get_state()
+    ref = O.run_nve(sysm.pos, sysm.vel, sysm.box, O.LJParams.single(), DT, SKIN, 30, policy=1, every_k=5)
+    assert s.info()["n_builds"] - 1 == ref["rebuilds"] == 6
+    assert np.abs(pos + img * sysm.box - (ref["pos"] + ref["image"] * sysm.box)).max() < 1e-10
+
+
+def test_energy_conservation_mixed():
+    sysm = W.lj_fcc(10, seed=1)
+    s = make(sysm, "mixed")
+    pe0, ke0, _ = s.energy_virial()
+    s.step(100)
+    pe1, ke1, _ = s.energy_virial()
+    ref = O.run_nve(sysm.pos, sysm.vel, sysm.box, O.LJParams.single(), DT, SKIN, 100, history=True)
+    e_ref = (ref["pe"][-1] + ref["ke"][-1]) / sysm.n
+    assert abs((pe1 + ke1) / sysm.n - e_ref) < 1e-4
+
+
+# ---------------------------------------------------------------- device pointers and edge cases
+def test_device_pointer_path_matches_host_path():
+    sysm = liquid(10)
+    dev = torch.device("cuda")
+    s = M.System(sysm.n, sysm.box, stream=torch.cuda.current_stream().cuda_stream)
+    s.set_state(torch.from_numpy(sysm.pos).to(dev), torch.from_numpy(sysm.vel).to(dev),
+                torch.from_numpy(sysm.species).to(dev))
+    Fd = torch.empty((sysm.n, 3), dtype=torch.float64, device=dev)
+    s.forces(Fd)
+    torch.cuda.synchronize()
+    Fh = make(sysm, "mixed").forces()
+    assert np.array_equal(Fd.cpu().numpy(), Fh)
+
+
+def test_edge_cases():
+    box = np.array([12.0, 12.0, 12.0])
+    # one atom: no neighbours, zero force
+    s = M.System(1, box)
+    s.set_state(np.array([[1.0, 2.0, 3.0]]), np.zeros((1, 3)))
+    assert np.all(s.forces() == 0.0)
+    assert len(s.neighbors()) == 0
+    s.step(3)
+    # two atoms beyond the list radius
+    s2 = M.System(2, box, precision=M.MD_FP64)
+    s2.set_state(np.array([[1.0, 1.0, 1.0], [7.0, 7.0, 7.0]]), np.zeros((2, 3)))
+    assert np.all(s2.forces() == 0.0)
+    # empty system
+    s0 = M.System(0, box)
+    s0.set_state(np.zeros((0, 3)), np.zeros((0, 3)))
+    s0.step(2)
+    assert s0.energy_virial()[0] == 0.0
+    # errors surface as codes
+    s3 = M.System(4, box)
+    with pytest.raises(M.MDError) as e:
+        s3.forces()
+    assert e.value.code == M.MD_ERR_STATE
+    with pytest.raises(M.MDError) as e:
+        s3.set_state(np.ones((4, 3)), np.zeros((4, 3)), np.array([0, 1, 0, 0], dtype=np.int32))
+    assert e.value.code == M.MD_ERR_ARG
+    # a dense clump in a mostly empty box overflows the capacities sized from the mean
+    # density; the library regrows them and still matches the oracle
+    clump, _ = W.fcc_lattice(5, 5, 4, 0.5)
+    clump = W.gaussian_jitter(clump + 4.0, box, 0.01, seed=7)
+    s4 = M.System(len(clump), box, sigma=0.3, r_cut=0.75, skin=0.3)
+    s4.set_state(np.ascontiguousarray(clump), np.zeros_like(clump))
+    P = O.LJParams.single(sig=0.3, rc=0.75)
+    assert force_error(s4.forces(), O.lj_forces(clump, box, P)[0]) <= 2e-5
+    assert s4.info()["max_list"] > 24
+
+
+# ---------------------------------------------------------------- full size (2,048,000 atoms)
+@pytest.mark.parametrize("lst", ["full", "half"])
+def test_full_size_config2_sampled(lst):
+    """80^3 fcc cells at rho*=0.8442 with liquid-like jitter, the benchmark's launch
+    configuration: pair count equals the oracle's, sampled forces match."""
+    sysm = W.lj_fcc(80, seed=2, jitter=0.05)
+    s = make(sysm, "mixed", lst)
+    F = s.forces()
+    info = s.info()
+    assert info["ncell"] == [44, 44, 44]
+    n_pairs_ref = O._load().orc_neighbor_pairs(sysm.n, np.ascontiguousarray(sysm.pos).ravel(), sysm.box,
+                                               RC + SKIN, 0, 0, None)
+    expect = n_pairs_ref if lst == "half" else 2 * n_pairs_ref
+    assert info["list_entries"] == expect
+    idx = np.sort(W.splitmix64(11, 0, 256) % np.uint64(sysm.n)).astype(np.int64)
+    Fs, _, _ = O.lj_forces_subset(sysm.pos, sysm.box, O.LJParams.single(), idx)
+    mag = np.sqrt((Fs ** 2).sum(1))
+    frms = np.sqrt((F ** 2).sum(1).mean())
+    e = np.sqrt(((F[idx] - Fs) ** 2).sum(1)) / np.maximum(mag, frms)
+    assert e.max() <= TOL["mixed"]
+    if lst == "half":
+        q = np.rint(F * 2.0 ** 32).astype(np.int64)
+        assert np.all(q.sum(axis=0) == 0)
