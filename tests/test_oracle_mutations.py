@@ -22,7 +22,7 @@ MUTATIONS = {
     "nonstrict_cutoff_search": ("if (r2 < r2max) fn(ctx, i, j, d, r2);\n            }\n        return;",
                                 "if (r2 <= r2max) fn(ctx, i, j, d, r2);\n            }\n        return;"),
     "no_minimum_image": ("return d - L * nearbyint(d / L);", "return d + 0.0 * L;"),
-    "virial_index_swap": ("a->vir[3] += d[0] * (fr * d[1]);", "a->vir[3] += d[0] * (fr * d[2]);"),
+    "virial_index_swap": ("csum_add(&a->vir[3], d[0] * (fr * d[1]));", "csum_add(&a->vir[3], d[0] * (fr * d[2]));"),
     "half_cell_shell": ("for (int ox = -1; ox <= 1; ++ox) {", "for (int ox = 0; ox <= 1; ++ox) {"),
     "full_kick": ("hdtm[s] = (0.5 * dt) / mass[s];", "hdtm[s] = dt / mass[s];"),
     "sigma_not_squared": ("double sr2 = (s * s) / r2;\n    double s6 = sr2 * sr2 * sr2;\n    double u",

@@ -210,6 +210,11 @@ def test_fcc_lattice_sums_and_zero_force():
     assert np.abs(f).max() < 1e-11
     # the same numbers to the 8 digits computed by an independent shell summation
     assert pe / 4000 == pytest.approx(-6.7733680, abs=1e-7)
+    # a larger crystal: the whole-system sums stay at rounding level of the exact value
+    pos14, box14 = W.fcc_lattice(14, 14, 14, a)
+    _, pe14, vir14 = O.lj_forces(pos14, box14, O.LJParams.single())
+    assert pe14 / len(pos14) == pytest.approx(e_atom, rel=1e-13)
+    assert (vir14[0] + vir14[1] + vir14[2]) / len(pos14) == pytest.approx(w_atom, rel=1e-13)
     assert (vir[0] + vir[1] + vir[2]) / 4000 == pytest.approx(-22.158199, abs=5e-7)
 
 
