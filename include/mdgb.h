@@ -97,6 +97,7 @@ typedef struct {
     int64_t timed_force_evals; /* force evaluations included in force_ms */
     double build_ms;           /* summed device time of binning + list builds (only while timing is on) */
     int64_t timed_builds;      /* builds included in build_ms */
+    int64_t n_redos;           /* md_step chunks redone after a rebuild outgrew the captured capacities */
 } md_info;
 
 /*
@@ -147,6 +148,11 @@ int md_forces(md_system *s, double *f_out, int device_ptrs);
 /*
  * Integrate n_steps velocity-Verlet steps: v += dt F/(2m); x += dt v;
  * rebuild lists if the policy says so; F = F(x); v += dt F/(2m).
+ * Steps run as CUDA-graph launches (one graph per step, the rebuild decision
+ * taken on the device in a conditional node); the host reads the device status
+ * once per chunk of up to 200 steps.  If a rebuild inside a chunk outgrows the
+ * list or tile capacity, the chunk is redone from a snapshot of its starting
+ * state after the capacities have been regrown (md_info.n_redos counts these).
  * Energies are not computed on the way (use md_energy_virial).
  * Errors: MD_ERR_NONFINITE, MD_ERR_SKIN_VIOLATION, overflow codes, MD_ERR_CUDA.
  */

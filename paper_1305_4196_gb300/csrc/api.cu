@@ -27,8 +27,8 @@ struct md_system {
     double rcut = 0, skin = 0, rl = 0, rl2 = 0, dt = 0, lim2 = 0;
     int precision = MD_MIXED, list_kind = MD_LIST_FULL, rebuild = MD_REBUILD_SKIN_HALF, rebuild_k = 10;
     int list_cap = 0, tile_cap = 0;
-    DevState st[2]{};
-    int cur = 0;
+    DevState st[3]{};  // [0] the state, [1] scratch for the reorder gather, [2] snapshot for redo
+    int cur = 0;       // always 0: the state lives in st[0]
     // binning scratch
     int32_t *atom_cell = nullptr, *cell_count = nullptr, *cursor = nullptr, *slot_key = nullptr,
             *slot_src = nullptr, *sorted_src = nullptr, *scan_scratch = nullptr;
@@ -40,11 +40,25 @@ struct md_system {
     int max_list = 0, max_tile = 0;
     std::vector<void*> allocs;
     // launch accounting and optional event timing
-    int64_t launches = 0, force_evals = 0;
+    int64_t launches = 0, force_evals = 0, n_redos = 0;
     bool timing = false;
     double force_ms = 0, build_ms = 0;
     int64_t timed_force = 0, timed_build = 0;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_force, ev_build, ev_free;
+    // graph-captured time steps
+    struct StepGraph {
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        cudaGraphNode_t ev_a = nullptr, ev_b = nullptr;
+    };
+    cudaStream_t cap_stream = nullptr;
+    StepGraph g_first, g_mid;
+    bool graphs_valid = false;
+    int graph_tile_cap = 0, graph_list_cap = 0;
+    bool graph_timing = false;
+    long long* d_ctrl = nullptr;  // [0] step counter, [1] builds done inside graphs
+    long long* h_ctrl = nullptr;  // pinned mirror
+    bool snapshot_first = true;
     char msg[512] = "";
 };
 
@@ -152,8 +166,9 @@ int alloc_lists(md_system* s, int cap) {
     int rc = dalloc(s, &nl, (size_t)cap * s->np);
     if (rc) return rc;
     dfree(s, s->st[0].nl);
-    s->st[0].nl = s->st[1].nl = nl;
+    s->st[0].nl = s->st[1].nl = s->st[2].nl = nl;
     s->list_cap = cap;
+    s->graphs_valid = false;
     return MD_OK;
 }
 
@@ -177,22 +192,24 @@ int check_err(md_system* s, uint32_t mask) {
     return fail(s, MD_ERR_ARG, "device error 0x%x", e);
 }
 
-// ---- binning: assign, count, scan, scatter, in-cell order, gather (swaps the state buffers)
+// ---- binning: assign, count, scan, scatter, in-cell order, gather + copy back
+void enqueue_bin(md_system* s, cudaStream_t st) {
+    const Geometry& g = s->g;
+    cudaMemsetAsync(s->cell_count, 0, sizeof(int32_t) * g.ncell, st);
+    cudaMemsetAsync(s->cursor, 0, sizeof(int32_t) * g.ncell, st);
+    const DevState& a = s->st[0];
+    launch_bin_assign(a, g, s->atom_cell, s->cell_count, st);
+    launch_scan(s->cell_count, a.cell_start, g.ncell, s->scan_scratch, st);
+    launch_scatter(a, s->atom_cell, a.cell_start, s->cursor, s->slot_key, s->slot_src, st);
+    launch_cell_sort(g, a.cell_start, s->slot_key, s->slot_src, s->sorted_src, st);
+    launch_gather(a, s->st[1], g, s->sorted_src, s->atom_cell, st);
+}
+
 int do_bin(md_system* s) {
     if (s->n == 0) return MD_OK;
-    const Geometry& g = s->g;
-    CK(cudaMemsetAsync(s->cell_count, 0, sizeof(int32_t) * g.ncell, s->stream));
-    CK(cudaMemsetAsync(s->cursor, 0, sizeof(int32_t) * g.ncell, s->stream));
-    DevState& a = s->st[s->cur];
-    DevState& b = s->st[s->cur ^ 1];
-    launch_bin_assign(a, g, s->atom_cell, s->cell_count, s->stream);
-    launch_scan(s->cell_count, a.cell_start, g.ncell, s->scan_scratch, s->stream);
-    launch_scatter(a, s->atom_cell, a.cell_start, s->cursor, s->slot_key, s->slot_src, s->stream);
-    launch_cell_sort(g, a.cell_start, s->slot_key, s->slot_src, s->sorted_src, s->stream);
-    launch_gather(b, a, g, s->sorted_src, s->atom_cell, mixed(s), s->stream);
+    enqueue_bin(s, s->stream);
     CKL();
-    s->launches += 7;
-    s->cur ^= 1;
+    s->launches += 8;
     s->lists_valid = false;
     s->forces_valid = false;
     return MD_OK;
@@ -215,6 +232,8 @@ int do_build(md_system* s) {
         DevState& a = s->st[s->cur];
         CK(cudaMemsetAsync(a.stats, 0, 4 * sizeof(int32_t), s->stream));
         CK(cudaMemsetAsync(a.err, 0, sizeof(uint32_t), s->stream));
+        if (build_lists_smem(s->list_cap, s->tile_cap) > 226 * 1024 && s->tile_cap > s->max_tile)
+            s->tile_cap = std::max(s->max_tile, round_up(s->max_tile + 1, 32));
         if (build_lists_smem(s->list_cap, s->tile_cap) > 226 * 1024)
             return fail(s, MD_ERR_CELL_OVERFLOW, "tile (%d atoms) and lists (%d) exceed shared memory",
                         s->tile_cap, s->list_cap);
@@ -255,11 +274,19 @@ int do_build(md_system* s) {
             s->lists_valid = true;
             // keep the tile capacity close to the need (max_tile counts the dummy slot) so
             // that more CTAs fit per SM and every shared-memory layout stays within limits
-            s->tile_cap = round_up(max_tile + max_tile / 8 + 32, 32);
+            // (25 % headroom: later rebuilds inside graph-launched steps reuse this capacity)
+            s->tile_cap = std::max(max_tile, std::min(round_up(max_tile + max_tile / 4 + 64, 32),
+                                                      round_up((int)s->n + 1, 32)));
             return MD_OK;
         }
     }
     return fail(s, MD_ERR_LIST_OVERFLOW, "capacity regrowth did not converge");
+}
+
+void enqueue_forces(md_system* s, int with_energy, cudaStream_t st) {
+    const DevState& a = s->st[0];
+    if (mixed(s)) launch_forces_mixed(a, s->g, s->pt, s->to, s->tile_cap, half(s), with_energy, st);
+    else launch_forces_fp64(a, s->g, s->pt, s->tile_cap, half(s), with_energy, st);
 }
 
 int do_forces(md_system* s, int with_energy) {
@@ -325,6 +352,148 @@ int validate_params(md_system* s, const md_params* p, double r_cut) {
     return MD_OK;
 }
 
+// ---- graph-captured time steps
+//
+// One step = integrate -> step control (sets the IF condition) -> IF(rebuild){binning,
+// gather, copy back, list build} -> forces.  Kernel arguments are fixed at capture,
+// which is why the state always lives in st[0].  Captured for the first step of a call
+// (half kick + drift) and for the following ones (closing + opening kick + drift).
+void destroy_graph(md_system::StepGraph& g) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    if (g.graph) cudaGraphDestroy(g.graph);
+    g = md_system::StepGraph{};
+}
+
+int capture_step(md_system* s, int mode, md_system::StepGraph& out) {
+    destroy_graph(out);
+    cudaStream_t cs = s->cap_stream;
+    cudaGraph_t g = nullptr;
+    CK(cudaGraphCreate(&g, 0));
+    out.graph = g;
+    cudaGraphConditionalHandle h;
+    CK(cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault));
+    CK(cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    const DevState& a = s->st[0];
+    launch_integrate(a, s->g, s->pt, mode, mixed(s), s->dt, s->lim2, cs);
+    launch_step_ctrl(s->rebuild == MD_REBUILD_EVERY_K ? 1 : 0, s->rebuild_k, a.rebuild_flag, s->d_ctrl,
+                     s->d_ctrl + 1, a.err, h, cs);
+    cudaStreamCaptureStatus status;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t ndeps = 0;
+    cudaGraph_t cg = nullptr;
+    CK(cudaStreamGetCaptureInfo(cs, &status, nullptr, &cg, &deps, nullptr, &ndeps));
+    alignas(cudaGraphNodeParams) unsigned char cp_raw[sizeof(cudaGraphNodeParams)];
+    std::memset(cp_raw, 0, sizeof(cp_raw));  // all reserved bytes must be zero
+    cudaGraphNodeParams& cp = *reinterpret_cast<cudaGraphNodeParams*>(cp_raw);
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeIf;
+    cp.conditional.size = 1;
+    cudaGraphNode_t cnode;
+    CK(cudaGraphAddNode(&cnode, cg, deps, nullptr, ndeps, &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    CK(cudaStreamUpdateCaptureDependencies(cs, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies));
+    if (s->timing) {
+        auto ev = take_events(s);
+        s->ev_free.push_back(ev);
+        CK(cudaEventRecordWithFlags(ev.first, cs, cudaEventRecordExternal));
+        CK(cudaStreamGetCaptureInfo(cs, &status, nullptr, &cg, &deps, nullptr, &ndeps));
+        out.ev_a = ndeps ? deps[0] : nullptr;
+        enqueue_forces(s, 0, cs);
+        CK(cudaEventRecordWithFlags(ev.second, cs, cudaEventRecordExternal));
+        CK(cudaStreamGetCaptureInfo(cs, &status, nullptr, &cg, &deps, nullptr, &ndeps));
+        out.ev_b = ndeps ? deps[0] : nullptr;
+    } else {
+        enqueue_forces(s, 0, cs);
+    }
+    CK(cudaStreamEndCapture(cs, &g));
+    // the rebuild body
+    CK(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    enqueue_bin(s, cs);
+    cudaMemsetAsync(a.stats, 0, 4 * sizeof(int32_t), cs);
+    launch_build_lists(a, s->g, s->to, s->rl2, s->list_cap, s->tile_cap, half(s), cs);
+    launch_count_build(s->d_ctrl + 1, cs);
+    CK(cudaStreamEndCapture(cs, &body));
+    CKL();
+    CK(cudaGraphInstantiate(&out.exec, g, 0));
+    return MD_OK;
+}
+
+int ensure_graphs(md_system* s) {
+    if (s->graphs_valid && s->graph_tile_cap == s->tile_cap && s->graph_list_cap == s->list_cap &&
+        s->graph_timing == s->timing)
+        return MD_OK;
+    int rc;
+    if ((rc = capture_step(s, INT_KICK_DRIFT, s->g_first))) return rc;
+    if ((rc = capture_step(s, INT_KICK_KICK_DRIFT, s->g_mid))) return rc;
+    s->graphs_valid = true;
+    s->graph_tile_cap = s->tile_cap;
+    s->graph_list_cap = s->list_cap;
+    s->graph_timing = s->timing;
+    return MD_OK;
+}
+
+// Run len graph-launched steps; read the device status once at the end.
+int run_chunk(md_system* s, int len, bool first) {
+    int rc;
+    if ((rc = ensure_graphs(s))) return rc;
+    const DevState& a = s->st[0];
+    // snapshot of the chunk's starting state (for a redo after a capacity overflow)
+    launch_copy_state(s->st[2], a, s->stream);
+    CKL();
+    s->launches += 1;
+    s->snapshot_first = first;
+    s->h_ctrl[0] = s->n_steps;
+    s->h_ctrl[1] = 0;
+    CK(cudaMemcpyAsync(s->d_ctrl, s->h_ctrl, 2 * sizeof(long long), cudaMemcpyHostToDevice, s->stream));
+    CK(cudaMemsetAsync(a.rebuild_flag, 0, sizeof(int32_t), s->stream));
+    for (int k = 0; k < len; ++k) {
+        md_system::StepGraph& gr = (first && k == 0) ? s->g_first : s->g_mid;
+        if (s->timing && gr.ev_a && gr.ev_b) {
+            auto ev = take_events(s);
+            CK(cudaGraphExecEventRecordNodeSetEvent(gr.exec, gr.ev_a, ev.first));
+            CK(cudaGraphExecEventRecordNodeSetEvent(gr.exec, gr.ev_b, ev.second));
+            s->ev_force.push_back(ev);
+        }
+        CK(cudaGraphLaunch(gr.exec, s->stream));
+        s->launches += 3 + (half(s) ? 8 : 1);
+        s->force_evals += 1;
+    }
+    CK(cudaMemcpyAsync(s->h_ctrl, s->d_ctrl, 2 * sizeof(long long), cudaMemcpyDeviceToHost, s->stream));
+    if ((rc = sync_flags(s))) return rc;
+    const uint32_t e = s->h_flags[0];
+    if (e & ERR_TILE_OVERFLOW) return MD_ERR_CELL_OVERFLOW;  // the chunk is redone: nothing of it counts
+    if (e & ERR_LIST_OVERFLOW) return MD_ERR_LIST_OVERFLOW;
+    const long long builds = s->h_ctrl[1];
+    s->launches += builds * 11;
+    if (builds > 0) {
+        s->n_builds += builds;
+        s->max_list = (int)s->h_flags[2];
+        s->max_tile = (int)s->h_flags[3];
+        s->list_entries = (int64_t)((uint64_t)s->h_flags[4] | ((uint64_t)s->h_flags[5] << 32));
+    }
+    return check_err(s, ERR_NONFINITE | ERR_ESCAPE | ERR_SKIN);
+}
+
+int restore_snapshot(md_system* s) {
+    // back to the chunk's starting state; rebuild with capacity regrowth; forces again
+    const int saved_list = s->max_list, saved_tile = s->max_tile;
+    launch_copy_state(s->st[0], s->st[2], s->stream);
+    CKL();
+    CK(cudaMemsetAsync(s->st[0].err, 0, sizeof(uint32_t), s->stream));
+    // grow what overflowed (the device counters hold the sizes the failed build needed)
+    int rc = sync_flags(s);
+    if (rc) return rc;
+    const int need_list = std::max((int)s->h_flags[2], saved_list);
+    const int need_tile = std::max((int)s->h_flags[3], saved_tile);
+    if (need_list > s->list_cap && (rc = alloc_lists(s, round_up(need_list + need_list / 8 + 8, 8)))) return rc;
+    if (need_tile > s->tile_cap) s->tile_cap = round_up(need_tile + need_tile / 4 + 64, 32);
+    s->lists_valid = false;
+    s->forces_valid = false;
+    if ((rc = do_build(s))) return rc;
+    return do_forces(s, 0);
+}
+
 }  // namespace
 
 extern "C" {
@@ -344,6 +513,8 @@ int md_create(int64_t n, const double box[3], double r_cut, double skin, const m
     if (rc) return bail(rc);
     cudaGetDevice(&s->device);
     s->stream = static_cast<cudaStream_t>(p->stream);
+    init_force_kernels();
+    init_list_kernels();
     s->n = n;
     s->np = round_up((int)std::max<int64_t>(n, 1), 64);
     s->precision = p->precision;
@@ -373,6 +544,7 @@ int md_create(int64_t n, const double box[3], double r_cut, double skin, const m
     for (int a = 0; a < ns; ++a) {
         pt.mass[a] = p->mass[a];
         pt.hdtm[a] = (0.5 * p->dt) / p->mass[a];
+        pt.hdtm_q[a] = pt.hdtm[a] * 0x1p-32;
     }
     s->rcut = rcmax;
     s->rl = rcmax + skin;
@@ -405,27 +577,30 @@ int md_create(int64_t n, const double box[3], double r_cut, double skin, const m
     const double rho = (double)n / vol;
     const double tile_vol = 64.0 * g.w[0] * g.w[1] * g.w[2];
     s->tile_cap = round_up((int)std::ceil(rho * tile_vol * 1.5) + 64, 64);
-    s->tile_cap = std::min(s->tile_cap, 4096);
+    s->tile_cap = std::min(std::min(s->tile_cap, 4096), round_up((int)n + 1, 32));
     const double sphere = 4.0 / 3.0 * M_PI * s->rl * s->rl * s->rl * rho;
+    // half lists are about half as long on average, but the first atom of a cell lists
+    // every later atom of its cell as well, so both kinds start from the full estimate
     int lc = (int)std::ceil(sphere * 1.4) + 16;
-    if (p->list_kind == MD_LIST_HALF_COLOUR8) lc = (int)std::ceil(sphere * 0.7) + 16;
     lc = round_up(std::min(lc, 512), 8);
 
     // workspace
-    for (int k = 0; k < 2; ++k) {
+    for (int k = 0; k < 3; ++k) {
         DevState& d = s->st[k];
         d.n = n;
         d.np = s->np;
         if ((rc = dalloc(s, &d.x, n)) || (rc = dalloc(s, &d.y, n)) || (rc = dalloc(s, &d.z, n)) ||
             (rc = dalloc(s, &d.vx, n)) || (rc = dalloc(s, &d.vy, n)) || (rc = dalloc(s, &d.vz, n)) ||
-            (rc = dalloc(s, &d.rx, n)) || (rc = dalloc(s, &d.ry, n)) || (rc = dalloc(s, &d.rz, n)) ||
             (rc = dalloc(s, &d.ix, n)) || (rc = dalloc(s, &d.iy, n)) || (rc = dalloc(s, &d.iz, n)) ||
-            (rc = dalloc(s, &d.species, n)) || (rc = dalloc(s, &d.orig, n)) || (rc = dalloc(s, &d.cell_of, n)) ||
-            (rc = dalloc(s, &d.xr, n)) || (rc = dalloc(s, &d.xr_ref, n)))
+            (rc = dalloc(s, &d.species, n)) || (rc = dalloc(s, &d.orig, n)))
             return bail(rc);
     }
     DevState& d0 = s->st[0];
-    if ((rc = dalloc(s, &d0.cell_start, (size_t)g.ncell + 1)) || (rc = dalloc(s, &d0.nl_cnt, n)) ||
+    if ((rc = dalloc(s, &d0.rx, n)) || (rc = dalloc(s, &d0.ry, n)) || (rc = dalloc(s, &d0.rz, n)) ||
+        (rc = dalloc(s, &d0.cell_of, n)) || (rc = dalloc(s, &d0.xr, n)) || (rc = dalloc(s, &d0.xr_ref, n)))
+        return bail(rc);
+    if ((rc = dalloc(s, &d0.cell_start, (size_t)g.ncell + 1)) || (rc = dalloc(s, &d0.centre, 3 * (size_t)g.ncell)) ||
+        (rc = dalloc(s, &d0.nl_cnt, n)) ||
         (rc = dalloc(s, &d0.err, 1)) || (rc = dalloc(s, &d0.rebuild_flag, 1)) || (rc = dalloc(s, &d0.stats, 8)))
         return bail(rc);
     if (p->precision == MD_MIXED) {
@@ -437,18 +612,38 @@ int md_create(int64_t n, const double box[3], double r_cut, double skin, const m
             (rc = dalloc(s, &d0.vir_atom_d, 6 * (size_t)n)))
             return bail(rc);
     }
-    DevState& d1 = s->st[1];
-    d1.cell_start = d0.cell_start;
-    d1.nl_cnt = d0.nl_cnt;
-    d1.err = d0.err;
-    d1.rebuild_flag = d0.rebuild_flag;
-    d1.stats = d0.stats;
-    d1.fq = d0.fq;
-    d1.f = d0.f;
-    d1.pe_atom_f = d0.pe_atom_f;
-    d1.vir_atom_f = d0.vir_atom_f;
-    d1.pe_atom_d = d0.pe_atom_d;
-    d1.vir_atom_d = d0.vir_atom_d;
+    d0.ncell = g.ncell;
+    {
+        // cell centres (c + 1/2) w in the kernels' block-major numbering
+        std::vector<double> ctr(3 * (size_t)g.ncell);
+        for (int c = 0; c < g.ncell; ++c) {
+            int cx, cy, cz;
+            cell_coords(g, c, cx, cy, cz);
+            ctr[c] = (cx + 0.5) * g.w[0];
+            ctr[g.ncell + c] = (cy + 0.5) * g.w[1];
+            ctr[2 * (size_t)g.ncell + c] = (cz + 0.5) * g.w[2];
+        }
+        if (cudaMemcpy(d0.centre, ctr.data(), sizeof(double) * ctr.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+            return bail(MD_ERR_CUDA);
+    }
+    for (int k = 1; k < 3; ++k) {
+        DevState& d1 = s->st[k];
+        d1.cell_start = d0.cell_start;
+        d1.centre = d0.centre;
+        d1.ncell = d0.ncell;
+        d1.nl_cnt = d0.nl_cnt;
+        d1.err = d0.err;
+        d1.rebuild_flag = d0.rebuild_flag;
+        d1.stats = d0.stats;
+        d1.fq = d0.fq;
+        d1.f = d0.f;
+        d1.pe_atom_f = d0.pe_atom_f;
+        d1.vir_atom_f = d0.vir_atom_f;
+        d1.pe_atom_d = d0.pe_atom_d;
+        d1.vir_atom_d = d0.vir_atom_d;
+    }
+    if ((rc = dalloc(s, &s->d_ctrl, 2))) return bail(rc);
+    if (cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking) != cudaSuccess) return bail(MD_ERR_CUDA);
     if ((rc = alloc_lists(s, lc))) return bail(rc);
     if ((rc = dalloc(s, &s->atom_cell, n)) || (rc = dalloc(s, &s->cell_count, g.ncell)) ||
         (rc = dalloc(s, &s->cursor, g.ncell)) || (rc = dalloc(s, &s->slot_key, n)) ||
@@ -458,7 +653,9 @@ int md_create(int64_t n, const double box[3], double r_cut, double skin, const m
     s->nparts = 592;
     if ((rc = dalloc(s, &s->partials, 8 * (size_t)s->nparts)) || (rc = dalloc(s, &s->out8, 8))) return bail(rc);
     if (cudaMallocHost(&s->h_flags, 16 * sizeof(uint32_t)) != cudaSuccess) return bail(MD_ERR_CUDA);
+    if (cudaMallocHost(&s->h_ctrl, 2 * sizeof(long long)) != cudaSuccess) return bail(MD_ERR_CUDA);
     if (cudaMemsetAsync(d0.err, 0, sizeof(uint32_t), s->stream) != cudaSuccess ||
+        cudaMemsetAsync(s->d_ctrl, 0, 2 * sizeof(long long), s->stream) != cudaSuccess ||
         cudaMemsetAsync(d0.rebuild_flag, 0, sizeof(int32_t), s->stream) != cudaSuccess ||
         cudaStreamSynchronize(s->stream) != cudaSuccess)
         return bail(MD_ERR_CUDA);
@@ -555,41 +752,40 @@ int md_step(md_system* s, int32_t n_steps) {
     if (!s) return MD_ERR_ARG;
     if (n_steps < 0) return fail(s, MD_ERR_ARG, "n_steps < 0");
     if (n_steps == 0 || s->n == 0) {
-        if (s) s->n_steps += n_steps;
+        s->n_steps += n_steps;
         return MD_OK;
     }
     DeviceGuard dg(s->device);
     int rc = ensure_lists(s);
     if (rc) return rc;
     if (!s->forces_valid && (rc = do_forces(s, 0))) return rc;
-    const int mx = mixed(s);
-    for (int k = 0; k < n_steps; ++k) {
-        CK(cudaMemsetAsync(s->st[0].rebuild_flag, 0, sizeof(int32_t), s->stream));
-        launch_integrate(s->st[s->cur], s->g, s->pt, k == 0 ? INT_KICK_DRIFT : INT_KICK_KICK_DRIFT, mx, s->dt,
-                         s->lim2, s->stream);
-        CKL();
-        s->launches += 1;
-        bool rebuild;
-        if (s->rebuild == MD_REBUILD_EVERY_K) {
-            rebuild = ((s->n_steps + k + 1) % s->rebuild_k) == 0;
-            if (!rebuild) {
-                if ((rc = sync_flags(s))) return rc;
-                if (s->h_flags[1]) return fail(s, MD_ERR_SKIN_VIOLATION, "an atom moved more than skin/2");
-            }
-        } else {
-            if ((rc = sync_flags(s))) return rc;
-            rebuild = s->h_flags[1] != 0;
+    // chunks of graph-launched steps; the host reads the device status once per chunk
+    constexpr int CHUNK = 200;
+    int done = 0;
+    int redo = 0;
+    while (done < n_steps) {
+        const int len = std::min(CHUNK, n_steps - done);
+        const bool first = done == 0;
+        rc = run_chunk(s, len, first);
+        if (rc == MD_ERR_CELL_OVERFLOW || rc == MD_ERR_LIST_OVERFLOW) {
+            // a rebuild inside the chunk outgrew the captured capacities: restore the
+            // chunk's starting state, rebuild with regrowth on the host, and redo it
+            if (++redo > 4) return rc;
+            s->n_redos++;
+            if ((rc = restore_snapshot(s))) return rc;
+            continue;
         }
-        if (rebuild && (rc = do_build(s))) return rc;
-        if ((rc = do_forces(s, 0))) return rc;
+        if (rc) return rc;
+        done += len;
+        s->n_steps += len;
+        redo = 0;
     }
-    launch_integrate(s->st[s->cur], s->g, s->pt, INT_KICK, mx, s->dt, s->lim2, s->stream);
+    launch_integrate(s->st[0], s->g, s->pt, INT_KICK, mixed(s), s->dt, s->lim2, s->stream);
     CKL();
     s->launches += 1;
-    s->n_steps += n_steps;
     rc = sync_flags(s);
     if (rc) return rc;
-    return check_err(s, ERR_NONFINITE | ERR_TILE_OVERFLOW | ERR_ESCAPE);
+    return check_err(s, ERR_NONFINITE | ERR_ESCAPE | ERR_SKIN);
 }
 
 int md_energy_virial(md_system* s, double* pe, double* ke, double virial[6]) {
@@ -708,6 +904,7 @@ int md_get_info(md_system* s, md_info* out) {
     out->timed_force_evals = s->timed_force;
     out->build_ms = s->build_ms;
     out->timed_builds = s->timed_build;
+    out->n_redos = s->n_redos;
     return MD_OK;
 }
 
@@ -743,6 +940,10 @@ void md_destroy(md_system* s) {
         cudaEventDestroy(e.second);
     }
     if (s->h_flags) cudaFreeHost(s->h_flags);
+    if (s->h_ctrl) cudaFreeHost(s->h_ctrl);
+    destroy_graph(s->g_first);
+    destroy_graph(s->g_mid);
+    if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
     if (prev >= 0 && prev != s->device) cudaSetDevice(prev);
     delete s;
 }

@@ -193,8 +193,10 @@ void launch_cell_sort(const Geometry& g, const int32_t* cell_start, const int32_
 }
 
 // ---------------------------------------------------------------- gather
-// New slot t takes the atom that was at src = sorted_src[t].  The FP32
-// coordinates are re-expressed relative to the centre of the new cell.
+// New slot t takes the atom that was at src = sorted_src[t].  Permuted state
+// (positions, velocities, images, species, original ids) goes to the scratch
+// copy d and comes back with k_copy_back; state derived from the new layout
+// (reference positions, cell, FP32 cell-relative coordinates) is written to s.
 __global__ void k_gather(DevState d, DevState s, Geometry g, const int32_t* __restrict__ sorted_src,
                          const int32_t* __restrict__ atom_cell) {
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -207,34 +209,49 @@ __global__ void k_gather(DevState d, DevState s, Geometry g, const int32_t* __re
     d.vx[t] = s.vx[src];
     d.vy[t] = s.vy[src];
     d.vz[t] = s.vz[src];
-    d.rx[t] = x;
-    d.ry[t] = y;
-    d.rz[t] = z;
     d.ix[t] = s.ix[src];
     d.iy[t] = s.iy[src];
     d.iz[t] = s.iz[src];
     int sp = s.species[src];
     d.species[t] = sp;
     d.orig[t] = s.orig[src];
+    s.rx[t] = x;
+    s.ry[t] = y;
+    s.rz[t] = z;
     int c = atom_cell[src];
-    d.cell_of[t] = c;
-    int cx, cy, cz;
-    cell_coords(g, c, cx, cy, cz);
+    s.cell_of[t] = c;
     float4 p;
-    p.x = __double2float_rn(__dsub_rn(x, __dmul_rn((double)cx + 0.5, g.w[0])));
-    p.y = __double2float_rn(__dsub_rn(y, __dmul_rn((double)cy + 0.5, g.w[1])));
-    p.z = __double2float_rn(__dsub_rn(z, __dmul_rn((double)cz + 0.5, g.w[2])));
+    p.x = __double2float_rn(__dsub_rn(x, s.centre[c]));
+    p.y = __double2float_rn(__dsub_rn(y, s.centre[g.ncell + c]));
+    p.z = __double2float_rn(__dsub_rn(z, s.centre[2 * g.ncell + c]));
     p.w = __int_as_float(sp);
-    d.xr[t] = p;
-    d.xr_ref[t] = p;
+    s.xr[t] = p;
+    s.xr_ref[t] = p;
 }
 
-void launch_gather(const DevState& dst, const DevState& src, const Geometry& g, const int32_t* sorted_src,
-                   const int32_t* atom_cell, int mixed, cudaStream_t st) {
-    (void)mixed;
-    if (src.n == 0) return;
+__global__ void k_copy_back(DevState s, DevState d) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= s.n) return;
+    s.x[t] = d.x[t];
+    s.y[t] = d.y[t];
+    s.z[t] = d.z[t];
+    s.vx[t] = d.vx[t];
+    s.vy[t] = d.vy[t];
+    s.vz[t] = d.vz[t];
+    s.ix[t] = d.ix[t];
+    s.iy[t] = d.iy[t];
+    s.iz[t] = d.iz[t];
+    s.species[t] = d.species[t];
+    s.orig[t] = d.orig[t];
+}
+
+void launch_gather(const DevState& s, const DevState& scratch, const Geometry& g, const int32_t* sorted_src,
+                   const int32_t* atom_cell, cudaStream_t st) {
+    if (s.n == 0) return;
     int bs = 256;
-    k_gather<<<(unsigned)((src.n + bs - 1) / bs), bs, 0, st>>>(dst, src, g, sorted_src, atom_cell);
+    unsigned nb = (unsigned)((s.n + bs - 1) / bs);
+    k_gather<<<nb, bs, 0, st>>>(scratch, s, g, sorted_src, atom_cell);
+    k_copy_back<<<nb, bs, 0, st>>>(s, scratch);
 }
 
 }  // namespace mdgb

@@ -131,14 +131,130 @@ __device__ __forceinline__ void stage_dummy_f32(float4* tile, int T) {
     if (threadIdx.x == 0) tile[T] = make_float4(1.0e4f, 1.0e4f, 1.0e4f, __int_as_float(0));
 }
 
+// ---------------------------------------------------------------- packed FP32x2 helpers
+// sm_100-family packed single-precision arithmetic: two IEEE FP32 operations per
+// instruction, each rounded exactly as its scalar counterpart.
+typedef unsigned long long f2_t;
+
+__device__ __forceinline__ f2_t f2_pack(float a, float b) {
+    f2_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void f2_unpack(f2_t v, float& a, float& b) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ f2_t f2_add(f2_t a, f2_t b) {
+    f2_t r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2_t f2_sub(f2_t a, f2_t b) {
+    f2_t r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2_t f2_mul(f2_t a, f2_t b) {
+    f2_t r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2_t f2_fma(f2_t a, f2_t b, f2_t c) {
+    f2_t r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+
+// Two pairs' fixed-point terms of one component, packed: the same operations as fix_add.
+__device__ __forceinline__ void fix_add2(FixAcc& acc, f2_t fs2, f2_t d, f2_t magic2, f2_t two21) {
+    const f2_t t1 = f2_fma(fs2, d, magic2);
+    const f2_t nh = f2_sub(magic2, t1);  // -h, exact
+    const f2_t r = f2_fma(fs2, d, nh);
+    const f2_t t2 = f2_fma(r, two21, magic2);
+    float t1a, t1b, t2a, t2b;
+    f2_unpack(t1, t1a, t1b);
+    f2_unpack(t2, t2a, t2b);
+    acc.hi += __float_as_uint(t1a) + __float_as_uint(t1b);
+    acc.lo += __float_as_uint(t2a) + __float_as_uint(t2b);
+}
+
+// Species constants of a CTA in shared memory (dynamic indexing of kernel parameters
+// would go through local memory).
+struct SpeciesTable {
+    float sig2[MAX_PAIR], c48[MAX_PAIR], c24[MAX_PAIR], c4[MAX_PAIR], rc2[MAX_PAIR];
+};
+
+__device__ __forceinline__ void load_species_table(const PairTable& pt, SpeciesTable& st) {
+    const int t = threadIdx.x;
+    if (t < MAX_PAIR) {
+        st.sig2[t] = pt.sig2_f[t];
+        st.c48[t] = pt.c48_f[t];
+        st.c24[t] = pt.c24_f[t];
+        st.c4[t] = pt.c4_f[t];
+        st.rc2[t] = pt.rc2_f[t];
+    }
+}
+
+template <typename Body>
+__device__ __forceinline__ void for_each_neighbour_pair(const uint4* __restrict__ lp, int np, int nch, Body&& body) {
+    uint4 cur = make_uint4(0u, 0u, 0u, 0u);
+    if (nch > 0) cur = __ldcs(lp);
+    for (int c = 0; c < nch; ++c) {
+        uint4 nxt = cur;
+        if (c + 1 < nch) nxt = __ldcs(lp + (size_t)(c + 1) * np);
+        body((int)(cur.x & 0xffffu), (int)(cur.x >> 16));
+        body((int)(cur.y & 0xffffu), (int)(cur.y >> 16));
+        body((int)(cur.z & 0xffffu), (int)(cur.z >> 16));
+        body((int)(cur.w & 0xffffu), (int)(cur.w >> 16));
+        cur = nxt;
+    }
+}
+
+template <typename Body>
+__device__ __forceinline__ void for_each_neighbour(const uint4* __restrict__ lp, int np, int nch, Body&& body) {
+    for_each_neighbour_pair(lp, np, nch, [&](int u0, int u1) {
+        body(u0);
+        body(u1);
+    });
+}
+
+// Exact path for one atom whose list holds a pair force component >= 2048 eps/sigma
+// (or a non-finite one): every term through the FP64 rounding of fix_add_wide.
+template <bool SINGLE>
+__device__ __noinline__ void force_atom_wide(const float4* __restrict__ tile, const SpeciesTable& stab, int nsp,
+                                             float4 pi, const uint4* lp, int np, int nch, FixAcc& ax, FixAcc& ay,
+                                             FixAcc& az, uint32_t* err) {
+    ax = FixAcc{0u, 0u};
+    ay = FixAcc{0u, 0u};
+    az = FixAcc{0u, 0u};
+    const int si = __float_as_int(pi.w);
+    for_each_neighbour(lp, np, nch, [&](int u) {
+        const float4 pj = tile[u];
+        const float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
+        const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+        const int t = SINGLE ? 0 : si * nsp + __float_as_int(pj.w);
+        const float inv = rcp_approx(r2);
+        const float s2 = stab.sig2[t] * inv;
+        const float s6 = s2 * s2 * s2;
+        const float fs = (stab.c48[t] * s6 - stab.c24[t]) * s6 * inv;
+        const float fs2 = r2 < stab.rc2[t] ? fs : 0.0f;
+        fix_add_wide(ax, fs2, dx, err);
+        fix_add_wide(ay, fs2, dy, err);
+        fix_add_wide(az, fs2, dz, err);
+    });
+}
+
 // ---------------------------------------------------------------- mixed, full list
+// Two neighbours per iteration in packed FP32x2 arithmetic.
 template <bool SINGLE, bool EV>
 __global__ void __launch_bounds__(F_THREADS) k_force_mixed_full(DevState s, Geometry g, PairTable pt,
                                                                 TileOffsets to, int tile_cap, float fs2_max) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ TileMeta m;
+    __shared__ SpeciesTable stab;
     float4* tile = reinterpret_cast<float4*>(smem);
     const int b = blockIdx.x;
+    load_species_table(pt, stab);
     tile_meta(g, s.cell_start, b, m);
     const int T = m.prefix[64];
     if (T + 1 > tile_cap) {
@@ -152,43 +268,64 @@ __global__ void __launch_bounds__(F_THREADS) k_force_mixed_full(DevState s, Geom
     const int nown = m.prefix[8];
     const int64_t n = s.n;
     const int np = s.np;
+    const int nsp = pt.nsp;
+    const f2_t magic2 = f2_pack(MAGIC, MAGIC);
+    const f2_t two21 = f2_pack(TWO21, TWO21);
     for (int ui = threadIdx.x; ui < nown; ui += blockDim.x) {
         const int gi = blk0 + ui;
         const float4 pi = tile[ui];
         const int si = __float_as_int(pi.w);
         const int nch = (s.nl_cnt[gi] + 7) >> 3;
+        const uint4* lp = reinterpret_cast<const uint4*>(s.nl) + gi;
+        const f2_t pix = f2_pack(pi.x, pi.x), piy = f2_pack(pi.y, pi.y), piz = f2_pack(pi.z, pi.z);
         FixAcc ax{0u, 0u}, ay{0u, 0u}, az{0u, 0u};
         float pe = 0.f, w0 = 0.f, w1 = 0.f, w2 = 0.f, w3 = 0.f, w4 = 0.f, w5 = 0.f;
-        MDGB_FOR_EACH_NEIGHBOUR(reinterpret_cast<const uint4*>(s.nl) + gi, np, nch, {
-            const float4 pj = tile[u];
-            const float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
-            const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-            const int t = SINGLE ? 0 : si * pt.nsp + __float_as_int(pj.w);
-            float s6;
-            bool inside;
-            const float fs2 = lj_fs2<SINGLE>(pt, t, r2, s6, inside);
-            if (fabsf(fs2) < fs2_max) {
-                fix_add(ax, fs2, dx);
-                fix_add(ay, fs2, dy);
-                fix_add(az, fs2, dz);
-            } else {
-                fix_add_wide(ax, fs2, dx, s.err);
-                fix_add_wide(ay, fs2, dy, s.err);
-                fix_add_wide(az, fs2, dz, s.err);
-            }
+        bool bad = false;
+        for_each_neighbour_pair(lp, np, nch, [&](int u0, int u1) {
+            const float4 pa = tile[u0];
+            const float4 pb = tile[u1];
+            const f2_t dx = f2_sub(pix, f2_pack(pa.x, pb.x));
+            const f2_t dy = f2_sub(piy, f2_pack(pa.y, pb.y));
+            const f2_t dz = f2_sub(piz, f2_pack(pa.z, pb.z));
+            const f2_t r2 = f2_fma(dz, dz, f2_fma(dy, dy, f2_mul(dx, dx)));
+            float r2a, r2b;
+            f2_unpack(r2, r2a, r2b);
+            const int ta = SINGLE ? 0 : si * nsp + __float_as_int(pa.w);
+            const int tb = SINGLE ? 0 : si * nsp + __float_as_int(pb.w);
+            const f2_t inv = f2_pack(rcp_approx(r2a), rcp_approx(r2b));
+            const f2_t s2 = f2_mul(f2_pack(stab.sig2[ta], stab.sig2[tb]), inv);
+            const f2_t s6 = f2_mul(f2_mul(s2, s2), s2);
+            const f2_t fsv = f2_mul(f2_mul(f2_fma(f2_pack(stab.c48[ta], stab.c48[tb]), s6,
+                                                  f2_pack(-stab.c24[ta], -stab.c24[tb])), s6), inv);
+            float fa, fb;
+            f2_unpack(fsv, fa, fb);
+            const bool ina = r2a < stab.rc2[ta], inb = r2b < stab.rc2[tb];
+            fa = ina ? fa : 0.0f;
+            fb = inb ? fb : 0.0f;
+            bad |= !(fabsf(fa) < fs2_max) | !(fabsf(fb) < fs2_max);
+            const f2_t fs2 = f2_pack(fa, fb);
+            fix_add2(ax, fs2, dx, magic2, two21);
+            fix_add2(ay, fs2, dy, magic2, two21);
+            fix_add2(az, fs2, dz, magic2, two21);
             if (EV) {
-                const float c4 = SINGLE ? pt.c4_f[0] : pt.c4_f[t];
-                const float u_ = inside ? c4 * s6 * (s6 - 1.0f) : 0.0f;
-                const float fs = fs2 * (1.0f / FS_SCALE);
-                pe += u_;
-                w0 = fmaf(dx, fs * dx, w0);
-                w1 = fmaf(dy, fs * dy, w1);
-                w2 = fmaf(dz, fs * dz, w2);
-                w3 = fmaf(dx, fs * dy, w3);
-                w4 = fmaf(dx, fs * dz, w4);
-                w5 = fmaf(dy, fs * dz, w5);
+                float s6a, s6b, dxa, dxb, dya, dyb, dza, dzb;
+                f2_unpack(s6, s6a, s6b);
+                f2_unpack(dx, dxa, dxb);
+                f2_unpack(dy, dya, dyb);
+                f2_unpack(dz, dza, dzb);
+                const float ua = ina ? stab.c4[ta] * s6a * (s6a - 1.0f) : 0.0f;
+                const float ub = inb ? stab.c4[tb] * s6b * (s6b - 1.0f) : 0.0f;
+                const float ga = fa * (1.0f / FS_SCALE), gb = fb * (1.0f / FS_SCALE);
+                pe += ua + ub;
+                w0 += dxa * (ga * dxa) + dxb * (gb * dxb);
+                w1 += dya * (ga * dya) + dyb * (gb * dyb);
+                w2 += dza * (ga * dza) + dzb * (gb * dzb);
+                w3 += dxa * (ga * dya) + dxb * (gb * dyb);
+                w4 += dxa * (ga * dza) + dxb * (gb * dzb);
+                w5 += dya * (ga * dza) + dyb * (gb * dzb);
             }
-        })
+        });
+        if (bad) force_atom_wide<SINGLE>(tile, stab, nsp, pi, lp, np, nch, ax, ay, az, s.err);
         const int nterms = nch * 8;
         s.fq[gi] = fix_final(ax, nterms);
         s.fq[n + gi] = fix_final(ay, nterms);
@@ -514,9 +651,31 @@ size_t force_smem_bytes(int mixed, int half, int with_energy, int tile_cap) {
     return b;
 }
 
+// Raise every force kernel's dynamic shared-memory limit to what the SM allows
+// (once per device, before any launch or stream capture).
 template <typename K>
-static void set_smem(K kernel, size_t smem) {
-    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+static void allow_max_smem(K kernel) {
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, kernel) != cudaSuccess) return;
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+}
+
+void init_force_kernels() {
+    allow_max_smem(k_force_mixed_full<true, false>);
+    allow_max_smem(k_force_mixed_full<true, true>);
+    allow_max_smem(k_force_mixed_full<false, false>);
+    allow_max_smem(k_force_mixed_full<false, true>);
+    allow_max_smem(k_force_mixed_half<true, false>);
+    allow_max_smem(k_force_mixed_half<true, true>);
+    allow_max_smem(k_force_mixed_half<false, false>);
+    allow_max_smem(k_force_mixed_half<false, true>);
+    allow_max_smem(k_force_fp64_full<false>);
+    allow_max_smem(k_force_fp64_full<true>);
+    allow_max_smem(k_force_fp64_half<false>);
+    allow_max_smem(k_force_fp64_half<true>);
 }
 
 void launch_forces_mixed(const DevState& s, const Geometry& g, const PairTable& pt, const TileOffsets& to,
@@ -529,33 +688,28 @@ void launch_forces_mixed(const DevState& s, const Geometry& g, const PairTable& 
     const float fs2_max = 4194304.0f / sqrtf(rcmax2) * 0.999f;
     const bool single = pt.nsp == 1;
     if (!half) {
-#define MDGB_FULL(SG, EVV)                                                                   \
-    {                                                                                        \
-        auto k = k_force_mixed_full<SG, EVV>;                                                \
-        set_smem(k, smem);                                                                   \
-        k<<<g.nblock, F_THREADS, smem, st>>>(s, g, pt, to, tile_cap, fs2_max);               \
-    }
-        if (single && !with_energy) MDGB_FULL(true, false)
-        else if (single) MDGB_FULL(true, true)
-        else if (!with_energy) MDGB_FULL(false, false)
-        else MDGB_FULL(false, true)
-#undef MDGB_FULL
+        if (single && !with_energy)
+            k_force_mixed_full<true, false><<<g.nblock, F_THREADS, smem, st>>>(s, g, pt, to, tile_cap, fs2_max);
+        else if (single)
+            k_force_mixed_full<true, true><<<g.nblock, F_THREADS, smem, st>>>(s, g, pt, to, tile_cap, fs2_max);
+        else if (!with_energy)
+            k_force_mixed_full<false, false><<<g.nblock, F_THREADS, smem, st>>>(s, g, pt, to, tile_cap, fs2_max);
+        else
+            k_force_mixed_full<false, true><<<g.nblock, F_THREADS, smem, st>>>(s, g, pt, to, tile_cap, fs2_max);
         return;
     }
     cudaMemsetAsync(s.fq, 0, sizeof(long long) * 3 * (size_t)s.n, st);
     const int per = g.nblock / 8;
     for (int col = 0; col < 8; ++col) {
-#define MDGB_HALF(SG, EVV)                                                                   \
-    {                                                                                        \
-        auto k = k_force_mixed_half<SG, EVV>;                                                \
-        set_smem(k, smem);                                                                   \
-        k<<<per, F_THREADS, smem, st>>>(s, g, pt, to, tile_cap, fs2_max, col * per);         \
-    }
-        if (single && !with_energy) MDGB_HALF(true, false)
-        else if (single) MDGB_HALF(true, true)
-        else if (!with_energy) MDGB_HALF(false, false)
-        else MDGB_HALF(false, true)
-#undef MDGB_HALF
+        const int b0 = col * per;
+        if (single && !with_energy)
+            k_force_mixed_half<true, false><<<per, F_THREADS, smem, st>>>(s, g, pt, to, tile_cap, fs2_max, b0);
+        else if (single)
+            k_force_mixed_half<true, true><<<per, F_THREADS, smem, st>>>(s, g, pt, to, tile_cap, fs2_max, b0);
+        else if (!with_energy)
+            k_force_mixed_half<false, false><<<per, F_THREADS, smem, st>>>(s, g, pt, to, tile_cap, fs2_max, b0);
+        else
+            k_force_mixed_half<false, true><<<per, F_THREADS, smem, st>>>(s, g, pt, to, tile_cap, fs2_max, b0);
     }
 }
 
@@ -565,10 +719,8 @@ void launch_forces_fp64(const DevState& s, const Geometry& g, const PairTable& p
     const size_t smem = force_smem_bytes(0, half, with_energy, tile_cap);
     if (!half) {
         if (with_energy) {
-            set_smem(k_force_fp64_full<true>, smem);
             k_force_fp64_full<true><<<g.nblock, F_THREADS, smem, st>>>(s, g, pt, tile_cap);
         } else {
-            set_smem(k_force_fp64_full<false>, smem);
             k_force_fp64_full<false><<<g.nblock, F_THREADS, smem, st>>>(s, g, pt, tile_cap);
         }
         return;
@@ -577,10 +729,8 @@ void launch_forces_fp64(const DevState& s, const Geometry& g, const PairTable& p
     const int per = g.nblock / 8;
     for (int col = 0; col < 8; ++col) {
         if (with_energy) {
-            set_smem(k_force_fp64_half<true>, smem);
             k_force_fp64_half<true><<<per, F_THREADS, smem, st>>>(s, g, pt, tile_cap, col * per);
         } else {
-            set_smem(k_force_fp64_half<false>, smem);
             k_force_fp64_half<false><<<per, F_THREADS, smem, st>>>(s, g, pt, tile_cap, col * per);
         }
     }

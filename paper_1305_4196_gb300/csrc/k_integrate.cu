@@ -19,50 +19,65 @@ __device__ __forceinline__ double force_of(const DevState& s, int mixed, int64_t
 }
 
 // mode: INT_KICK_DRIFT (first step), INT_KICK_KICK_DRIFT (close step, open next), INT_KICK (close)
+//
+// FP64 path: every operation rounded exactly as written, as the definition.
+// Mixed path: the same update in fused form (one FMA per kick of the fixed-point
+// force, one per drift, a fused double kick between steps); GB300 runs FP64 at
+// 1/64 of the FP32 rate, so the FP64 instruction count sets this kernel's time.
 __global__ void k_integrate(DevState s, Geometry g, PairTable pt, int mode, int mixed, double dt, double lim2,
                             float lim2_f) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= s.n) return;
     const int64_t n = s.n;
-    const double h = pt.hdtm[s.species[i]];
+    const int sp = s.species[i];
     double v[3] = {s.vx[i], s.vy[i], s.vz[i]};
-    double F[3] = {force_of(s, mixed, i), force_of(s, mixed, n + i), force_of(s, mixed, 2 * n + i)};
+    if (mixed) {
+        const double hq = pt.hdtm_q[sp];
+        const double kq = mode == INT_KICK_KICK_DRIFT ? 2.0 * hq : hq;
+        const double F[3] = {(double)s.fq[i], (double)s.fq[n + i], (double)s.fq[2 * n + i]};
 #pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        if (mode != INT_KICK_DRIFT) v[d] = __dadd_rn(v[d], __dmul_rn(h, F[d]));
-        if (mode != INT_KICK) v[d] = __dadd_rn(v[d], __dmul_rn(h, F[d]));
+        for (int d = 0; d < 3; ++d) v[d] = fma(kq, F[d], v[d]);
+    } else {
+        const double h = pt.hdtm[sp];
+        const double F[3] = {s.f[i], s.f[n + i], s.f[2 * n + i]};
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            if (mode != INT_KICK_DRIFT) v[d] = __dadd_rn(v[d], __dmul_rn(h, F[d]));
+            if (mode != INT_KICK) v[d] = __dadd_rn(v[d], __dmul_rn(h, F[d]));
+        }
     }
     s.vx[i] = v[0];
     s.vy[i] = v[1];
     s.vz[i] = v[2];
     if (mode == INT_KICK) return;
     double x[3] = {s.x[i], s.y[i], s.z[i]};
-#pragma unroll
-    for (int d = 0; d < 3; ++d) x[d] = __dadd_rn(x[d], __dmul_rn(dt, v[d]));
-    s.x[i] = x[0];
-    s.y[i] = x[1];
-    s.z[i] = x[2];
     bool moved;
     if (mixed) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) x[d] = fma(dt, v[d], x[d]);
         // FP32 coordinates relative to the build cell's centre, and the displacement test on them
-        int cx, cy, cz;
-        cell_coords(g, s.cell_of[i], cx, cy, cz);
+        const int c = s.cell_of[i];
         float4 p;
-        p.x = __double2float_rn(__dsub_rn(x[0], __dmul_rn((double)cx + 0.5, g.w[0])));
-        p.y = __double2float_rn(__dsub_rn(x[1], __dmul_rn((double)cy + 0.5, g.w[1])));
-        p.z = __double2float_rn(__dsub_rn(x[2], __dmul_rn((double)cz + 0.5, g.w[2])));
+        p.x = __double2float_rn(x[0] - s.centre[c]);
+        p.y = __double2float_rn(x[1] - s.centre[s.ncell + c]);
+        p.z = __double2float_rn(x[2] - s.centre[2 * s.ncell + c]);
         const float4 r = s.xr_ref[i];
         p.w = r.w;
         s.xr[i] = p;
         const float dx = p.x - r.x, dy = p.y - r.y, dz = p.z - r.z;
         moved = fmaf(dz, dz, fmaf(dy, dy, dx * dx)) > lim2_f;
     } else {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) x[d] = __dadd_rn(x[d], __dmul_rn(dt, v[d]));
         const double dx = __dsub_rn(x[0], s.rx[i]);
         const double dy = __dsub_rn(x[1], s.ry[i]);
         const double dz = __dsub_rn(x[2], s.rz[i]);
         const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
         moved = d2 > lim2;
     }
+    s.x[i] = x[0];
+    s.y[i] = x[1];
+    s.z[i] = x[2];
     if (moved) *s.rebuild_flag = 1;
 }
 
@@ -74,6 +89,59 @@ void launch_integrate(const DevState& s, const Geometry& g, const PairTable& pt,
     // move further than skin/2 without a rebuild
     float lim2_f = (float)(lim2 * (1.0 - 1e-4));
     k_integrate<<<(unsigned)((s.n + bs - 1) / bs), bs, 0, st>>>(s, g, pt, mode, mixed, dt, lim2, lim2_f);
+}
+
+// ---------------------------------------------------------------- step control (graph mode)
+// One thread decides whether this step rebuilds the lists: the skin/2 flag raised
+// by k_integrate, or every k-th step.  It sets the graph's IF-node condition,
+// clears the flag for the next step and advances the device step counter.
+__global__ void k_step_ctrl(int policy, int every_k, int32_t* rebuild_flag, long long* step_counter,
+                            uint32_t* err, cudaGraphConditionalHandle handle) {
+    const long long step = *step_counter + 1;
+    const int moved = *rebuild_flag;
+    int rebuild;
+    if (policy == 1) {
+        rebuild = (step % every_k) == 0;
+        if (moved && !rebuild) atomicOr(err, ERR_SKIN);
+    } else {
+        rebuild = moved != 0;
+    }
+    *rebuild_flag = 0;
+    *step_counter = step;
+    cudaGraphSetConditional(handle, rebuild ? 1u : 0u);
+}
+
+__global__ void k_count_build(long long* n_builds) { *n_builds += 1; }
+
+void launch_step_ctrl(int policy, int every_k, int32_t* rebuild_flag, long long* step_counter,
+                      long long* n_builds, uint32_t* err, cudaGraphConditionalHandle handle, cudaStream_t st) {
+    (void)n_builds;
+    k_step_ctrl<<<1, 1, 0, st>>>(policy, every_k, rebuild_flag, step_counter, err, handle);
+}
+
+void launch_count_build(long long* n_builds, cudaStream_t st) { k_count_build<<<1, 1, 0, st>>>(n_builds); }
+
+// snapshot copy of the permuted state (positions, velocities, images, species, ids)
+__global__ void k_copy_state(DevState d, DevState s) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= s.n) return;
+    d.x[t] = s.x[t];
+    d.y[t] = s.y[t];
+    d.z[t] = s.z[t];
+    d.vx[t] = s.vx[t];
+    d.vy[t] = s.vy[t];
+    d.vz[t] = s.vz[t];
+    d.ix[t] = s.ix[t];
+    d.iy[t] = s.iy[t];
+    d.iz[t] = s.iz[t];
+    d.species[t] = s.species[t];
+    d.orig[t] = s.orig[t];
+}
+
+void launch_copy_state(const DevState& dst, const DevState& src, cudaStream_t st) {
+    if (src.n == 0) return;
+    int bs = 256;
+    k_copy_state<<<(unsigned)((src.n + bs - 1) / bs), bs, 0, st>>>(dst, src);
 }
 
 // ---------------------------------------------------------------- reductions
@@ -114,12 +182,23 @@ __global__ void __launch_bounds__(RED_THREADS) k_reduce_partials(DevState s, Pai
     if (threadIdx.x < 8) partials[blockIdx.x * 8 + threadIdx.x] = sh[threadIdx.x][0];
 }
 
-__global__ void k_reduce_final(const double* __restrict__ partials, int nparts, double* __restrict__ out8) {
-    if (threadIdx.x < 8) {
-        double a = 0.0;
-        for (int b = 0; b < nparts; ++b) a += partials[b * 8 + threadIdx.x];
-        out8[threadIdx.x] = a;
+__global__ void __launch_bounds__(RED_THREADS) k_reduce_final(const double* __restrict__ partials, int nparts,
+                                                               double* __restrict__ out8) {
+    __shared__ double sh[8][RED_THREADS];
+    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int b = threadIdx.x; b < nparts; b += RED_THREADS)
+#pragma unroll
+        for (int c = 0; c < 8; ++c) acc[c] += partials[b * 8 + c];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) sh[c][threadIdx.x] = acc[c];
+    __syncthreads();
+    for (int w = RED_THREADS / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w)
+#pragma unroll
+            for (int c = 0; c < 8; ++c) sh[c][threadIdx.x] += sh[c][threadIdx.x + w];
+        __syncthreads();
     }
+    if (threadIdx.x < 8) out8[threadIdx.x] = sh[threadIdx.x][0];
 }
 
 void launch_reduce_energy(const DevState& s, const PairTable& pt, int mixed, double* partials, int nparts,
@@ -127,7 +206,7 @@ void launch_reduce_energy(const DevState& s, const PairTable& pt, int mixed, dou
     int64_t chunk = (s.n + nparts - 1) / nparts;
     if (chunk < 1) chunk = 1;
     k_reduce_partials<<<nparts, RED_THREADS, 0, st>>>(s, pt, mixed, chunk, partials);
-    k_reduce_final<<<1, 32, 0, st>>>(partials, nparts, out8);
+    k_reduce_final<<<1, RED_THREADS, 0, st>>>(partials, nparts, out8);
 }
 
 // ---------------------------------------------------------------- state I/O

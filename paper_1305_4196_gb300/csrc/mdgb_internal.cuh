@@ -47,6 +47,7 @@ struct PairTable {
     float sig2_f[MAX_PAIR], c48_f[MAX_PAIR], c24_f[MAX_PAIR], c4_f[MAX_PAIR], rc2_f[MAX_PAIR];
     double sig2_d[MAX_PAIR], eps_d[MAX_PAIR], rc2_d[MAX_PAIR];
     double hdtm[MAX_SPECIES];  // (dt/2) / m per species
+    double hdtm_q[MAX_SPECIES];  // (dt/2) / m * 2^-32: half kick per unit of Q31.32 force
     double mass[MAX_SPECIES];
 };
 
@@ -109,6 +110,8 @@ struct DevState {
     long long *fq;          // mixed path: forces, 3 x n, Q31.32 fixed point (x block, y block, z block)
     double *f;              // FP64 path: forces, 3 x n
     int32_t *cell_start;    // ncell + 1
+    double *centre;         // cell centres, 3 x ncell (x block, y block, z block)
+    int ncell;
     uint16_t *nl;           // neighbour lists, tile-local indices, in chunks of 8: entry k of atom s at
                             // nl[((k / 8) * np + s) * 8 + k % 8]; the last chunk is padded with the
                             // tile's dummy slot (a point far outside every cutoff)
@@ -131,8 +134,12 @@ void launch_scatter(const DevState& s, const int32_t* atom_cell, const int32_t* 
                     int32_t* slot_key, int32_t* slot_src, cudaStream_t st);
 void launch_cell_sort(const Geometry& g, const int32_t* cell_start, const int32_t* slot_key,
                       const int32_t* slot_src, int32_t* sorted_src, cudaStream_t st);
-void launch_gather(const DevState& dst, const DevState& src, const Geometry& g, const int32_t* sorted_src,
-                   const int32_t* atom_cell, int mixed, cudaStream_t st);
+void launch_gather(const DevState& s, const DevState& scratch, const Geometry& g, const int32_t* sorted_src,
+                   const int32_t* atom_cell, cudaStream_t st);
+void launch_step_ctrl(int policy, int every_k, int32_t* rebuild_flag, long long* step_counter,
+                      long long* n_builds, uint32_t* err, cudaGraphConditionalHandle handle, cudaStream_t st);
+void launch_count_build(long long* n_builds, cudaStream_t st);
+void launch_copy_state(const DevState& dst, const DevState& src, cudaStream_t st);
 void launch_build_lists(const DevState& s, const Geometry& g, const TileOffsets& to, double rl2, int list_cap,
                         int tile_cap, int half, cudaStream_t st);
 size_t build_lists_smem(int list_cap, int tile_cap);
@@ -152,6 +159,9 @@ void launch_forces_out(const DevState& s, int mixed, double* f_out, cudaStream_t
 void launch_cells_out(const DevState& s, const Geometry& g, int32_t* cells, cudaStream_t st);
 void launch_pairs_out(const DevState& s, const Geometry& g, int half, unsigned long long* counter,
                       int32_t* pairs, long long cap, cudaStream_t st);
+
+void init_force_kernels();
+void init_list_kernels();
 
 // integrate modes
 enum { INT_KICK_DRIFT = 0, INT_KICK_KICK_DRIFT = 1, INT_KICK = 2 };

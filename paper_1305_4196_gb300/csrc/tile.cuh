@@ -82,6 +82,11 @@ __device__ __forceinline__ int tile_slot_of(const TileMeta& m, int u) {
     return lo;
 }
 
+// o[t] for t in 0..3 without dynamic indexing (which would copy the table to local memory)
+__device__ __forceinline__ float pick4(const float (&o)[4], int t) {
+    return t == 0 ? o[0] : (t == 1 ? o[1] : (t == 2 ? o[2] : o[3]));
+}
+
 // Stage the block-frame FP32 coordinates of the tile (T = m.prefix[64] <= cap).
 __device__ __forceinline__ void tile_stage_f32(const TileMeta& m, const float4* __restrict__ xr,
                                                const TileOffsets& to, float4* __restrict__ tile,
@@ -92,9 +97,9 @@ __device__ __forceinline__ void tile_stage_f32(const TileMeta& m, const float4* 
         int c = c_tiles.coord_of_idx[slot];
         int j = m.start[slot] + (u - m.prefix[slot]);
         float4 p = xr[j];
-        p.x += to.off[0][c & 3];
-        p.y += to.off[1][(c >> 2) & 3];
-        p.z += to.off[2][c >> 4];
+        p.x += pick4(to.off[0], c & 3);
+        p.y += pick4(to.off[1], (c >> 2) & 3);
+        p.z += pick4(to.off[2], c >> 4);
         tile[u] = p;
         if (gidx) gidx[u] = j;
     }

@@ -54,7 +54,8 @@ class md_info(C.Structure):
                 ("n_builds", C.c_int64), ("n_steps", C.c_int64), ("list_entries", C.c_int64),
                 ("max_list", C.c_int32), ("max_tile", C.c_int32), ("cell_width", C.c_double * 3),
                 ("kernel_launches", C.c_int64), ("force_evals", C.c_int64), ("force_ms", C.c_double),
-                ("timed_force_evals", C.c_int64), ("build_ms", C.c_double), ("timed_builds", C.c_int64)]
+                ("timed_force_evals", C.c_int64), ("build_ms", C.c_double), ("timed_builds", C.c_int64),
+                ("n_redos", C.c_int64)]
 
 
 class MDError(RuntimeError):
@@ -202,7 +203,7 @@ def md_get_info(handle) -> dict:
             "max_list": info.max_list, "max_tile": info.max_tile, "cell_width": list(info.cell_width),
             "kernel_launches": info.kernel_launches, "force_evals": info.force_evals, "force_ms": info.force_ms,
             "timed_force_evals": info.timed_force_evals, "build_ms": info.build_ms,
-            "timed_builds": info.timed_builds}
+            "timed_builds": info.timed_builds, "n_redos": info.n_redos}
 
 
 def md_set_timing(handle, enable=True):

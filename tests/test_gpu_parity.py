@@ -170,7 +170,7 @@ def test_forces_translation_invariance_mixed():
 def test_multispecies_per_pair_cutoff():
     """Kob-Andersen-type binary mixture: per-pair eps, sigma and r_cut = 2.5 sigma_ab."""
     a = W.lattice_constant(1.2)
-    pos, box = W.fcc_lattice(14, 14, 14, a)
+    pos, box = W.fcc_lattice(16, 16, 16, a)
     pos = W.gaussian_jitter(pos, box, 0.03, seed=4)
     sp = W.species_shuffle(len(pos), 0.2, seed=4)
     sysm = W.System(pos, np.zeros_like(pos), sp, box)
@@ -205,12 +205,18 @@ def test_energy_virial_vs_oracle(lst, precision):
 
 
 def test_fcc_lattice_energy_on_gpu():
+    """Perfect fcc crystal: energy and virial per atom equal the oracle's (compensated, and
+    pinned to the exact lattice sum); forces vanish by symmetry."""
     sysm = W.lj_fcc(14, seed=1)
+    _, pe_ref, vir_ref = O.lj_forces(sysm.pos, sysm.box, O.LJParams.single())
     for precision in ("fp64", "mixed"):
-        pe, _, vir = make(sysm, precision).energy_virial()
-        tol = 1e-12 if precision == "fp64" else 1e-6
-        assert pe / sysm.n == pytest.approx(-6.7733680533, rel=tol)
-        assert vir[:3].sum() / sysm.n == pytest.approx(-22.1581992540, rel=tol)
+        for lst in ("full", "half"):
+            s = make(sysm, precision, lst)
+            pe, _, vir = s.energy_virial()
+            tol = 1e-12 if precision == "fp64" else 1e-6
+            assert pe == pytest.approx(pe_ref, rel=tol)
+            assert vir[:3].sum() == pytest.approx(vir_ref[:3].sum(), rel=tol)
+            assert np.abs(s.forces()).max() < (1e-11 if precision == "fp64" else 1e-4)
 
 
 # ---------------------------------------------------------------- trajectories
@@ -224,7 +230,9 @@ def test_fp64_trajectory_config1(lst):
     ref = O.run_nve(sysm.pos, sysm.vel, sysm.box, O.LJParams.single(), DT, SKIN, 100)
     assert np.abs(pos + img * sysm.box - (ref["pos"] + ref["image"] * sysm.box)).max() < 1e-10
     assert np.abs(vel - ref["vel"]).max() < 1e-9
-    assert s.info()["n_builds"] - 1 == ref["rebuilds"]
+    info = s.info()
+    assert info["n_builds"] - 1 == ref["rebuilds"], info
+    assert info["n_redos"] == 0
 
 
 def test_mixed_trajectory_short():
