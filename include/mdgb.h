@@ -153,6 +153,10 @@ int md_forces(md_system *s, double *f_out, int device_ptrs);
  * once per chunk of up to 200 steps.  If a rebuild inside a chunk outgrows the
  * list or tile capacity, the chunk is redone from a snapshot of its starting
  * state after the capacities have been regrown (md_info.n_redos counts these).
+ * With the environment variable MDGB_NO_GRAPHS=1 set when the system is
+ * created, the same kernels are launched from the host instead and the rebuild
+ * flag is read after every step (slower; for profilers that do not follow
+ * kernels into conditional graph nodes).
  * Energies are not computed on the way (use md_energy_virial).
  * Errors: MD_ERR_NONFINITE, MD_ERR_SKIN_VIOLATION, overflow codes, MD_ERR_CUDA.
  */

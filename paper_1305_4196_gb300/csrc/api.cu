@@ -10,6 +10,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
@@ -56,6 +57,7 @@ struct md_system {
     bool graphs_valid = false;
     int graph_tile_cap = 0, graph_list_cap = 0;
     bool graph_timing = false;
+    bool use_graphs = true;  // MDGB_NO_GRAPHS=1 at md_create: host-launched steps (profilers see every kernel)
     long long* d_ctrl = nullptr;  // [0] step counter, [1] builds done inside graphs
     long long* h_ctrl = nullptr;  // pinned mirror
     bool snapshot_first = true;
@@ -232,8 +234,6 @@ int do_build(md_system* s) {
         DevState& a = s->st[s->cur];
         CK(cudaMemsetAsync(a.stats, 0, 4 * sizeof(int32_t), s->stream));
         CK(cudaMemsetAsync(a.err, 0, sizeof(uint32_t), s->stream));
-        if (build_lists_smem(s->list_cap, s->tile_cap) > 226 * 1024 && s->tile_cap > s->max_tile)
-            s->tile_cap = std::max(s->max_tile, round_up(s->max_tile + 1, 32));
         if (build_lists_smem(s->list_cap, s->tile_cap) > 226 * 1024)
             return fail(s, MD_ERR_CELL_OVERFLOW, "tile (%d atoms) and lists (%d) exceed shared memory",
                         s->tile_cap, s->list_cap);
@@ -251,8 +251,10 @@ int do_build(md_system* s) {
         const int max_list = (int)s->h_flags[2], max_tile = (int)s->h_flags[3];
         bool again = false;
         if (e & ERR_TILE_OVERFLOW) {
-            int cap = round_up(max_tile + max_tile / 4 + 64, 64);
-            if (cap > 65535) return fail(s, MD_ERR_CELL_OVERFLOW, "tile of %d atoms exceeds 16-bit indices", max_tile);
+            // a tile never holds more than all atoms plus the dummy slot
+            int cap = std::max(max_tile, std::min(round_up(max_tile + max_tile / 4 + 64, 32),
+                                                  round_up((int)s->n + 1, 32)));
+            if (cap > 32767) return fail(s, MD_ERR_CELL_OVERFLOW, "tile of %d atoms exceeds 15-bit indices", max_tile);
             s->tile_cap = cap;
             again = true;
         }
@@ -433,9 +435,35 @@ int ensure_graphs(md_system* s) {
     return MD_OK;
 }
 
+// The same step sequence launched from the host, reading the rebuild flag after every
+// step (for profilers, which do not see kernels inside conditional graph nodes).
+int run_steps_direct(md_system* s, int len, bool first) {
+    int rc;
+    const DevState& a = s->st[0];
+    for (int k = 0; k < len; ++k) {
+        CK(cudaMemsetAsync(a.rebuild_flag, 0, sizeof(int32_t), s->stream));
+        launch_integrate(a, s->g, s->pt, (first && k == 0) ? INT_KICK_DRIFT : INT_KICK_KICK_DRIFT, mixed(s), s->dt,
+                         s->lim2, s->stream);
+        CKL();
+        s->launches += 1;
+        if ((rc = sync_flags(s))) return rc;
+        const long long step = s->n_steps + k + 1;
+        bool rebuild = s->h_flags[1] != 0;
+        if (s->rebuild == MD_REBUILD_EVERY_K) {
+            const bool due = (step % s->rebuild_k) == 0;
+            if (rebuild && !due) return fail(s, MD_ERR_SKIN_VIOLATION, "an atom moved more than skin/2");
+            rebuild = due;
+        }
+        if (rebuild && (rc = do_build(s))) return rc;
+        if ((rc = do_forces(s, 0))) return rc;
+    }
+    return MD_OK;
+}
+
 // Run len graph-launched steps; read the device status once at the end.
 int run_chunk(md_system* s, int len, bool first) {
     int rc;
+    if (!s->use_graphs) return run_steps_direct(s, len, first);
     if ((rc = ensure_graphs(s))) return rc;
     const DevState& a = s->st[0];
     // snapshot of the chunk's starting state (for a redo after a capacity overflow)
@@ -515,6 +543,10 @@ int md_create(int64_t n, const double box[3], double r_cut, double skin, const m
     s->stream = static_cast<cudaStream_t>(p->stream);
     init_force_kernels();
     init_list_kernels();
+    {
+        const char* ng = std::getenv("MDGB_NO_GRAPHS");
+        s->use_graphs = !(ng && ng[0] && ng[0] != '0');
+    }
     s->n = n;
     s->np = round_up((int)std::max<int64_t>(n, 1), 64);
     s->precision = p->precision;
@@ -577,7 +609,7 @@ int md_create(int64_t n, const double box[3], double r_cut, double skin, const m
     const double rho = (double)n / vol;
     const double tile_vol = 64.0 * g.w[0] * g.w[1] * g.w[2];
     s->tile_cap = round_up((int)std::ceil(rho * tile_vol * 1.5) + 64, 64);
-    s->tile_cap = std::min(std::min(s->tile_cap, 4096), round_up((int)n + 1, 32));
+    s->tile_cap = std::min(s->tile_cap, round_up((int)n + 1, 32));
     const double sphere = 4.0 / 3.0 * M_PI * s->rl * s->rl * s->rl * rho;
     // half lists are about half as long on average, but the first atom of a cell lists
     // every later atom of its cell as well, so both kinds start from the full estimate

@@ -271,6 +271,10 @@ __global__ void __launch_bounds__(F_THREADS) k_force_mixed_full(DevState s, Geom
     const int nsp = pt.nsp;
     const f2_t magic2 = f2_pack(MAGIC, MAGIC);
     const f2_t two21 = f2_pack(TWO21, TWO21);
+    const f2_t sig2_1 = f2_pack(pt.sig2_f[0], pt.sig2_f[0]);
+    const f2_t c48_1 = f2_pack(pt.c48_f[0], pt.c48_f[0]);
+    const f2_t nc24_1 = f2_pack(-pt.c24_f[0], -pt.c24_f[0]);
+    const float rc2_1 = pt.rc2_f[0];
     for (int ui = threadIdx.x; ui < nown; ui += blockDim.x) {
         const int gi = blk0 + ui;
         const float4 pi = tile[ui];
@@ -293,13 +297,17 @@ __global__ void __launch_bounds__(F_THREADS) k_force_mixed_full(DevState s, Geom
             const int ta = SINGLE ? 0 : si * nsp + __float_as_int(pa.w);
             const int tb = SINGLE ? 0 : si * nsp + __float_as_int(pb.w);
             const f2_t inv = f2_pack(rcp_approx(r2a), rcp_approx(r2b));
-            const f2_t s2 = f2_mul(f2_pack(stab.sig2[ta], stab.sig2[tb]), inv);
+            // single species: the constants are kernel parameters (constant-bank operands)
+            const f2_t sig2 = SINGLE ? sig2_1 : f2_pack(stab.sig2[ta], stab.sig2[tb]);
+            const f2_t c48 = SINGLE ? c48_1 : f2_pack(stab.c48[ta], stab.c48[tb]);
+            const f2_t nc24 = SINGLE ? nc24_1 : f2_pack(-stab.c24[ta], -stab.c24[tb]);
+            const float rc2a = SINGLE ? rc2_1 : stab.rc2[ta], rc2b = SINGLE ? rc2_1 : stab.rc2[tb];
+            const f2_t s2 = f2_mul(sig2, inv);
             const f2_t s6 = f2_mul(f2_mul(s2, s2), s2);
-            const f2_t fsv = f2_mul(f2_mul(f2_fma(f2_pack(stab.c48[ta], stab.c48[tb]), s6,
-                                                  f2_pack(-stab.c24[ta], -stab.c24[tb])), s6), inv);
+            const f2_t fsv = f2_mul(f2_mul(f2_fma(c48, s6, nc24), s6), inv);
             float fa, fb;
             f2_unpack(fsv, fa, fb);
-            const bool ina = r2a < stab.rc2[ta], inb = r2b < stab.rc2[tb];
+            const bool ina = r2a < rc2a, inb = r2b < rc2b;
             fa = ina ? fa : 0.0f;
             fb = inb ? fb : 0.0f;
             bad |= !(fabsf(fa) < fs2_max) | !(fabsf(fb) < fs2_max);
@@ -313,8 +321,9 @@ __global__ void __launch_bounds__(F_THREADS) k_force_mixed_full(DevState s, Geom
                 f2_unpack(dx, dxa, dxb);
                 f2_unpack(dy, dya, dyb);
                 f2_unpack(dz, dza, dzb);
-                const float ua = ina ? stab.c4[ta] * s6a * (s6a - 1.0f) : 0.0f;
-                const float ub = inb ? stab.c4[tb] * s6b * (s6b - 1.0f) : 0.0f;
+                const float c4a = SINGLE ? pt.c4_f[0] : stab.c4[ta], c4b = SINGLE ? pt.c4_f[0] : stab.c4[tb];
+                const float ua = ina ? c4a * s6a * (s6a - 1.0f) : 0.0f;
+                const float ub = inb ? c4b * s6b * (s6b - 1.0f) : 0.0f;
                 const float ga = fa * (1.0f / FS_SCALE), gb = fb * (1.0f / FS_SCALE);
                 pe += ua + ub;
                 w0 += dxa * (ga * dxa) + dxb * (gb * dxb);

@@ -50,6 +50,11 @@ __device__ __forceinline__ f2_t f2_pack(float a, float b) {
 __device__ __forceinline__ void f2_unpack(f2_t v, float& a, float& b) {
     asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
 }
+__device__ __forceinline__ float pi_x(f2_t v) {
+    float a, b;
+    f2_unpack(v, a, b);
+    return a;
+}
 __device__ __forceinline__ f2_t f2_sub(f2_t a, f2_t b) {
     f2_t r;
     asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
@@ -66,82 +71,83 @@ __device__ __forceinline__ f2_t f2_fma(f2_t a, f2_t b, f2_t c) {
     return r;
 }
 
-// Per-warp list staging: each own atom of the warp has a 64-slot ring of list
-// entries in shared memory; whole chunks of 8 entries are flushed to the list
-// matrix as soon as they fill (chunk c of atom gi at uint4 index c * np + gi).
-constexpr int RING = 64;
-constexpr int WARP_ATOMS = 32;  // own atoms handled by one warp pass
+// Scan of one group of 32 consecutive tile candidates g0 .. g0+31 against a lane's
+// atom, two per step in packed FP32x2.  Candidate k of the group lands in bit
+// 31-k of the masks: `maybe` has r^2 <= band_hi (inside the list radius or in the
+// FP64 re-test band), `sure` has r^2 < band_lo (inside for certain).  Each bit is
+// the sign of r^2 - threshold shifted in, so a candidate costs one integer op on
+// top of its distance arithmetic.
+__device__ __forceinline__ void scan_group(const float4* __restrict__ tile, int g0, f2_t pix, f2_t piy, f2_t piz,
+                                           f2_t hi2, f2_t lo2, unsigned& maybe, unsigned& sure) {
+    unsigned mm = 0u, ms = 0u;
+#pragma unroll
+    for (int k = 0; k < 32; k += 2) {
+        const float4 pa = tile[g0 + k];
+        const float4 pb = tile[g0 + k + 1];
+        const f2_t dx = f2_sub(pix, f2_pack(pa.x, pb.x));
+        const f2_t dy = f2_sub(piy, f2_pack(pa.y, pb.y));
+        const f2_t dz = f2_sub(piz, f2_pack(pa.z, pb.z));
+        const f2_t r2 = f2_fma(dz, dz, f2_fma(dy, dy, f2_mul(dx, dx)));
+        float ha, hb, la, lb;
+        f2_unpack(f2_sub(r2, hi2), ha, hb);
+        f2_unpack(f2_sub(r2, lo2), la, lb);
+        mm = (mm << 1) | (__float_as_uint(ha) >> 31);
+        mm = (mm << 1) | (__float_as_uint(hb) >> 31);
+        ms = (ms << 1) | (__float_as_uint(la) >> 31);
+        ms = (ms << 1) | (__float_as_uint(lb) >> 31);
+    }
+    maybe = mm;
+    sure = ms;
+}
 
-// One neighbour cell (tile indices u0 .. u1-1) against the warp's own atoms
-// own_begin .. own_begin+na-1.  Lanes hold candidates; the warp steps through the
-// own atoms, and __ballot_sync / __popc turn each atom's accepted candidates into
-// consecutive list slots with no per-lane loop.  OWN marks the atoms' own cell,
-// where the atom itself (full lists) or every atom up to it (half lists) is excluded.
-// Candidates inside the FP64 re-test band are re-tested in the definition's order.
+// Candidates u0 .. u1-1 of one neighbour cell: scan in groups of 32, then append
+// the accepted ones to the lane's column of the list buffer in candidate order.
+// OWN marks the atom's own cell, where the atom itself (full lists) or every atom
+// up to it (half lists) is excluded.  Band candidates are re-tested in FP64.
 template <int HALF, bool OWN>
-__device__ __forceinline__ void scan_cell_ballot(const float4* __restrict__ tile, const int32_t* __restrict__ gidx,
-                                                 const DevState& s, const Geometry& g, double rl2, int u0, int u1,
-                                                 int own_begin, int na, int lane, float band_lo, float band_hi,
-                                                 uint16_t* __restrict__ ring, int* __restrict__ cnt_s,
-                                                 uint4* __restrict__ out0, int list_cap, int T) {
-    const unsigned lt = (1u << lane) - 1u;
+__device__ __forceinline__ void scan_cell(const float4* __restrict__ tile, const int32_t* __restrict__ gidx,
+                                          const DevState& s, const Geometry& g, double rl2, int u0, int u1, f2_t pix,
+                                          f2_t piy, f2_t piz, f2_t hi2, f2_t lo2, int ui, bool active,
+                                          uint16_t* __restrict__ col, int list_cap, int& cnt) {
     for (int g0 = u0; g0 < u1; g0 += 32) {
-        const int u = g0 + lane;
-        const bool valid = u < u1;
-        const float4 pj = tile[valid ? u : u0];
-        for (int a = 0; a < na; ++a) {
-            const int ui = own_begin + a;
-            const float4 pi = tile[ui];  // broadcast
-            const float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
-            const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-            bool maybe = valid && r2 <= band_hi;
-            if (OWN) maybe = maybe && (HALF ? u > ui : u != ui);
-            unsigned bm = __ballot_sync(0xffffffffu, maybe);
-            if (bm == 0u) continue;
-            const bool sure = r2 < band_lo;
-            if (__ballot_sync(0xffffffffu, maybe && !sure)) {
-                bool take = maybe && (sure || fp64_pair_test(s.x, s.y, s.z, g.L[0], g.L[1], g.L[2], gidx[ui],
-                                                            gidx[valid ? u : u0], rl2));
-                bm = __ballot_sync(0xffffffffu, take);
-                maybe = take;
+        unsigned mm, ms;
+        scan_group(tile, g0, pix, piy, piz, hi2, lo2, mm, ms);
+        const int nvalid = u1 - g0;
+        if (nvalid < 32) mm &= ~0u << (32 - nvalid);
+        if (OWN) {
+            const int rel = ui - g0;  // own atom's bit is 31 - rel
+            if (HALF) {
+                if (rel >= 31) mm = 0u;
+                else if (rel >= 0) mm &= ~0u >> (rel + 1);
+            } else if (rel >= 0 && rel < 32) {
+                mm &= ~(0x80000000u >> rel);
             }
-            const int c = cnt_s[a];
-            const int cn = c + __popc(bm);
-            uint16_t* r = ring + a * RING;
-            if (maybe) {
-                const int k = c + __popc(bm & lt);
-                if (k < list_cap) r[k & (RING - 1)] = (uint16_t)u;
+        }
+        if (!active) mm = 0u;
+        const unsigned band = mm & ~ms;
+        while (mm) {
+            const int k = __clz(mm);
+            const unsigned bit = 0x80000000u >> k;
+            mm &= ~bit;
+            const int u = g0 + k;
+            if (band & bit) {
+                if (!fp64_pair_test(s.x, s.y, s.z, g.L[0], g.L[1], g.L[2], gidx[ui], gidx[u], rl2)) continue;
             }
-            __syncwarp();
-            // flush the chunks this atom completed
-            const int f0 = c >> 3, f1 = (cn < list_cap ? cn : list_cap) >> 3;
-            if (lane < f1 - f0) {
-                const int ch = f0 + lane;
-                const uint16_t* q = r + ((ch * 8) & (RING - 1));
-                uint4 v;
-                v.x = q[0] | ((unsigned)q[1] << 16);
-                v.y = q[2] | ((unsigned)q[3] << 16);
-                v.z = q[4] | ((unsigned)q[5] << 16);
-                v.w = q[6] | ((unsigned)q[7] << 16);
-                out0[(size_t)ch * s.np + a] = v;
-            }
-            if (lane == 0) cnt_s[a] = cn;
-            __syncwarp();
+            if (cnt < list_cap) col[cnt * 32] = (uint16_t)u;
+            ++cnt;
         }
     }
-    (void)T;
 }
 
 template <int HALF>
 __global__ void __launch_bounds__(NL_WARPS * 32, 2) k_build_lists(DevState s, Geometry g, TileOffsets to,
-                                                               double rl2, float band_lo, float band_hi,
-                                                               int list_cap, int tile_cap) {
+                                                                  double rl2, float band_lo, float band_hi,
+                                                                  int list_cap, int tile_cap) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ TileMeta m;
-    float4* tile = reinterpret_cast<float4*>(smem);                    // tile_cap
-    int32_t* gidx = reinterpret_cast<int32_t*>(tile + tile_cap);       // tile_cap
-    int* cnt_all = reinterpret_cast<int*>(gidx + tile_cap);            // NL_WARPS x 32
-    uint16_t* ring_all = reinterpret_cast<uint16_t*>(cnt_all + NL_WARPS * WARP_ATOMS);  // NL_WARPS x 32 x RING
+    float4* tile = reinterpret_cast<float4*>(smem);                   // tile_cap + 32: groups read past T
+    int32_t* gidx = reinterpret_cast<int32_t*>(tile + tile_cap + 32);  // tile_cap
+    uint16_t* buf = reinterpret_cast<uint16_t*>(gidx + tile_cap);     // NL_WARPS x list_cap x 32
 
     const int b = blockIdx.x;
     tile_meta(g, s.cell_start, b, m);
@@ -152,54 +158,68 @@ __global__ void __launch_bounds__(NL_WARPS * 32, 2) k_build_lists(DevState s, Ge
         return;
     }
     tile_stage_f32(m, s.xr, to, tile, gidx);
+    for (int u = T + threadIdx.x; u < T + 32; u += blockDim.x)
+        tile[u] = make_float4(1.0e4f, 1.0e4f, 1.0e4f, __int_as_float(0));
     __syncthreads();
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int lx = warp & 1, ly = (warp >> 1) & 1, lz = warp >> 2;
-    const int own_begin0 = m.prefix[warp], own_count = m.prefix[warp + 1] - own_begin0;
+    const int own_begin = m.prefix[warp], own_count = m.prefix[warp + 1] - own_begin;
+    uint16_t* col = buf + (size_t)warp * list_cap * 32 + lane;
     const int blk0 = m.start[0];
     const int own_coord = (lx + 1) + 4 * (ly + 1) + 16 * (lz + 1);
-    int* cnt_s = cnt_all + warp * WARP_ATOMS;
-    uint16_t* ring = ring_all + (size_t)warp * WARP_ATOMS * RING;
+    const f2_t hi2 = f2_pack(band_hi, band_hi), lo2 = f2_pack(band_lo, band_lo);
     int max_cnt = 0;
     unsigned long long sum_cnt = 0;
 
-    for (int base = 0; base < own_count; base += WARP_ATOMS) {
-        const int na = own_count - base < WARP_ATOMS ? own_count - base : WARP_ATOMS;
-        const int own_begin = own_begin0 + base;
-        uint4* out0 = reinterpret_cast<uint4*>(s.nl) + (blk0 + own_begin);
-        cnt_s[lane] = 0;
-        __syncwarp();
+    for (int base = 0; base < own_count; base += 32) {
+        const int e = base + lane;
+        const bool active = e < own_count;
+        const int ui = own_begin + (active ? e : 0);
+        const float4 pi = tile[ui];
+        const f2_t pix = f2_pack(pi.x, pi.x), piy = f2_pack(pi.y, pi.y), piz = f2_pack(pi.z, pi.z);
+        int cnt = 0;
         {
             const int slot = c_tiles.idx_of_coord[own_coord];
-            scan_cell_ballot<HALF, true>(tile, gidx, s, g, rl2, m.prefix[slot], m.prefix[slot + 1], own_begin, na,
-                                         lane, band_lo, band_hi, ring, cnt_s, out0, list_cap, T);
+            scan_cell<HALF, true>(tile, gidx, s, g, rl2, m.prefix[slot], m.prefix[slot + 1], pix, piy, piz, hi2,
+                                  lo2, ui, active, col, list_cap, cnt);
         }
 #pragma unroll 1
         for (int key = HALF ? 1 : -13; key <= 13; ++key) {
             if (key == 0) continue;
             const int oz = (key + 13) / 9 - 1, oy = ((key + 13) / 3) % 3 - 1, ox = (key + 13) % 3 - 1;
             const int slot = c_tiles.idx_of_coord[own_coord + ox + 4 * oy + 16 * oz];
-            scan_cell_ballot<HALF, false>(tile, gidx, s, g, rl2, m.prefix[slot], m.prefix[slot + 1], own_begin, na,
-                                          lane, band_lo, band_hi, ring, cnt_s, out0, list_cap, T);
+            scan_cell<HALF, false>(tile, gidx, s, g, rl2, m.prefix[slot], m.prefix[slot + 1], pix, piy, piz, hi2,
+                                   lo2, ui, active, col, list_cap, cnt);
         }
-        // lane a finishes atom a: last partial chunk (padded with the dummy slot T), count, stats
-        if (lane < na) {
-            const int cnt = cnt_s[lane];
-            const int ccnt = cnt < list_cap ? cnt : list_cap;
-            if (ccnt & 7) {
-                const int ch = ccnt >> 3;
-                const uint16_t* q = ring + lane * RING + ((ch * 8) & (RING - 1));
-                unsigned e[8];
-#pragma unroll
-                for (int k = 0; k < 8; ++k) e[k] = k < (ccnt & 7) ? q[k] : (unsigned)T;
-                out0[(size_t)ch * s.np + lane] =
-                    make_uint4(e[0] | (e[1] << 16), e[2] | (e[3] << 16), e[4] | (e[5] << 16), e[6] | (e[7] << 16));
-            }
+        const int gi = blk0 + ui;
+        if (active) {
             if (cnt > list_cap) atomicOr(s.err, ERR_LIST_OVERFLOW);
-            s.nl_cnt[blk0 + own_begin + lane] = (uint16_t)ccnt;
+            s.nl_cnt[gi] = (uint16_t)(cnt < list_cap ? cnt : list_cap);
             max_cnt = cnt > max_cnt ? cnt : max_cnt;
             sum_cnt += (unsigned long long)cnt;
+        }
+        // write the lists in chunks of 8 (one 16-byte store per chunk), padding the
+        // last chunk with the tile's dummy slot T
+        const int ccnt = active ? (cnt < list_cap ? cnt : list_cap) : 0;
+        const int nch = (ccnt + 7) >> 3;
+        int wch = nch;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) wch = max(wch, __shfl_xor_sync(0xffffffffu, wch, o));
+        __syncwarp();
+        uint4* out = reinterpret_cast<uint4*>(s.nl) + gi;
+        for (int c = 0; c < wch; ++c) {
+            if (c < nch) {
+                unsigned v[4];
+#pragma unroll
+                for (int h = 0; h < 4; ++h) {
+                    const int k0 = 8 * c + 2 * h, k1 = k0 + 1;
+                    const unsigned a0 = k0 < ccnt ? col[k0 * 32] : (unsigned)T;
+                    const unsigned a1 = k1 < ccnt ? col[k1 * 32] : (unsigned)T;
+                    v[h] = a0 | (a1 << 16);
+                }
+                out[(size_t)c * s.np] = make_uint4(v[0], v[1], v[2], v[3]);
+            }
         }
         __syncwarp();
     }
@@ -215,9 +235,8 @@ __global__ void __launch_bounds__(NL_WARPS * 32, 2) k_build_lists(DevState s, Ge
 }
 
 static size_t nl_smem_bytes(int list_cap, int tile_cap) {
-    (void)list_cap;
-    return (size_t)tile_cap * (sizeof(float4) + sizeof(int32_t)) + (size_t)NL_WARPS * WARP_ATOMS * sizeof(int) +
-           (size_t)NL_WARPS * WARP_ATOMS * RING * sizeof(uint16_t);
+    return (size_t)(tile_cap + 32) * sizeof(float4) + (size_t)tile_cap * sizeof(int32_t) +
+           (size_t)NL_WARPS * 32 * list_cap * 2;
 }
 
 void launch_build_lists(const DevState& s, const Geometry& g, const TileOffsets& to, double rl2, int list_cap,

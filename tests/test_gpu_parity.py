@@ -235,6 +235,22 @@ def test_fp64_trajectory_config1(lst):
     assert info["n_redos"] == 0
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_graph_and_direct_launch_give_identical_steps(precision, monkeypatch):
+    """md_step through CUDA graphs with the rebuild decided on the device, and the same
+    kernels launched from the host (MDGB_NO_GRAPHS=1), give bit-identical trajectories."""
+    sysm = W.lj_fcc(10, seed=3)
+    a = make(sysm, precision, "full")
+    a.step(60)
+    monkeypatch.setenv("MDGB_NO_GRAPHS", "1")
+    b = make(sysm, precision, "full")
+    b.step(60)
+    pa, va, ia = a.get_state()
+    pb, vb, ib = b.get_state()
+    assert np.array_equal(pa, pb) and np.array_equal(va, vb) and np.array_equal(ia, ib)
+    assert a.info()["n_builds"] == b.info()["n_builds"]
+
+
 def test_mixed_trajectory_short():
     sysm = W.lj_fcc(10, seed=1)
     s = make(sysm, "mixed", "full")
