@@ -199,6 +199,32 @@ int md_get_info(md_system *s, md_info *out);
  */
 int md_set_timing(md_system *s, int enable);
 
+/*
+ * Kinetic energy 1/2 sum m v^2 of n atoms, for callers that cannot allocate
+ * device memory at the moment they need it - e.g. code that runs while a CUDA
+ * stream is being captured into a graph (no cudaMalloc there), or a host that
+ * gives this library a fixed memory budget and locks allocation afterwards.
+ * The paper has no counterpart of this call: it is a deployment variant of the
+ * deterministic FP64 two-pass reduction md_energy_virial uses.  It needs no
+ * md_system and allocates nothing: its partial sums live in a file-scope static
+ * device array of 1024 doubles (8 KiB), which every GPU that loads the library
+ * keeps until the process exits.
+ *   vel      device, n x 3 doubles (any order); species: device, n int32, or NULL (all 0)
+ *   mass     host, n_species doubles (1 <= n_species <= 4), copied by value
+ *   ke_out   device, one double, written on `stream` (cudaStream_t, NULL = legacy default)
+ * Limits and errors: MD_ERR_ARG if n < 0 or n > 2^30 (the largest size it
+ * accepts), if ke_out or mass is NULL, or if n_species is out of range; nothing
+ * is launched then.  MD_ERR_CUDA if the launch fails.
+ * The first call on each device looks up the array's device address with that
+ * device current (cudaGetSymbolAddress); make that first call before any stream
+ * capture.  Every call overwrites the whole partial-sum array it uses, so nothing
+ * has to start at zero, but all calls share the one array: calls whose kernels
+ * overlap on the GPU (different streams, no ordering between them) race and may
+ * return wrong sums.  Asynchronous: ke_out is valid once the stream reaches it.
+ */
+int md_kinetic_energy_noalloc(int64_t n, const double *vel, const int32_t *species,
+                              const double *mass, int32_t n_species, double *ke_out, void *stream);
+
 /* Copy the last error message into buf (at most len bytes, NUL-terminated). */
 int md_last_error(md_system *s, char *buf, int64_t len);
 

@@ -39,7 +39,7 @@ MD_REBUILD_EVERY_K = 1
 
 EXPORTED = ["md_create", "md_set_state", "md_bin_cells", "md_build_neighbors", "md_forces", "md_step",
             "md_energy_virial", "md_get_state", "md_get_neighbors", "md_get_cells", "md_get_info",
-            "md_set_timing", "md_last_error", "md_destroy"]
+            "md_set_timing", "md_last_error", "md_destroy", "md_kinetic_energy_noalloc"]
 
 
 class md_params(C.Structure):
@@ -86,6 +86,7 @@ def _load():
     lib.md_get_cells.argtypes = [P, P]
     lib.md_get_info.argtypes = [P, C.POINTER(md_info)]
     lib.md_set_timing.argtypes = [P, C.c_int]
+    lib.md_kinetic_energy_noalloc.argtypes = [C.c_int64, P, P, C.POINTER(C.c_double), C.c_int32, P, P]
     lib.md_last_error.argtypes = [P, C.c_char_p, C.c_int64]
     lib.md_destroy.argtypes = [P]
     lib.md_destroy.restype = None
@@ -208,6 +209,17 @@ def md_get_info(handle) -> dict:
 
 def md_set_timing(handle, enable=True):
     _check(handle, _lib.md_set_timing(handle, int(bool(enable))))
+
+
+def md_kinetic_energy_noalloc(n, vel, species, mass, ke_out, stream=None):
+    """Kinetic energy of device velocities into the device scalar ke_out, with no device
+    allocation (see include/mdgb.h); returns the C status code."""
+    mass = np.ascontiguousarray(np.atleast_1d(mass), dtype=np.float64)
+    vp, _ = _ptr(vel)
+    sp, _ = _ptr(species)
+    op, _ = _ptr(ke_out)
+    return _lib.md_kinetic_energy_noalloc(int(n), vp, sp, mass.ctypes.data_as(C.POINTER(C.c_double)),
+                                          int(mass.shape[0]), op, C.c_void_p(stream) if stream else None)
 
 
 def md_destroy(handle):
