@@ -178,6 +178,20 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def measured_force_traffic(n):
+    """DRAM bytes per force launch from the committed ncu capture (profiles/force_traffic.json),
+    scaled to n atoms; None if the force kernel's source changed since the capture."""
+    import hashlib
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "force_traffic.json")))
+        src = os.path.join(ROOT, "paper_1305_4196_gb300", "csrc", "k_force.cu")
+        if hashlib.sha256(open(src, "rb").read()).hexdigest() != rec["k_force_cu_sha256"]:
+            return None
+        return (rec["dram_read_bytes"] + rec["dram_write_bytes"]) * n / rec["atoms"]
+    except Exception:
+        return None
+
+
 def algorithmic_force_bytes(n, entries, precision):
     """Bytes one force evaluation must move at least: coordinates (16 B FP32 / 28 B FP64 with
     species) and list length (2 B) read per atom, force written (24 B), 2 B per list entry."""
@@ -252,7 +266,9 @@ def run_ours(args):
     achieved = abytes / (f_ms * 1e-3) / 1e9
     roofline = {"bound": "hbm", "kernel": "k_force_mixed_full" if args.precision == "mixed" else "k_force_fp64_full",
                 "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)", "traffic": None,
+                "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
+                "traffic": measured_force_traffic(sysm.n) if args.precision == "mixed" and args.list == "full" else None,
+                "traffic_note": "ncu dram read+write of a 1,048,576-atom launch scaled by atoms",
                 "algorithmic_bytes": abytes, "avg_launch_ms": f_ms, "launches_timed": info1["timed_force_evals"],
                 "force_share_of_step": info1["force_ms"] / ms}
 
