@@ -34,6 +34,8 @@ WORKLOADS = {
     "lj_liquid_2048000": dict(n_cells=80, rho=0.8442, T=0.72, seed=2),
     # smaller case of the same kernels for profiler captures (lists still exceed L2)
     "lj_liquid_1048576": dict(n_cells=64, rho=0.8442, T=0.72, seed=2),
+    # strongly inhomogeneous: fcc slab (30 % of a 151.2 sigma cube) plus 40 fcc nanoparticles in vacuum
+    "slab_nanoparticles_1192114": dict(L=152.0, rho=0.8442, T=0.3, seed=3),
 }
 
 
@@ -117,6 +119,8 @@ class ClockSampler:
 def make_workload(name):
     from paper_1305_4196_gb300 import workloads as W
     w = WORKLOADS[name]
+    if "L" in w:
+        return W.slab_nanoparticles(w["L"], rho=w["rho"], T=w["T"], seed=w["seed"])
     return W.lj_fcc(w["n_cells"], rho=w["rho"], T=w["T"], seed=w["seed"])
 
 
@@ -193,10 +197,13 @@ def measured_force_traffic(n):
 
 
 def algorithmic_force_bytes(n, entries, precision):
-    """Bytes one force evaluation must move at least: coordinates (16 B FP32 / 28 B FP64 with
-    species) and list length (2 B) read per atom, force written (24 B), 2 B per list entry."""
-    per_atom = (16 if precision == "mixed" else 28) + 2 + 24
-    return n * per_atom + 2 * entries
+    """Algorithmic bytes of one full-list force evaluation, the per-unit figures of the method's
+    cost model: per atom its coordinates with species (16 B FP32 / 28 B FP64), a 4 B list
+    length and the 24 B force written; per list entry one 4 B neighbour index.  The kernels
+    store lists as 2 B tile-local indices with a 2 B length, so the DRAM traffic they cause
+    (roofline.traffic, from ncu) is below this figure."""
+    per_atom = (16 if precision == "mixed" else 28) + 4 + 24
+    return n * per_atom + 4 * entries
 
 
 def run_ours(args):
@@ -333,9 +340,37 @@ def run_ours(args):
 
 
 def comparisons(args, sysm, M, stream, value):
-    """Same workload on the FP64 GPU path and on the 8-colour half-list path (short runs)."""
+    """Same workload on the FP64 GPU path and on the 8-colour half-list path (short runs), and
+    the per-atom cost of the strongly inhomogeneous workload next to this one."""
     import torch
     out = {}
+    if args.workload.startswith("lj_liquid"):
+        inh = make_workload("slab_nanoparticles_1192114")
+        s = M.System(inh.n, inh.box, precision=M.MD_MIXED if args.precision == "mixed" else M.MD_FP64,
+                     list_kind=M.MD_LIST_FULL if args.list == "full" else M.MD_LIST_HALF_COLOUR8,
+                     stream=stream.cuda_stream)
+        s.set_state(inh.pos, inh.vel, inh.species)
+        s.step(args.inner)
+        torch.cuda.synchronize()
+        info0 = s.info()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(3):
+            s.step(args.inner)
+            s.energy_virial()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        info1 = s.info()
+        ns_inh = ms * 1e6 / (inh.n * 3 * args.inner)
+        ns_hom = 1e9 / value
+        out["inhomogeneous"] = {"workload": "slab_nanoparticles_1192114", "atoms": inh.n,
+                                "box_sigma": float(inh.box[0]), "timesteps": 3 * args.inner,
+                                "value": inh.n * 3 * args.inner / (ms * 1e-3), "unit": METRIC,
+                                "ns_per_atom_timestep": ns_inh,
+                                "rebuilds_per_timestep": (info1["n_builds"] - info0["n_builds"]) / (3 * args.inner),
+                                "per_atom_cost_vs_homogeneous": ns_inh / ns_hom}
+        s.close()
     runs = []
     if args.precision == "mixed":
         runs.append(("fp64_gpu", M.MD_FP64, M.MD_LIST_FULL, 10, 2))

@@ -29,6 +29,10 @@
 namespace mdgb {
 
 constexpr int F_THREADS = 256;
+constexpr int FULL_THREADS = 256;  // CTA size of the full-list mixed kernel
+// Register cap of the full-list mixed kernel: 48 keeps 5 CTAs (40 warps) resident per SM.
+// The kernel is latency bound, and more resident warps beat longer per-thread schedules.
+#define MDGB_FULL_MAX_REGS 48
 constexpr float MAGIC = 12582912.0f;   // 1.5 * 2^23: adding it rounds |a| < 2^22 to an integer
 constexpr float TWO21 = 2097152.0f;    // 2^21
 constexpr float FS_SCALE = 2048.0f;    // 2^11: pair force scaled so that rint() yields multiples of 2^-11
@@ -195,13 +199,16 @@ __device__ __forceinline__ void load_species_table(const PairTable& pt, SpeciesT
     }
 }
 
+// Chunks 0, 1, ... nch-1 of one list, chunk c at lp[c * stride] (stride in uint4 units),
+// two entries per call of body; the next chunk is loaded while this one is used.
 template <typename Body>
-__device__ __forceinline__ void for_each_neighbour_pair(const uint4* __restrict__ lp, int np, int nch, Body&& body) {
+__device__ __forceinline__ void for_each_neighbour_pair(const uint4* __restrict__ lp, size_t stride, int nch,
+                                                        Body&& body) {
     uint4 cur = make_uint4(0u, 0u, 0u, 0u);
     if (nch > 0) cur = __ldcs(lp);
     for (int c = 0; c < nch; ++c) {
         uint4 nxt = cur;
-        if (c + 1 < nch) nxt = __ldcs(lp + (size_t)(c + 1) * np);
+        if (c + 1 < nch) nxt = __ldcs(lp + (size_t)(c + 1) * stride);
         body((int)(cur.x & 0xffffu), (int)(cur.x >> 16));
         body((int)(cur.y & 0xffffu), (int)(cur.y >> 16));
         body((int)(cur.z & 0xffffu), (int)(cur.z >> 16));
@@ -211,24 +218,34 @@ __device__ __forceinline__ void for_each_neighbour_pair(const uint4* __restrict_
 }
 
 template <typename Body>
-__device__ __forceinline__ void for_each_neighbour(const uint4* __restrict__ lp, int np, int nch, Body&& body) {
-    for_each_neighbour_pair(lp, np, nch, [&](int u0, int u1) {
+__device__ __forceinline__ void for_each_neighbour(const uint4* __restrict__ lp, size_t stride, int nch,
+                                                   Body&& body) {
+    for_each_neighbour_pair(lp, stride, nch, [&](int u0, int u1) {
         body(u0);
         body(u1);
     });
+}
+
+// One tile entry with a single 128-bit shared-memory load (base = shared address of the tile).
+__device__ __forceinline__ float4 lds_tile(unsigned base, int u) {
+    float4 v;
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "r"(base + ((unsigned)u << 4)));
+    return v;
 }
 
 // Exact path for one atom whose list holds a pair force component >= 2048 eps/sigma
 // (or a non-finite one): every term through the FP64 rounding of fix_add_wide.
 template <bool SINGLE>
 __device__ __noinline__ void force_atom_wide(const float4* __restrict__ tile, const SpeciesTable& stab, int nsp,
-                                             float4 pi, const uint4* lp, int np, int nch, FixAcc& ax, FixAcc& ay,
-                                             FixAcc& az, uint32_t* err) {
+                                             float4 pi, const uint4* lp, size_t stride, int nch, FixAcc& ax,
+                                             FixAcc& ay, FixAcc& az, uint32_t* err) {
     ax = FixAcc{0u, 0u};
     ay = FixAcc{0u, 0u};
     az = FixAcc{0u, 0u};
     const int si = __float_as_int(pi.w);
-    for_each_neighbour(lp, np, nch, [&](int u) {
+    for_each_neighbour(lp, stride, nch, [&](int u) {
         const float4 pj = tile[u];
         const float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
         const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
@@ -245,9 +262,10 @@ __device__ __noinline__ void force_atom_wide(const float4* __restrict__ tile, co
 }
 
 // ---------------------------------------------------------------- mixed, full list
-// Two neighbours per iteration in packed FP32x2 arithmetic.
+// One thread per atom, two neighbours per iteration in packed FP32x2 arithmetic; each
+// neighbour is one 128-bit shared-memory load.
 template <bool SINGLE, bool EV>
-__global__ void __launch_bounds__(F_THREADS) k_force_mixed_full(DevState s, Geometry g, PairTable pt,
+__global__ void __maxnreg__(MDGB_FULL_MAX_REGS) k_force_mixed_full(DevState s, Geometry g, PairTable pt,
                                                                 TileOffsets to, int tile_cap, float fs2_max) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ TileMeta m;
@@ -261,13 +279,15 @@ __global__ void __launch_bounds__(F_THREADS) k_force_mixed_full(DevState s, Geom
         if (threadIdx.x == 0) atomicOr(s.err, ERR_TILE_OVERFLOW);
         return;
     }
-    tile_stage_f32(m, s.xr, to, tile, nullptr);
+    const int nown = m.prefix[8];
+    if (nown == 0) return;
+    tile_stage_f32_cells(m, s.xr, to, tile);
     stage_dummy_f32(tile, T);
     __syncthreads();
+    const unsigned tile_s = (unsigned)__cvta_generic_to_shared(tile);
     const int blk0 = m.start[0];
-    const int nown = m.prefix[8];
     const int64_t n = s.n;
-    const int np = s.np;
+    const size_t np = s.np;
     const int nsp = pt.nsp;
     const f2_t magic2 = f2_pack(MAGIC, MAGIC);
     const f2_t two21 = f2_pack(TWO21, TWO21);
@@ -286,8 +306,8 @@ __global__ void __launch_bounds__(F_THREADS) k_force_mixed_full(DevState s, Geom
         float pe = 0.f, w0 = 0.f, w1 = 0.f, w2 = 0.f, w3 = 0.f, w4 = 0.f, w5 = 0.f;
         bool bad = false;
         for_each_neighbour_pair(lp, np, nch, [&](int u0, int u1) {
-            const float4 pa = tile[u0];
-            const float4 pb = tile[u1];
+            const float4 pa = lds_tile(tile_s, u0);
+            const float4 pb = lds_tile(tile_s, u1);
             const f2_t dx = f2_sub(pix, f2_pack(pa.x, pb.x));
             const f2_t dy = f2_sub(piy, f2_pack(pa.y, pb.y));
             const f2_t dz = f2_sub(piz, f2_pack(pa.z, pb.z));
@@ -372,7 +392,7 @@ __global__ void __launch_bounds__(F_THREADS) k_force_mixed_half(DevState s, Geom
         if (threadIdx.x == 0) atomicOr(s.err, ERR_TILE_OVERFLOW);
         return;
     }
-    tile_stage_f32(m, s.xr, to, tile, nullptr);
+    tile_stage_f32_cells(m, s.xr, to, tile);
     stage_dummy_f32(tile, T);
     for (int u = threadIdx.x; u <= T; u += blockDim.x) {
 #pragma unroll
@@ -698,13 +718,13 @@ void launch_forces_mixed(const DevState& s, const Geometry& g, const PairTable& 
     const bool single = pt.nsp == 1;
     if (!half) {
         if (single && !with_energy)
-            k_force_mixed_full<true, false><<<g.nblock, F_THREADS, smem, st>>>(s, g, pt, to, tile_cap, fs2_max);
+            k_force_mixed_full<true, false><<<g.nblock, FULL_THREADS, smem, st>>>(s, g, pt, to, tile_cap, fs2_max);
         else if (single)
-            k_force_mixed_full<true, true><<<g.nblock, F_THREADS, smem, st>>>(s, g, pt, to, tile_cap, fs2_max);
+            k_force_mixed_full<true, true><<<g.nblock, FULL_THREADS, smem, st>>>(s, g, pt, to, tile_cap, fs2_max);
         else if (!with_energy)
-            k_force_mixed_full<false, false><<<g.nblock, F_THREADS, smem, st>>>(s, g, pt, to, tile_cap, fs2_max);
+            k_force_mixed_full<false, false><<<g.nblock, FULL_THREADS, smem, st>>>(s, g, pt, to, tile_cap, fs2_max);
         else
-            k_force_mixed_full<false, true><<<g.nblock, F_THREADS, smem, st>>>(s, g, pt, to, tile_cap, fs2_max);
+            k_force_mixed_full<false, true><<<g.nblock, FULL_THREADS, smem, st>>>(s, g, pt, to, tile_cap, fs2_max);
         return;
     }
     cudaMemsetAsync(s.fq, 0, sizeof(long long) * 3 * (size_t)s.n, st);

@@ -87,6 +87,33 @@ __device__ __forceinline__ float pick4(const float (&o)[4], int t) {
     return t == 0 ? o[0] : (t == 1 ? o[1] : (t == 2 ? o[2] : o[3]));
 }
 
+// Stage the block-frame FP32 coordinates of the tile, one warp per tile cell (lanes
+// over the cell's atoms, two cells per step so that two loads are in flight).
+__device__ __forceinline__ void tile_stage_f32_cells(const TileMeta& m, const float4* __restrict__ xr,
+                                                     const TileOffsets& to, float4* __restrict__ tile) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int slot = warp; slot < 64; slot += 2 * nw) {
+        const int slot2 = slot + nw;
+        const int c = c_tiles.coord_of_idx[slot];
+        const int u0 = m.prefix[slot], cnt = m.prefix[slot + 1] - u0, j0 = m.start[slot];
+        const int c2 = slot2 < 64 ? c_tiles.coord_of_idx[slot2] : 0;
+        const int v0 = slot2 < 64 ? m.prefix[slot2] : 0;
+        const int cnt2 = slot2 < 64 ? m.prefix[slot2 + 1] - v0 : 0;
+        const int k0 = slot2 < 64 ? m.start[slot2] : 0;
+        const float ox = pick4(to.off[0], c & 3), oy = pick4(to.off[1], (c >> 2) & 3), oz = pick4(to.off[2], c >> 4);
+        const float ox2 = pick4(to.off[0], c2 & 3), oy2 = pick4(to.off[1], (c2 >> 2) & 3),
+                    oz2 = pick4(to.off[2], c2 >> 4);
+        const int most = cnt > cnt2 ? cnt : cnt2;
+        for (int e = lane; e < most; e += 32) {
+            float4 p = make_float4(0.f, 0.f, 0.f, 0.f), q = p;
+            if (e < cnt) p = xr[j0 + e];
+            if (e < cnt2) q = xr[k0 + e];
+            if (e < cnt) tile[u0 + e] = make_float4(p.x + ox, p.y + oy, p.z + oz, p.w);
+            if (e < cnt2) tile[v0 + e] = make_float4(q.x + ox2, q.y + oy2, q.z + oz2, q.w);
+        }
+    }
+}
+
 // Stage the block-frame FP32 coordinates of the tile (T = m.prefix[64] <= cap).
 __device__ __forceinline__ void tile_stage_f32(const TileMeta& m, const float4* __restrict__ xr,
                                                const TileOffsets& to, float4* __restrict__ tile,
