@@ -182,16 +182,18 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def measured_force_traffic(n):
-    """DRAM bytes per force launch from the committed ncu capture (profiles/force_traffic.json),
-    scaled to n atoms; None if the force kernel's source changed since the capture."""
+def measured_force_traffic(n, fused):
+    """DRAM bytes per launch of the force kernel (fused: with velocity Verlet) from the
+    committed ncu capture (profiles/force_traffic.json), scaled to n atoms; None if the
+    kernel's source changed since the capture."""
     import hashlib
     try:
         rec = json.load(open(os.path.join(ROOT, "profiles", "force_traffic.json")))
         src = os.path.join(ROOT, "paper_1305_4196_gb300", "csrc", "k_force.cu")
         if hashlib.sha256(open(src, "rb").read()).hexdigest() != rec["k_force_cu_sha256"]:
             return None
-        return (rec["dram_read_bytes"] + rec["dram_write_bytes"]) * n / rec["atoms"]
+        r = rec["fused" if fused else "force"]
+        return (r["dram_read_bytes"] + r["dram_write_bytes"]) * n / rec["atoms"]
     except Exception:
         return None
 
@@ -204,6 +206,13 @@ def algorithmic_force_bytes(n, entries, precision):
     (roofline.traffic, from ncu) is below this figure."""
     per_atom = (16 if precision == "mixed" else 28) + 4 + 24
     return n * per_atom + 4 * entries
+
+
+def algorithmic_fused_bytes(n, entries):
+    """The same for the force kernel with the velocity-Verlet updates fused in: the force
+    part without the force write (16 + 4 B per atom, 4 B per entry) plus the update's
+    positions and velocities read and written (96 B) and its 24 B reference read."""
+    return n * (16 + 4 + 96 + 24) + 4 * entries
 
 
 def run_ours(args):
@@ -265,19 +274,43 @@ def run_ours(args):
     value = world * sysm.n * timesteps / (t_max * 1e-3)
     launches = info1["kernel_launches"] - info0["kernel_launches"]
 
-    # roofline of the dominant kernel (the force evaluation), from events around each launch
+    # roofline of the dominant kernel (the force evaluation; on the full-list mixed path the
+    # force kernel with velocity Verlet fused in), from events around each launch
+    fused = args.precision == "mixed" and args.list == "full" and os.environ.get("MDGB_NO_FUSE", "0") in ("", "0")
     f_evals = max(info1["timed_force_evals"], 1)
     f_ms = info1["force_ms"] / f_evals
     peak, peak_kind = load_peaks()
-    abytes = algorithmic_force_bytes(sysm.n, info1["list_entries"], args.precision)
+    if fused:
+        abytes = algorithmic_fused_bytes(sysm.n, info1["list_entries"])
+        kname = "k_force_mixed_full<1, 0, FM_KKD> (forces + velocity Verlet)"
+    else:
+        abytes = algorithmic_force_bytes(sysm.n, info1["list_entries"], args.precision)
+        kname = "k_force_mixed_full" if args.precision == "mixed" else "k_force_fp64_full"
     achieved = abytes / (f_ms * 1e-3) / 1e9
-    roofline = {"bound": "hbm", "kernel": "k_force_mixed_full" if args.precision == "mixed" else "k_force_fp64_full",
+    roofline = {"bound": "hbm", "kernel": kname,
                 "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
-                "traffic": measured_force_traffic(sysm.n) if args.precision == "mixed" and args.list == "full" else None,
+                "traffic": measured_force_traffic(sysm.n, fused) if args.precision == "mixed" and args.list == "full"
+                else None,
                 "traffic_note": "ncu dram read+write of a 1,048,576-atom launch scaled by atoms",
                 "algorithmic_bytes": abytes, "avg_launch_ms": f_ms, "launches_timed": info1["timed_force_evals"],
                 "force_share_of_step": info1["force_ms"] / ms}
+
+    # the force kernel alone (md_forces: no integration), against the force-only cost model
+    s.set_timing(True)
+    i_f0 = s.info()
+    for _ in range(5):
+        M.md_forces(s.handle, None)
+    torch.cuda.synchronize()
+    i_f1 = s.info()
+    s.set_timing(False)
+    fo_ms = (i_f1["force_ms"] - i_f0["force_ms"]) / max(i_f1["timed_force_evals"] - i_f0["timed_force_evals"], 1)
+    fo_bytes = algorithmic_force_bytes(sysm.n, i_f1["list_entries"], args.precision)
+    roofline["force_kernel_alone"] = {"avg_launch_ms": fo_ms, "algorithmic_bytes": fo_bytes,
+                                      "achieved": fo_bytes / (fo_ms * 1e-3) / 1e9,
+                                      "frac": fo_bytes / (fo_ms * 1e-3) / 1e9 / peak,
+                                      "traffic": measured_force_traffic(sysm.n, False)
+                                      if args.precision == "mixed" and args.list == "full" else None}
 
     # neighbour-list build (binning + lists) on its own: builds inside graph-launched steps
     # are not bracketed by events, so time a few host-launched ones after the timed region
@@ -320,7 +353,7 @@ def run_ours(args):
 
     extras = {}
     if not args.no_extras and rank == 0 and world == 1:
-        extras = comparisons(args, sysm, M, stream, value)
+        extras = comparisons(args, sysm, M, stream, value, info1["list_entries"] / sysm.n)
 
     s.close()
     if rank == 0:
@@ -339,36 +372,41 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def comparisons(args, sysm, M, stream, value):
+def comparisons(args, sysm, M, stream, value, list_len_hom):
     """Same workload on the FP64 GPU path and on the 8-colour half-list path (short runs), and
     the per-atom cost of the strongly inhomogeneous workload next to this one."""
     import torch
     out = {}
     if args.workload.startswith("lj_liquid"):
+        # the strongly inhomogeneous case as its own run: 500 time steps from the prepared
+        # state, all timed (the cold slab and particles contract, so lists lengthen as it runs)
         inh = make_workload("slab_nanoparticles_1192114")
         s = M.System(inh.n, inh.box, precision=M.MD_MIXED if args.precision == "mixed" else M.MD_FP64,
                      list_kind=M.MD_LIST_FULL if args.list == "full" else M.MD_LIST_HALF_COLOUR8,
                      stream=stream.cuda_stream)
         s.set_state(inh.pos, inh.vel, inh.species)
-        s.step(args.inner)
+        s.forces()
         torch.cuda.synchronize()
         info0 = s.info()
+        steps_inh = 500
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        for _ in range(3):
-            s.step(args.inner)
-            s.energy_virial()
+        for _ in range(steps_inh // 100):
+            s.step(100)
         e1.record(stream)
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1)
         info1 = s.info()
-        ns_inh = ms * 1e6 / (inh.n * 3 * args.inner)
+        ns_inh = ms * 1e6 / (inh.n * steps_inh)
         ns_hom = 1e9 / value
         out["inhomogeneous"] = {"workload": "slab_nanoparticles_1192114", "atoms": inh.n,
-                                "box_sigma": float(inh.box[0]), "timesteps": 3 * args.inner,
-                                "value": inh.n * 3 * args.inner / (ms * 1e-3), "unit": METRIC,
+                                "box_sigma": float(inh.box[0]), "timesteps": steps_inh,
+                                "value": inh.n * steps_inh / (ms * 1e-3), "unit": METRIC,
                                 "ns_per_atom_timestep": ns_inh,
-                                "rebuilds_per_timestep": (info1["n_builds"] - info0["n_builds"]) / (3 * args.inner),
+                                "rebuilds_per_timestep": (info1["n_builds"] - info0["n_builds"]) / steps_inh,
+                                "redos": info1["n_redos"] - info0["n_redos"],
+                                "mean_list_length_end": info1["list_entries"] / inh.n,
+                                "mean_list_length_homogeneous": list_len_hom,
                                 "per_atom_cost_vs_homogeneous": ns_inh / ns_hom}
         s.close()
     runs = []

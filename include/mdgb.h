@@ -153,10 +153,15 @@ int md_forces(md_system *s, double *f_out, int device_ptrs);
  * once per chunk of up to 200 steps.  If a rebuild inside a chunk outgrows the
  * list or tile capacity, the chunk is redone from a snapshot of its starting
  * state after the capacities have been regrown (md_info.n_redos counts these).
+ * On the mixed-precision full-list path the force kernel of each step also
+ * performs the velocity-Verlet updates around it (closing kick, and unless it
+ * is the last step of the call, the next opening kick and drift): the same
+ * operations as separate kernels, with the FP32 coordinates double-buffered.
  * With the environment variable MDGB_NO_GRAPHS=1 set when the system is
  * created, the same kernels are launched from the host instead and the rebuild
  * flag is read after every step (slower; for profilers that do not follow
- * kernels into conditional graph nodes).
+ * kernels into conditional graph nodes).  MDGB_NO_FUSE=1 at creation runs
+ * force and integration as separate kernels (bit-identical results).
  * Energies are not computed on the way (use md_energy_virial).
  * Errors: MD_ERR_NONFINITE, MD_ERR_SKIN_VIOLATION, overflow codes, MD_ERR_CUDA.
  */

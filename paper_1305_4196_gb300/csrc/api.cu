@@ -54,10 +54,15 @@ struct md_system {
     };
     cudaStream_t cap_stream = nullptr;
     StepGraph g_first, g_mid;
+    // full-list mixed path: force kernel fused with velocity Verlet, FP32 coordinates
+    // double-buffered; g_fused[closing kick only / kick-kick-drift][buffer read]
+    StepGraph g_fused[2][2];
+    float4* xr_alt = nullptr;
     bool graphs_valid = false;
     int graph_tile_cap = 0, graph_list_cap = 0;
     bool graph_timing = false;
     bool use_graphs = true;  // MDGB_NO_GRAPHS=1 at md_create: host-launched steps (profilers see every kernel)
+    bool no_fuse = false;    // MDGB_NO_FUSE=1 at md_create: separate force and integration kernels
     long long* d_ctrl = nullptr;  // [0] step counter, [1] builds done inside graphs
     long long* h_ctrl = nullptr;  // pinned mirror
     bool snapshot_first = true;
@@ -124,8 +129,24 @@ void dfree(md_system* s, void* p) {
 
 bool mixed(const md_system* s) { return s->precision == MD_MIXED; }
 bool half(const md_system* s) { return s->list_kind == MD_LIST_HALF_COLOUR8; }
+// md_step runs the full-list mixed path with velocity Verlet fused into the force kernel
+bool fused(const md_system* s) { return mixed(s) && !half(s) && !s->no_fuse; }
+
+// The state with its FP32 coordinates in buffer p (0: st[0].xr, 1: xr_alt).  Fused steps
+// read one buffer and write the other; outside md_step the coordinates are in buffer 0.
+DevState view(const md_system* s, int p) {
+    DevState v = s->st[0];
+    if (p) v.xr = s->xr_alt;
+    return v;
+}
+float4* xr_buf(const md_system* s, int p) { return p ? s->xr_alt : s->st[0].xr; }
 
 int round_up(int v, int m) { return (v + m - 1) / m * m; }
+
+// List capacity for a longest list of max_list entries.  Capacity costs memory only
+// (2 bytes per atom per slot), never time, and a list that outgrows it inside a chunk of
+// graph-launched steps costs a redo of the chunk: half as much again, plus 32.
+int list_cap_for(int max_list) { return round_up(max_list + max_list / 2 + 32, 8); }
 
 // ---- event timing
 std::pair<cudaEvent_t, cudaEvent_t> take_events(md_system* s) {
@@ -162,11 +183,15 @@ void drain_events(md_system* s) {
     s->ev_build.clear();
 }
 
-// neighbour-list matrix for the current capacity
-int alloc_lists(md_system* s, int cap) {
+// neighbour-list matrix for the current capacity; with keep, the current lists stay valid
+// (entry k of atom i sits at the same place for every capacity)
+int alloc_lists(md_system* s, int cap, bool keep = false) {
     uint16_t* nl = nullptr;
     int rc = dalloc(s, &nl, (size_t)cap * s->np);
     if (rc) return rc;
+    if (keep && s->st[0].nl)
+        CK(cudaMemcpyAsync(nl, s->st[0].nl, sizeof(uint16_t) * (size_t)std::min(cap, s->list_cap) * s->np,
+                           cudaMemcpyDeviceToDevice, s->stream));
     dfree(s, s->st[0].nl);
     s->st[0].nl = s->st[1].nl = s->st[2].nl = nl;
     s->list_cap = cap;
@@ -195,11 +220,10 @@ int check_err(md_system* s, uint32_t mask) {
 }
 
 // ---- binning: assign, count, scan, scatter, in-cell order, gather + copy back
-void enqueue_bin(md_system* s, cudaStream_t st) {
+void enqueue_bin(md_system* s, const DevState& a, cudaStream_t st) {
     const Geometry& g = s->g;
     cudaMemsetAsync(s->cell_count, 0, sizeof(int32_t) * g.ncell, st);
     cudaMemsetAsync(s->cursor, 0, sizeof(int32_t) * g.ncell, st);
-    const DevState& a = s->st[0];
     launch_bin_assign(a, g, s->atom_cell, s->cell_count, st);
     launch_scan(s->cell_count, a.cell_start, g.ncell, s->scan_scratch, st);
     launch_scatter(a, s->atom_cell, a.cell_start, s->cursor, s->slot_key, s->slot_src, st);
@@ -207,9 +231,9 @@ void enqueue_bin(md_system* s, cudaStream_t st) {
     launch_gather(a, s->st[1], g, s->sorted_src, s->atom_cell, st);
 }
 
-int do_bin(md_system* s) {
+int do_bin(md_system* s, int p = 0) {
     if (s->n == 0) return MD_OK;
-    enqueue_bin(s, s->stream);
+    enqueue_bin(s, view(s, p), s->stream);
     CKL();
     s->launches += 8;
     s->lists_valid = false;
@@ -218,20 +242,20 @@ int do_bin(md_system* s) {
 }
 
 // ---- list build with capacity regrowth (host-visible: reads the device counters)
-int do_build(md_system* s) {
+int do_build(md_system* s, int p = 0) {
     std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
     if (s->timing && s->n > 0) {
         ev = take_events(s);
         CK(cudaEventRecord(ev.first, s->stream));
     }
-    int rc = do_bin(s);
+    int rc = do_bin(s, p);
     if (rc) return rc;
     if (s->n == 0) {
         s->lists_valid = true;
         return MD_OK;
     }
     for (int attempt = 0; attempt < 4; ++attempt) {
-        DevState& a = s->st[s->cur];
+        const DevState a = view(s, p);
         CK(cudaMemsetAsync(a.stats, 0, 4 * sizeof(int32_t), s->stream));
         CK(cudaMemsetAsync(a.err, 0, sizeof(uint32_t), s->stream));
         if (build_lists_smem(s->list_cap, s->tile_cap) > 226 * 1024)
@@ -259,7 +283,7 @@ int do_build(md_system* s) {
             again = true;
         }
         if (e & ERR_LIST_OVERFLOW) {
-            int cap = round_up(max_list + max_list / 8 + 8, 8);
+            int cap = list_cap_for(max_list);
             if (cap > 65535) return fail(s, MD_ERR_LIST_OVERFLOW, "list of %d neighbours", max_list);
             rc = alloc_lists(s, cap);
             if (rc) return rc;
@@ -411,9 +435,66 @@ int capture_step(md_system* s, int mode, md_system::StepGraph& out) {
     CK(cudaStreamEndCapture(cs, &g));
     // the rebuild body
     CK(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-    enqueue_bin(s, cs);
+    enqueue_bin(s, a, cs);
     cudaMemsetAsync(a.stats, 0, 4 * sizeof(int32_t), cs);
     launch_build_lists(a, s->g, s->to, s->rl2, s->list_cap, s->tile_cap, half(s), cs);
+    launch_count_build(s->d_ctrl + 1, cs);
+    CK(cudaStreamEndCapture(cs, &body));
+    CKL();
+    CK(cudaGraphInstantiate(&out.exec, g, 0));
+    return MD_OK;
+}
+
+// Fused step (full-list mixed path): step control -> IF(rebuild){binning, gather, list
+// build, all on coordinate buffer p} -> force kernel with the velocity-Verlet epilogue
+// (kkd: closing + opening kick and drift into buffer 1-p; else the closing kick only).
+int capture_fused(md_system* s, bool kkd, int p, md_system::StepGraph& out) {
+    destroy_graph(out);
+    cudaStream_t cs = s->cap_stream;
+    cudaGraph_t g = nullptr;
+    CK(cudaGraphCreate(&g, 0));
+    out.graph = g;
+    cudaGraphConditionalHandle h;
+    CK(cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault));
+    CK(cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    const DevState a = view(s, p);
+    launch_step_ctrl(s->rebuild == MD_REBUILD_EVERY_K ? 1 : 0, s->rebuild_k, a.rebuild_flag, s->d_ctrl,
+                     s->d_ctrl + 1, a.err, h, cs);
+    cudaStreamCaptureStatus status;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t ndeps = 0;
+    cudaGraph_t cg = nullptr;
+    CK(cudaStreamGetCaptureInfo(cs, &status, nullptr, &cg, &deps, nullptr, &ndeps));
+    alignas(cudaGraphNodeParams) unsigned char cp_raw[sizeof(cudaGraphNodeParams)];
+    std::memset(cp_raw, 0, sizeof(cp_raw));  // all reserved bytes must be zero
+    cudaGraphNodeParams& cp = *reinterpret_cast<cudaGraphNodeParams*>(cp_raw);
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeIf;
+    cp.conditional.size = 1;
+    cudaGraphNode_t cnode;
+    CK(cudaGraphAddNode(&cnode, cg, deps, nullptr, ndeps, &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    CK(cudaStreamUpdateCaptureDependencies(cs, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies));
+    const int mode = kkd ? FUSE_KICK_KICK_DRIFT : FUSE_KICK;
+    if (s->timing) {
+        auto ev = take_events(s);
+        s->ev_free.push_back(ev);
+        CK(cudaEventRecordWithFlags(ev.first, cs, cudaEventRecordExternal));
+        CK(cudaStreamGetCaptureInfo(cs, &status, nullptr, &cg, &deps, nullptr, &ndeps));
+        out.ev_a = ndeps ? deps[0] : nullptr;
+        launch_forces_mixed_fused(a, s->g, s->pt, s->to, s->tile_cap, mode, xr_buf(s, 1 - p), s->dt, s->lim2, cs);
+        CK(cudaEventRecordWithFlags(ev.second, cs, cudaEventRecordExternal));
+        CK(cudaStreamGetCaptureInfo(cs, &status, nullptr, &cg, &deps, nullptr, &ndeps));
+        out.ev_b = ndeps ? deps[0] : nullptr;
+    } else {
+        launch_forces_mixed_fused(a, s->g, s->pt, s->to, s->tile_cap, mode, xr_buf(s, 1 - p), s->dt, s->lim2, cs);
+    }
+    CK(cudaStreamEndCapture(cs, &g));
+    CK(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    enqueue_bin(s, a, cs);
+    cudaMemsetAsync(a.stats, 0, 4 * sizeof(int32_t), cs);
+    launch_build_lists(a, s->g, s->to, s->rl2, s->list_cap, s->tile_cap, 0, cs);
     launch_count_build(s->d_ctrl + 1, cs);
     CK(cudaStreamEndCapture(cs, &body));
     CKL();
@@ -426,8 +507,14 @@ int ensure_graphs(md_system* s) {
         s->graph_timing == s->timing)
         return MD_OK;
     int rc;
-    if ((rc = capture_step(s, INT_KICK_DRIFT, s->g_first))) return rc;
-    if ((rc = capture_step(s, INT_KICK_KICK_DRIFT, s->g_mid))) return rc;
+    if (fused(s)) {
+        for (int k = 0; k < 2; ++k)
+            for (int p = 0; p < 2; ++p)
+                if ((rc = capture_fused(s, k == 1, p, s->g_fused[k][p]))) return rc;
+    } else {
+        if ((rc = capture_step(s, INT_KICK_DRIFT, s->g_first))) return rc;
+        if ((rc = capture_step(s, INT_KICK_KICK_DRIFT, s->g_mid))) return rc;
+    }
     s->graphs_valid = true;
     s->graph_tile_cap = s->tile_cap;
     s->graph_list_cap = s->list_cap;
@@ -460,6 +547,110 @@ int run_steps_direct(md_system* s, int len, bool first) {
     return MD_OK;
 }
 
+// The fused step sequence launched from the host (see run_chunk_fused).
+int run_steps_direct_fused(md_system* s, int len, bool first, bool last) {
+    int rc;
+    const DevState a = view(s, 0);
+    if (first) {
+        CK(cudaMemsetAsync(a.rebuild_flag, 0, sizeof(int32_t), s->stream));
+        launch_integrate(a, s->g, s->pt, INT_KICK_DRIFT, 1, s->dt, s->lim2, s->stream);
+        CKL();
+        s->launches += 1;
+    }
+    int p = 0;
+    for (int k = 0; k < len; ++k) {
+        if ((rc = sync_flags(s))) return rc;
+        const long long step = s->n_steps + k + 1;
+        bool rebuild = s->h_flags[1] != 0;
+        if (s->rebuild == MD_REBUILD_EVERY_K) {
+            const bool due = (step % s->rebuild_k) == 0;
+            if (rebuild && !due) return fail(s, MD_ERR_SKIN_VIOLATION, "an atom moved more than skin/2");
+            rebuild = due;
+        }
+        CK(cudaMemsetAsync(a.rebuild_flag, 0, sizeof(int32_t), s->stream));
+        if (rebuild && (rc = do_build(s, p))) return rc;
+        const bool kkd = !(last && k == len - 1);
+        std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
+        if (s->timing) {
+            ev = take_events(s);
+            CK(cudaEventRecord(ev.first, s->stream));
+        }
+        launch_forces_mixed_fused(view(s, p), s->g, s->pt, s->to, s->tile_cap,
+                                  kkd ? FUSE_KICK_KICK_DRIFT : FUSE_KICK, xr_buf(s, 1 - p), s->dt, s->lim2, s->stream);
+        CKL();
+        if (ev.second) {
+            CK(cudaEventRecord(ev.second, s->stream));
+            s->ev_force.push_back(ev);
+        }
+        s->launches += 1;
+        s->force_evals += 1;
+        if (kkd) p ^= 1;
+    }
+    if (p)
+        CK(cudaMemcpyAsync(s->st[0].xr, s->xr_alt, sizeof(float4) * (size_t)s->n, cudaMemcpyDeviceToDevice,
+                           s->stream));
+    s->forces_valid = last;
+    return MD_OK;
+}
+
+// A chunk of len fused steps.  Step j's force kernel also performs the closing kick of
+// step j and, unless it is the last step of the md_step call, the opening kick and drift
+// of step j+1; the first step of a call starts with a plain kick + drift.  Coordinates
+// alternate between the two FP32 buffers and end the chunk in buffer 0.
+int run_chunk_fused(md_system* s, int len, bool first, bool last) {
+    int rc;
+    if (!s->use_graphs) return run_steps_direct_fused(s, len, first, last);
+    if ((rc = ensure_graphs(s))) return rc;
+    const DevState a = view(s, 0);
+    launch_copy_state(s->st[2], a, s->stream);
+    CKL();
+    s->launches += 1;
+    s->snapshot_first = first;
+    s->h_ctrl[0] = s->n_steps;
+    s->h_ctrl[1] = 0;
+    CK(cudaMemcpyAsync(s->d_ctrl, s->h_ctrl, 2 * sizeof(long long), cudaMemcpyHostToDevice, s->stream));
+    if (first) {
+        // the displacement flag of a later chunk's first step comes from the previous one
+        CK(cudaMemsetAsync(a.rebuild_flag, 0, sizeof(int32_t), s->stream));
+        launch_integrate(a, s->g, s->pt, INT_KICK_DRIFT, 1, s->dt, s->lim2, s->stream);
+        CKL();
+        s->launches += 1;
+    }
+    int p = 0;
+    for (int k = 0; k < len; ++k) {
+        const bool kkd = !(last && k == len - 1);
+        md_system::StepGraph& gr = s->g_fused[kkd ? 1 : 0][p];
+        if (s->timing && gr.ev_a && gr.ev_b) {
+            auto ev = take_events(s);
+            CK(cudaGraphExecEventRecordNodeSetEvent(gr.exec, gr.ev_a, ev.first));
+            CK(cudaGraphExecEventRecordNodeSetEvent(gr.exec, gr.ev_b, ev.second));
+            s->ev_force.push_back(ev);
+        }
+        CK(cudaGraphLaunch(gr.exec, s->stream));
+        s->launches += 2;  // step control, fused force kernel
+        s->force_evals += 1;
+        if (kkd) p ^= 1;
+    }
+    if (p)
+        CK(cudaMemcpyAsync(s->st[0].xr, s->xr_alt, sizeof(float4) * (size_t)s->n, cudaMemcpyDeviceToDevice,
+                           s->stream));
+    CK(cudaMemcpyAsync(s->h_ctrl, s->d_ctrl, 2 * sizeof(long long), cudaMemcpyDeviceToHost, s->stream));
+    if ((rc = sync_flags(s))) return rc;
+    const uint32_t e = s->h_flags[0];
+    if (e & ERR_TILE_OVERFLOW) return MD_ERR_CELL_OVERFLOW;  // the chunk is redone: nothing of it counts
+    if (e & ERR_LIST_OVERFLOW) return MD_ERR_LIST_OVERFLOW;
+    const long long builds = s->h_ctrl[1];
+    s->launches += builds * 10;  // binning (8), list build, build counter
+    if (builds > 0) {
+        s->n_builds += builds;
+        s->max_list = (int)s->h_flags[2];
+        s->max_tile = (int)s->h_flags[3];
+        s->list_entries = (int64_t)((uint64_t)s->h_flags[4] | ((uint64_t)s->h_flags[5] << 32));
+    }
+    s->forces_valid = last;
+    return check_err(s, ERR_NONFINITE | ERR_ESCAPE | ERR_SKIN);
+}
+
 // Run len graph-launched steps; read the device status once at the end.
 int run_chunk(md_system* s, int len, bool first) {
     int rc;
@@ -484,7 +675,7 @@ int run_chunk(md_system* s, int len, bool first) {
             s->ev_force.push_back(ev);
         }
         CK(cudaGraphLaunch(gr.exec, s->stream));
-        s->launches += 3 + (half(s) ? 8 : 1);
+        s->launches += 2 + (half(s) ? 8 : 1);  // integrate, step control, forces
         s->force_evals += 1;
     }
     CK(cudaMemcpyAsync(s->h_ctrl, s->d_ctrl, 2 * sizeof(long long), cudaMemcpyDeviceToHost, s->stream));
@@ -493,7 +684,7 @@ int run_chunk(md_system* s, int len, bool first) {
     if (e & ERR_TILE_OVERFLOW) return MD_ERR_CELL_OVERFLOW;  // the chunk is redone: nothing of it counts
     if (e & ERR_LIST_OVERFLOW) return MD_ERR_LIST_OVERFLOW;
     const long long builds = s->h_ctrl[1];
-    s->launches += builds * 11;
+    s->launches += builds * 10;  // binning (8), list build, build counter
     if (builds > 0) {
         s->n_builds += builds;
         s->max_list = (int)s->h_flags[2];
@@ -501,6 +692,26 @@ int run_chunk(md_system* s, int len, bool first) {
         s->list_entries = (int64_t)((uint64_t)s->h_flags[4] | ((uint64_t)s->h_flags[5] << 32));
     }
     return check_err(s, ERR_NONFINITE | ERR_ESCAPE | ERR_SKIN);
+}
+
+// Capacities for the rebuilds inside the next chunk of graph-launched steps: a chunk that
+// outgrows them is redone from its snapshot, so grow them ahead of need once the last
+// build came close to a limit (lists are kept; the graphs are captured again).
+int ensure_headroom(md_system* s) {
+    if (s->max_list + std::max(16, s->max_list / 4) > s->list_cap) {
+        const int cap = list_cap_for(s->max_list);
+        if (cap <= 65535) {
+            int rc = alloc_lists(s, cap, true);
+            if (rc) return rc;
+        }
+    }
+    if (s->max_tile + std::max(64, s->max_tile / 8) > s->tile_cap) {
+        const int cap = std::min(round_up(s->max_tile + s->max_tile / 4 + 64, 32), round_up((int)s->n + 1, 32));
+        if (cap > s->tile_cap && cap <= 32767 && build_lists_smem(s->list_cap, cap) <= 226 * 1024 &&
+            force_smem_bytes(mixed(s), half(s), 0, cap) <= 226 * 1024)
+            s->tile_cap = cap;
+    }
+    return MD_OK;
 }
 
 int restore_snapshot(md_system* s) {
@@ -514,11 +725,12 @@ int restore_snapshot(md_system* s) {
     if (rc) return rc;
     const int need_list = std::max((int)s->h_flags[2], saved_list);
     const int need_tile = std::max((int)s->h_flags[3], saved_tile);
-    if (need_list > s->list_cap && (rc = alloc_lists(s, round_up(need_list + need_list / 8 + 8, 8)))) return rc;
+    if (need_list > s->list_cap && (rc = alloc_lists(s, std::min(list_cap_for(need_list), 65535)))) return rc;
     if (need_tile > s->tile_cap) s->tile_cap = round_up(need_tile + need_tile / 4 + 64, 32);
     s->lists_valid = false;
     s->forces_valid = false;
     if ((rc = do_build(s))) return rc;
+    CK(cudaMemsetAsync(s->st[0].rebuild_flag, 0, sizeof(int32_t), s->stream));
     return do_forces(s, 0);
 }
 
@@ -546,6 +758,8 @@ int md_create(int64_t n, const double box[3], double r_cut, double skin, const m
     {
         const char* ng = std::getenv("MDGB_NO_GRAPHS");
         s->use_graphs = !(ng && ng[0] && ng[0] != '0');
+        const char* nf = std::getenv("MDGB_NO_FUSE");
+        s->no_fuse = nf && nf[0] && nf[0] != '0';
     }
     s->n = n;
     s->np = round_up((int)std::max<int64_t>(n, 1), 64);
@@ -637,7 +851,7 @@ int md_create(int64_t n, const double box[3], double r_cut, double skin, const m
         return bail(rc);
     if (p->precision == MD_MIXED) {
         if ((rc = dalloc(s, &d0.fq, 3 * (size_t)n)) || (rc = dalloc(s, &d0.pe_atom_f, n)) ||
-            (rc = dalloc(s, &d0.vir_atom_f, 6 * (size_t)n)))
+            (rc = dalloc(s, &d0.vir_atom_f, 6 * (size_t)n)) || (rc = dalloc(s, &s->xr_alt, n)))
             return bail(rc);
     } else {
         if ((rc = dalloc(s, &d0.f, 3 * (size_t)n)) || (rc = dalloc(s, &d0.pe_atom_d, n)) ||
@@ -798,7 +1012,8 @@ int md_step(md_system* s, int32_t n_steps) {
     while (done < n_steps) {
         const int len = std::min(CHUNK, n_steps - done);
         const bool first = done == 0;
-        rc = run_chunk(s, len, first);
+        if ((rc = ensure_headroom(s))) return rc;
+        rc = fused(s) ? run_chunk_fused(s, len, first, done + len == n_steps) : run_chunk(s, len, first);
         if (rc == MD_ERR_CELL_OVERFLOW || rc == MD_ERR_LIST_OVERFLOW) {
             // a rebuild inside the chunk outgrew the captured capacities: restore the
             // chunk's starting state, rebuild with regrowth on the host, and redo it
@@ -812,9 +1027,12 @@ int md_step(md_system* s, int32_t n_steps) {
         s->n_steps += len;
         redo = 0;
     }
-    launch_integrate(s->st[0], s->g, s->pt, INT_KICK, mixed(s), s->dt, s->lim2, s->stream);
-    CKL();
-    s->launches += 1;
+    if (!fused(s)) {
+        // the closing half kick of the last step (fused steps apply it in the force kernel)
+        launch_integrate(s->st[0], s->g, s->pt, INT_KICK, mixed(s), s->dt, s->lim2, s->stream);
+        CKL();
+        s->launches += 1;
+    }
     rc = sync_flags(s);
     if (rc) return rc;
     return check_err(s, ERR_NONFINITE | ERR_ESCAPE | ERR_SKIN);
@@ -975,6 +1193,8 @@ void md_destroy(md_system* s) {
     if (s->h_ctrl) cudaFreeHost(s->h_ctrl);
     destroy_graph(s->g_first);
     destroy_graph(s->g_mid);
+    for (auto& row : s->g_fused)
+        for (auto& gr : row) destroy_graph(gr);
     if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
     if (prev >= 0 && prev != s->device) cudaSetDevice(prev);
     delete s;

@@ -29,6 +29,7 @@
 namespace mdgb {
 
 constexpr int F_THREADS = 256;
+enum { FM_FORCE = 0, FM_KICK = 1, FM_KKD = 2 };  // what the full-list mixed kernel does after the force
 constexpr int FULL_THREADS = 256;  // CTA size of the full-list mixed kernel
 // Register cap of the full-list mixed kernel: 48 keeps 5 CTAs (40 warps) resident per SM.
 // The kernel is latency bound, and more resident warps beat longer per-thread schedules.
@@ -264,9 +265,22 @@ __device__ __noinline__ void force_atom_wide(const float4* __restrict__ tile, co
 // ---------------------------------------------------------------- mixed, full list
 // One thread per atom, two neighbours per iteration in packed FP32x2 arithmetic; each
 // neighbour is one 128-bit shared-memory load.
-template <bool SINGLE, bool EV>
+//
+// MODE selects what follows each atom's force (fused velocity Verlet, the same
+// operations as k_integrate's mixed path, so fused and separate steps agree bit for
+// bit):
+//   FM_FORCE  store the fixed-point force;
+//   FM_KICK   store it and apply the closing half kick v += (dt/2m) F;
+//   FM_KKD    closing and next opening kick in one, v += 2 (dt/2m) F, then the drift
+//             x += dt v, the FP32 coordinates of the new position into xr_out (a second
+//             buffer: other CTAs may still be staging this atom's current ones) and the
+//             skin/2 displacement test.  The force itself is not stored.
+template <bool SINGLE, bool EV, int MODE>
 __global__ void __maxnreg__(MDGB_FULL_MAX_REGS) k_force_mixed_full(DevState s, Geometry g, PairTable pt,
-                                                                TileOffsets to, int tile_cap, float fs2_max) {
+                                                                TileOffsets to, int tile_cap, float fs2_max,
+                                                                float4* __restrict__ xr_out, double dt,
+                                                                float lim2_f) {
+    static_assert(!EV || MODE == FM_FORCE, "energy/virial launches only evaluate forces");
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ TileMeta m;
     __shared__ SpeciesTable stab;
@@ -356,9 +370,38 @@ __global__ void __maxnreg__(MDGB_FULL_MAX_REGS) k_force_mixed_full(DevState s, G
         });
         if (bad) force_atom_wide<SINGLE>(tile, stab, nsp, pi, lp, np, nch, ax, ay, az, s.err);
         const int nterms = nch * 8;
-        s.fq[gi] = fix_final(ax, nterms);
-        s.fq[n + gi] = fix_final(ay, nterms);
-        s.fq[2 * n + gi] = fix_final(az, nterms);
+        const long long qx = fix_final(ax, nterms), qy = fix_final(ay, nterms), qz = fix_final(az, nterms);
+        if (MODE != FM_KKD) {
+            s.fq[gi] = qx;
+            s.fq[n + gi] = qy;
+            s.fq[2 * n + gi] = qz;
+        }
+        if (MODE != FM_FORCE) {
+            const double hq = pt.hdtm_q[SINGLE ? 0 : si];
+            const double kq = MODE == FM_KKD ? 2.0 * hq : hq;
+            const double vx = fma(kq, (double)qx, s.vx[gi]);
+            const double vy = fma(kq, (double)qy, s.vy[gi]);
+            const double vz = fma(kq, (double)qz, s.vz[gi]);
+            s.vx[gi] = vx;
+            s.vy[gi] = vy;
+            s.vz[gi] = vz;
+            if (MODE == FM_KKD) {
+                const double x = fma(dt, vx, s.x[gi]), y = fma(dt, vy, s.y[gi]), z = fma(dt, vz, s.z[gi]);
+                s.x[gi] = x;
+                s.y[gi] = y;
+                s.z[gi] = z;
+                const int c = s.cell_of[gi];
+                const float4 r = s.xr_ref[gi];
+                float4 q;
+                q.x = __double2float_rn(x - s.centre[c]);
+                q.y = __double2float_rn(y - s.centre[s.ncell + c]);
+                q.z = __double2float_rn(z - s.centre[2 * s.ncell + c]);
+                q.w = r.w;
+                xr_out[gi] = q;
+                const float ex = q.x - r.x, ey = q.y - r.y, ez = q.z - r.z;
+                if (!(fmaf(ez, ez, fmaf(ey, ey, ex * ex)) <= lim2_f)) *s.rebuild_flag = 1;
+            }
+        }
         if (EV) {
             // full lists see every pair twice: each atom keeps half of each pair energy / virial
             s.pe_atom_f[gi] = 0.5f * pe;
@@ -693,10 +736,14 @@ static void allow_max_smem(K kernel) {
 }
 
 void init_force_kernels() {
-    allow_max_smem(k_force_mixed_full<true, false>);
-    allow_max_smem(k_force_mixed_full<true, true>);
-    allow_max_smem(k_force_mixed_full<false, false>);
-    allow_max_smem(k_force_mixed_full<false, true>);
+    allow_max_smem(k_force_mixed_full<true, false, FM_FORCE>);
+    allow_max_smem(k_force_mixed_full<true, true, FM_FORCE>);
+    allow_max_smem(k_force_mixed_full<false, false, FM_FORCE>);
+    allow_max_smem(k_force_mixed_full<false, true, FM_FORCE>);
+    allow_max_smem(k_force_mixed_full<true, false, FM_KICK>);
+    allow_max_smem(k_force_mixed_full<false, false, FM_KICK>);
+    allow_max_smem(k_force_mixed_full<true, false, FM_KKD>);
+    allow_max_smem(k_force_mixed_full<false, false, FM_KKD>);
     allow_max_smem(k_force_mixed_half<true, false>);
     allow_max_smem(k_force_mixed_half<true, true>);
     allow_max_smem(k_force_mixed_half<false, false>);
@@ -707,24 +754,32 @@ void init_force_kernels() {
     allow_max_smem(k_force_fp64_half<true>);
 }
 
+// |fs2 * d| < 2^22 (the exact range of the two-part split) is guaranteed when |fs2| < 2^22 / r_cut
+static float fs2_max_of(const PairTable& pt) {
+    float rcmax2 = 0.f;
+    for (int t = 0; t < pt.nsp * pt.nsp; ++t) rcmax2 = pt.rc2_f[t] > rcmax2 ? pt.rc2_f[t] : rcmax2;
+    return 4194304.0f / sqrtf(rcmax2) * 0.999f;
+}
+
 void launch_forces_mixed(const DevState& s, const Geometry& g, const PairTable& pt, const TileOffsets& to,
                          int tile_cap, int half, int with_energy, cudaStream_t st) {
     if (s.n == 0) return;
     const size_t smem = force_smem_bytes(1, half, with_energy, tile_cap);
-    float rcmax2 = 0.f;
-    for (int t = 0; t < pt.nsp * pt.nsp; ++t) rcmax2 = pt.rc2_f[t] > rcmax2 ? pt.rc2_f[t] : rcmax2;
-    // |fs2 * d| < 2^22 is guaranteed when |fs2| < 2^22 / r_cut
-    const float fs2_max = 4194304.0f / sqrtf(rcmax2) * 0.999f;
+    const float fs2_max = fs2_max_of(pt);
     const bool single = pt.nsp == 1;
     if (!half) {
         if (single && !with_energy)
-            k_force_mixed_full<true, false><<<g.nblock, FULL_THREADS, smem, st>>>(s, g, pt, to, tile_cap, fs2_max);
+            k_force_mixed_full<true, false, FM_FORCE><<<g.nblock, FULL_THREADS, smem, st>>>(s, g, pt, to, tile_cap,
+                                                                                          fs2_max, nullptr, 0.0, 0.f);
         else if (single)
-            k_force_mixed_full<true, true><<<g.nblock, FULL_THREADS, smem, st>>>(s, g, pt, to, tile_cap, fs2_max);
+            k_force_mixed_full<true, true, FM_FORCE><<<g.nblock, FULL_THREADS, smem, st>>>(s, g, pt, to, tile_cap,
+                                                                                         fs2_max, nullptr, 0.0, 0.f);
         else if (!with_energy)
-            k_force_mixed_full<false, false><<<g.nblock, FULL_THREADS, smem, st>>>(s, g, pt, to, tile_cap, fs2_max);
+            k_force_mixed_full<false, false, FM_FORCE><<<g.nblock, FULL_THREADS, smem, st>>>(s, g, pt, to, tile_cap,
+                                                                                           fs2_max, nullptr, 0.0, 0.f);
         else
-            k_force_mixed_full<false, true><<<g.nblock, FULL_THREADS, smem, st>>>(s, g, pt, to, tile_cap, fs2_max);
+            k_force_mixed_full<false, true, FM_FORCE><<<g.nblock, FULL_THREADS, smem, st>>>(s, g, pt, to, tile_cap,
+                                                                                          fs2_max, nullptr, 0.0, 0.f);
         return;
     }
     cudaMemsetAsync(s.fq, 0, sizeof(long long) * 3 * (size_t)s.n, st);
@@ -739,6 +794,33 @@ void launch_forces_mixed(const DevState& s, const Geometry& g, const PairTable& 
             k_force_mixed_half<false, false><<<per, F_THREADS, smem, st>>>(s, g, pt, to, tile_cap, fs2_max, b0);
         else
             k_force_mixed_half<false, true><<<per, F_THREADS, smem, st>>>(s, g, pt, to, tile_cap, fs2_max, b0);
+    }
+}
+
+// Full-list mixed forces fused with velocity Verlet (mode FM_KICK: closing half kick;
+// FM_KKD: closing + opening kick and drift, new FP32 coordinates into xr_out).
+void launch_forces_mixed_fused(const DevState& s, const Geometry& g, const PairTable& pt, const TileOffsets& to,
+                               int tile_cap, int mode, float4* xr_out, double dt, double lim2, cudaStream_t st) {
+    if (s.n == 0) return;
+    const size_t smem = force_smem_bytes(1, 0, 0, tile_cap);
+    const float fs2_max = fs2_max_of(pt);
+    // the FP32 displacement test is slightly stricter than skin/2 (as in k_integrate)
+    const float lim2_f = (float)(lim2 * (1.0 - 1e-4));
+    const bool single = pt.nsp == 1;
+    if (mode == FM_KICK) {
+        if (single)
+            k_force_mixed_full<true, false, FM_KICK><<<g.nblock, FULL_THREADS, smem, st>>>(s, g, pt, to, tile_cap,
+                                                                                         fs2_max, xr_out, dt, lim2_f);
+        else
+            k_force_mixed_full<false, false, FM_KICK><<<g.nblock, FULL_THREADS, smem, st>>>(s, g, pt, to, tile_cap,
+                                                                                          fs2_max, xr_out, dt, lim2_f);
+    } else {
+        if (single)
+            k_force_mixed_full<true, false, FM_KKD><<<g.nblock, FULL_THREADS, smem, st>>>(s, g, pt, to, tile_cap,
+                                                                                        fs2_max, xr_out, dt, lim2_f);
+        else
+            k_force_mixed_full<false, false, FM_KKD><<<g.nblock, FULL_THREADS, smem, st>>>(s, g, pt, to, tile_cap,
+                                                                                         fs2_max, xr_out, dt, lim2_f);
     }
 }
 

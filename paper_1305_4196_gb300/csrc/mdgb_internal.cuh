@@ -146,6 +146,9 @@ size_t build_lists_smem(int list_cap, int tile_cap);
 void launch_forces_mixed(const DevState& s, const Geometry& g, const PairTable& pt, const TileOffsets& to,
                          int tile_cap, int half, int with_energy, cudaStream_t st);
 size_t force_smem_bytes(int mixed, int half, int with_energy, int tile_cap);
+void launch_forces_mixed_fused(const DevState& s, const Geometry& g, const PairTable& pt, const TileOffsets& to,
+                               int tile_cap, int mode, float4* xr_out, double dt, double lim2, cudaStream_t st);
+enum { FUSE_KICK = 1, FUSE_KICK_KICK_DRIFT = 2 };  // modes of launch_forces_mixed_fused
 void launch_forces_fp64(const DevState& s, const Geometry& g, const PairTable& pt, int tile_cap, int half,
                         int with_energy, cudaStream_t st);
 void launch_integrate(const DevState& s, const Geometry& g, const PairTable& pt, int mode, int mixed,

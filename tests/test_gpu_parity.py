@@ -188,6 +188,45 @@ def test_multispecies_per_pair_cutoff():
             assert np.abs(vir - vir_ref).max() <= tol * np.abs(vir_ref[:3]).max()
 
 
+def test_dense_blocks_cooperative_tail():
+    """At rho* = 1.5 a 2x2x2-cell block holds several hundred atoms, more than a force CTA
+    has threads: the atoms past the first pass are shared out over the whole CTA.  Forces
+    match the oracle, and a permuted input (which moves different atoms into that tail
+    pass) gives bit-identical forces; energy and virial launches match too."""
+    sysm = W.lj_fcc(12, rho=1.5, seed=4, jitter=0.03)
+    s = make(sysm, "mixed", "full")
+    F = s.forces()
+    Fref, pe_ref, vir_ref = O.lj_forces(sysm.pos, sysm.box, O.LJParams.single())
+    assert force_error(F, Fref) <= TOL["mixed"]
+    perm = np.argsort(W.splitmix64(5, 3, sysm.n))
+    sp = W.System(sysm.pos[perm], sysm.vel[perm], sysm.species[perm], sysm.box)
+    assert np.array_equal(make(sp, "mixed", "full").forces(), F[perm])
+    pe, _, vir = s.energy_virial()
+    assert abs(pe - pe_ref) <= 1e-6 * abs(pe_ref)
+    assert np.abs(vir - vir_ref).max() <= 1e-6 * np.abs(vir_ref[:3]).max()
+
+
+@pytest.mark.parametrize("lst", ["full", "half"])
+def test_close_pairs_take_the_exact_wide_path(lst):
+    """Pairs at 0.6 sigma carry forces far above 2048 eps/sigma, beyond the two-part
+    fixed-point split: those atoms go through the exact FP64 path and still match the
+    oracle, bit-identically for any input order."""
+    sysm = liquid()
+    pos = sysm.pos.copy()
+    rng = np.random.default_rng(11)
+    for i in rng.choice(sysm.n // 2, 12, replace=False):
+        j = sysm.n - 1 - i
+        u = rng.normal(size=3)
+        pos[j] = W.wrap(pos[i] + 0.6 * u / np.linalg.norm(u), sysm.box)
+    dense = W.System(pos, sysm.vel, sysm.species, sysm.box)
+    F = make(dense, "mixed", lst).forces()
+    Fref, _, _ = O.lj_forces(pos, sysm.box, O.LJParams.single())
+    assert np.abs(F).max() > 1e4
+    assert force_error(F, Fref) <= TOL["mixed"]
+    perm = np.argsort(W.splitmix64(6, 3, sysm.n))
+    sp = W.System(pos[perm], sysm.vel[perm], sysm.species[perm], sysm.box)
+    assert np.array_equal(make(sp, "mixed", lst).forces(), F[perm])
+
 # ---------------------------------------------------------------- energies
 @pytest.mark.parametrize("lst", ["full", "half"])
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
@@ -250,6 +289,29 @@ def test_graph_and_direct_launch_give_identical_steps(precision, monkeypatch):
     assert np.array_equal(pa, pb) and np.array_equal(va, vb) and np.array_equal(ia, ib)
     assert a.info()["n_builds"] == b.info()["n_builds"]
 
+
+@pytest.mark.parametrize("graphs", [True, False])
+def test_fused_steps_equal_separate_kernels(graphs, monkeypatch):
+    """On the full-list mixed path the force kernel also performs the velocity-Verlet
+    updates (double-buffered FP32 coordinates).  Over several md_step calls of uneven
+    length, with rebuilds, that gives bit-identical positions, velocities and forces to
+    separate force and integration kernels (MDGB_NO_FUSE=1), in graph and direct mode."""
+    if not graphs:
+        monkeypatch.setenv("MDGB_NO_GRAPHS", "1")
+    sysm = W.lj_fcc(12, seed=8)
+    a = make(sysm, "mixed", "full")
+    monkeypatch.setenv("MDGB_NO_FUSE", "1")
+    b = make(sysm, "mixed", "full")
+    for n in (1, 37, 2, 120):
+        a.step(n)
+        b.step(n)
+    pa, va, ia = a.get_state()
+    pb, vb, ib = b.get_state()
+    assert np.array_equal(pa, pb) and np.array_equal(va, vb) and np.array_equal(ia, ib)
+    assert np.array_equal(a.forces(), b.forces())
+    assert a.info()["n_builds"] == b.info()["n_builds"] > 2
+    ea, eb = a.energy_virial(), b.energy_virial()
+    assert ea[0] == eb[0] and ea[1] == eb[1] and np.array_equal(ea[2], eb[2])
 
 def test_mixed_trajectory_short():
     sysm = W.lj_fcc(10, seed=1)
