@@ -329,6 +329,105 @@ void orc_lj_forces_subset(int64_t n, const double *x, const double *box, const i
     }
 }
 
+/* ------------------------------------------------------- gradients */
+
+/*
+ * Reverse-mode derivatives of the Lennard-Jones forces, for force matching.
+ * L is any scalar function of the forces; G = dL/dF is given (N x 3).  With
+ * f_ij = g(r^2) d the force of pair (i,j) on i (d = x_i - x_j), the chain rule
+ * over the pairs closer than their cutoff (the pair set held fixed: the cutoff
+ * itself contributes no derivative) gives, with w = G_i - G_j:
+ *   dL/dx_i += g w + 2 g' (w . d) d,   dL/dx_j -= the same      (Hessian-vector product)
+ *   dL/deps_ab += (w . d) g / eps
+ *   dL/dsig_ab += (w . d) dg/dsig,  dg/dsig = 144 eps (4 s6^2 - s6) / (sig r^2)
+ * where g = 24 eps (2 s6^2 - s6) / r^2, s6 = (sig^2 / r^2)^3 and
+ * g' = dg/d(r^2) = 24 eps (4 s6 - 14 s6^2) / r^4.
+ * The species tables are symmetric: the derivative with respect to the shared value
+ * of an unordered species pair {a,b} is written to both [a][b] and [b][a].
+ * Also the energy's parameter derivatives dE/deps_ab = sum u / eps and
+ * dE/dsig_ab = sum 24 eps (2 s6^2 - s6) / sig (nullable outputs).
+ */
+typedef struct {
+    int32_t nsp;
+    const double *eps, *sig, *rc;
+    const int32_t *species;
+    const double *G;
+    double *gx;
+    csum *geps, *gsig, *eeps, *esig; /* per unordered species pair, index a * nsp + b with a <= b */
+} lj_grad_acc;
+
+static void lj_grad_pair(void *ctx, int64_t i, int64_t j, const double d[3], double r2)
+{
+    lj_grad_acc *a = (lj_grad_acc *)ctx;
+    int32_t si = a->species ? a->species[i] : 0;
+    int32_t sj = a->species ? a->species[j] : 0;
+    int32_t t = si * a->nsp + sj;
+    double rc = a->rc[t];
+    if (!(r2 < rc * rc)) return;
+    int32_t u = si <= sj ? si * a->nsp + sj : sj * a->nsp + si;
+    double s = a->sig[t];
+    double e = a->eps[t];
+    double sr2 = (s * s) / r2;
+    double s6 = sr2 * sr2 * sr2;
+    double g = 24.0 * e * (2.0 * s6 * s6 - s6) / r2;
+    if (a->G) {
+        double w[3], wd = 0.0;
+        for (int k = 0; k < 3; ++k) {
+            w[k] = a->G[3 * i + k] - a->G[3 * j + k];
+            wd += w[k] * d[k];
+        }
+        double gp = 24.0 * e * (4.0 * s6 - 14.0 * s6 * s6) / (r2 * r2);
+        for (int k = 0; k < 3; ++k) {
+            double h = g * w[k] + 2.0 * gp * wd * d[k];
+            a->gx[3 * i + k] += h;
+            a->gx[3 * j + k] -= h;
+        }
+        csum_add(&a->geps[u], wd * (g / e));
+        csum_add(&a->gsig[u], wd * (144.0 * e * (4.0 * s6 * s6 - s6) / (s * r2)));
+    }
+    if (a->eeps) {
+        csum_add(&a->eeps[u], 4.0 * (s6 * s6 - s6));
+        csum_add(&a->esig[u], 24.0 * e * (2.0 * s6 * s6 - s6) / s);
+    }
+}
+
+void orc_lj_grad(int64_t n, const double *x, const double *box, const int32_t *species, int32_t nsp,
+                 const double *eps, const double *sig, const double *rc, const double *G, double *gx,
+                 double *geps, double *gsig, double *dE_deps, double *dE_dsig)
+{
+    csum acc[4][64];
+    memset(acc, 0, sizeof(acc));
+    lj_grad_acc a;
+    memset(&a, 0, sizeof(a));
+    a.nsp = nsp;
+    a.eps = eps;
+    a.sig = sig;
+    a.rc = rc;
+    a.species = species;
+    a.G = G;
+    a.gx = gx;
+    a.geps = acc[0];
+    a.gsig = acc[1];
+    if (dE_deps) {
+        a.eeps = acc[2];
+        a.esig = acc[3];
+    }
+    if (G) memset(gx, 0, sizeof(double) * 3 * (size_t)n);
+    for_each_pair(n, x, box, max_cut(nsp, rc), 0, lj_grad_pair, &a);
+    for (int32_t p = 0; p < nsp; ++p)
+        for (int32_t q = 0; q < nsp; ++q) {
+            int32_t u = p <= q ? p * nsp + q : q * nsp + p;
+            if (G) {
+                geps[p * nsp + q] = csum_get(&acc[0][u]);
+                gsig[p * nsp + q] = csum_get(&acc[1][u]);
+            }
+            if (dE_deps) {
+                dE_deps[p * nsp + q] = csum_get(&acc[2][u]);
+                dE_dsig[p * nsp + q] = csum_get(&acc[3][u]);
+            }
+        }
+}
+
 /* ------------------------------------------------------- integration */
 
 /* Kinetic energy 1/2 sum m v^2 (mass per species). */

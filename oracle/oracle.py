@@ -65,6 +65,9 @@ def _configure(lib):
                                          C.c_int64, _lp, _dp, C.c_void_p, C.c_void_p]
     lib.orc_kinetic.restype = C.c_double
     lib.orc_kinetic.argtypes = [C.c_int64, _dp, C.c_void_p, _dp]
+    lib.orc_lj_grad.restype = None
+    lib.orc_lj_grad.argtypes = [C.c_int64, _dp, _dp, C.c_void_p, C.c_int32, _dp, _dp, _dp, C.c_void_p,
+                                C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
     lib.orc_run_nve.restype = C.c_int64
     lib.orc_run_nve.argtypes = [C.c_int64, _dp, _dp, _ip, _dp, C.c_void_p, C.c_int32, _dp, _dp, _dp,
                                 _dp, C.c_double, C.c_double, C.c_int32, C.c_int32, C.c_int64,
@@ -159,6 +162,39 @@ def lj_forces(pos, box, params: LJParams, species=None, brute=False, per_atom=Fa
     if per_atom:
         return f, float(pe[0]), vir, pea
     return f, float(pe[0]), vir
+
+
+def lj_force_grad(pos, box, params: LJParams, G, species=None):
+    """Reverse-mode derivatives of a scalar L(F) with dL/dF = G (N,3): returns
+    (dL/dx (N,3), dL/deps (nsp,nsp), dL/dsig (nsp,nsp)) over the pairs inside their cutoffs
+    (pair set held fixed).  Symmetric tables: entry [a][b] = [b][a] is the derivative with
+    respect to the shared value of the species pair {a,b}."""
+    lib = _load()
+    pos = _c(pos, np.float64)
+    box = _c(box, np.float64)
+    G = _c(G, np.float64)
+    n = pos.shape[0]
+    gx = np.zeros((n, 3))
+    ge = np.zeros((params.nsp, params.nsp))
+    gs = np.zeros((params.nsp, params.nsp))
+    sp = _sp(species)
+    lib.orc_lj_grad(n, pos.ravel(), box, sp[1] if sp else None, params.nsp, params.eps.ravel(), params.sig.ravel(),
+                    params.rc.ravel(), G.ctypes.data, gx.ctypes.data, ge.ctypes.data, gs.ctypes.data, None, None)
+    return gx, ge, gs
+
+
+def lj_energy_param_grad(pos, box, params: LJParams, species=None):
+    """(dE/deps, dE/dsig) as (nsp,nsp) tables (same convention as lj_force_grad)."""
+    lib = _load()
+    pos = _c(pos, np.float64)
+    box = _c(box, np.float64)
+    n = pos.shape[0]
+    de = np.zeros((params.nsp, params.nsp))
+    ds = np.zeros((params.nsp, params.nsp))
+    sp = _sp(species)
+    lib.orc_lj_grad(n, pos.ravel(), box, sp[1] if sp else None, params.nsp, params.eps.ravel(), params.sig.ravel(),
+                    params.rc.ravel(), None, None, None, None, de.ctypes.data, ds.ctypes.data)
+    return de, ds
 
 
 def lj_forces_pairs(pos, box, params: LJParams, pairs, species=None):

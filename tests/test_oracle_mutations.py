@@ -29,7 +29,16 @@ MUTATIONS = {
                           "double sr2 = s / r2;\n    double s6 = sr2 * sr2 * sr2;\n    double u"),
     "rebuild_threshold_full_skin": ("const double half_skin = 0.5 * skin;", "const double half_skin = skin;"),
     "wrap_image_sign": ("image[3 * i + k] += 1;", "image[3 * i + k] -= 1;"),
-    "species_index_transposed": ("int32_t t = si * a->nsp + sj;", "int32_t t = si * a->nsp + si;"),
+    "species_index_transposed": ("int32_t t = si * a->nsp + sj;\n    double rc = a->rc[t];\n    if (!(r2 < rc * rc)) return;\n    double s = a->sig[t];",
+                                 "int32_t t = si * a->nsp + si;\n    double rc = a->rc[t];\n    if (!(r2 < rc * rc)) return;\n    double s = a->sig[t];"),
+    "grad_gprime_factor": ("(4.0 * s6 - 14.0 * s6 * s6)", "(4.0 * s6 - 12.0 * s6 * s6)"),
+    "grad_sigma_factor": ("144.0 * e * (4.0 * s6 * s6 - s6)", "72.0 * e * (4.0 * s6 * s6 - s6)"),
+    "grad_w_sign": ("w[k] = a->G[3 * i + k] - a->G[3 * j + k];", "w[k] = a->G[3 * i + k] + a->G[3 * j + k];"),
+    "grad_hessian_rank1_factor": ("double h = g * w[k] + 2.0 * gp * wd * d[k];", "double h = g * w[k] + gp * wd * d[k];"),
+    "grad_energy_sigma": ("csum_add(&a->esig[u], 24.0 * e * (2.0 * s6 * s6 - s6) / s);",
+                          "csum_add(&a->esig[u], 24.0 * e * (s6 * s6 - s6) / s);"),
+    "grad_pair_index_unordered": ("int32_t u = si <= sj ? si * a->nsp + sj : sj * a->nsp + si;",
+                                  "int32_t u = si * a->nsp + sj;"),
 }
 
 

@@ -20,7 +20,12 @@ fails at least one of them:
   * sum of forces = 0, translation and permutation invariance;
   * velocity Verlet is second order and time reversible; the skin/2 rebuild
     rule fires at the step the kinematics dictate;
-  * the direct per-atom summation agrees with the cell-list whole-system path.
+  * the direct per-atom summation agrees with the cell-list whole-system path;
+  * force-matching gradients: central finite differences of the oracle's forces
+    with respect to every species-pair parameter and to positions, a dimer's
+    closed-form derivatives, and exact scaling identities (L is linear in eps;
+    forces are homogeneous of degree -1 in all lengths; sigma dE/dsigma summed
+    is the virial trace).
 """
 import math
 
@@ -371,3 +376,105 @@ def test_generators():
     assert 0.0 < u.min() and u.max() < 1.0 and abs(u.mean() - 0.5) < 0.005
     z = W.normal(5, 0, 100000)
     assert abs(z.mean()) < 0.01 and abs(z.std() - 1.0) < 0.01
+
+
+# ---------------------------------------------------------------- force-matching gradients
+_KA = dict(eps=[[1.0, 1.5], [1.5, 0.5]], sig=[[1.0, 0.8], [0.8, 0.88]])
+
+
+def _ka_small(seed, rc=2.2):
+    """Two-species jittered fcc (Kob-Andersen parameters, a fixed cutoff table)."""
+    s = W.lj_fcc(3, rho=1.2, seed=seed, jitter=0.06)
+    sp = W.species_shuffle(s.n, 0.2, seed)
+    P = O.LJParams(_KA["eps"], _KA["sig"], [[rc, rc], [rc, rc]], [1.0, 1.0])
+    return s, sp, P
+
+
+def test_force_grad_matches_finite_differences():
+    """dL/d(eps_ab, sig_ab) and dL/dx for L = sum G . F with a random G, against central
+    differences of the oracle's forces (pair set away from the cutoff, so it stays fixed)."""
+    for seed in range(1, 40):
+        s, sp, P = _ka_small(seed)
+        if _safe_from_cutoff(s.pos, s.box, 2.2, 1e-4):
+            break
+    else:
+        pytest.skip("no seed without a pair near the cutoff")
+    G = np.random.default_rng(seed).normal(size=(s.n, 3))
+    gx, ge, gs = O.lj_force_grad(s.pos, s.box, P, G, sp)
+
+    def L(eps, sig, pos):
+        return float((G * O.lj_forces(pos, s.box, O.LJParams(eps, sig, P.rc, P.mass), sp)[0]).sum())
+
+    h = 1e-6
+    for a, b in [(0, 0), (0, 1), (1, 1)]:
+        for table, grad in [("eps", ge), ("sig", gs)]:
+            lo = {"eps": P.eps.copy(), "sig": P.sig.copy()}
+            hi = {"eps": P.eps.copy(), "sig": P.sig.copy()}
+            for t, sgn in [(hi, 1.0), (lo, -1.0)]:
+                t[table][a, b] += sgn * h
+                if a != b:
+                    t[table][b, a] += sgn * h
+            fd = (L(hi["eps"], hi["sig"], s.pos) - L(lo["eps"], lo["sig"], s.pos)) / (2 * h)
+            assert grad[a, b] == grad[b, a]
+            assert fd == pytest.approx(grad[a, b], rel=1e-6, abs=1e-6)
+    for i in [0, 3, 50, 97]:
+        for k in range(3):
+            xp, xm = s.pos.copy(), s.pos.copy()
+            xp[i, k] += h
+            xm[i, k] -= h
+            fd = (L(P.eps, P.sig, xp) - L(P.eps, P.sig, xm)) / (2 * h)
+            assert fd == pytest.approx(gx[i, k], rel=1e-6, abs=1e-6)
+
+
+def test_force_grad_dimer_closed_form():
+    """Dimer along x at distance r, L = F_x on the first atom = 24 eps (2 s^12/r^13 - s^6/r^7):
+    dL/dx_1 = 24 eps (-26 s^12/r^14 + 7 s^6/r^8) along x, 0 across; dL/deps = L/eps;
+    dL/dsig = 24 eps (24 s^11/r^13 - 6 s^5/r^7)."""
+    eps, sig, r = 0.7, 1.3, 1.37
+    box = np.array([40.0, 40.0, 40.0])
+    pos = np.array([[20.0 + r, 20.0, 20.0], [20.0, 20.0, 20.0]])
+    P = O.LJParams.single(eps=eps, sig=sig, rc=4.0)
+    G = np.zeros((2, 3))
+    G[0, 0] = 1.0
+    gx, ge, gs = O.lj_force_grad(pos, box, P, G)
+    L = 24 * eps * (2 * sig ** 12 / r ** 13 - sig ** 6 / r ** 7)
+    assert O.lj_forces(pos, box, P)[0][0, 0] == pytest.approx(L, rel=1e-14)
+    assert gx[0, 0] == pytest.approx(24 * eps * (-26 * sig ** 12 / r ** 14 + 7 * sig ** 6 / r ** 8), rel=1e-13)
+    assert gx[1, 0] == pytest.approx(-gx[0, 0], rel=1e-15)
+    assert np.all(gx[:, 1:] == 0.0)
+    assert ge[0, 0] == pytest.approx(L / eps, rel=1e-13)
+    assert gs[0, 0] == pytest.approx(24 * eps * (24 * sig ** 11 / r ** 13 - 6 * sig ** 5 / r ** 7), rel=1e-13)
+
+
+def test_force_grad_scaling_identities():
+    """Exact identities of the analytic gradient (no finite differences): L = G . F is linear
+    in eps, so sum eps dL/deps = L; F is homogeneous of degree -1 under scaling all lengths
+    (positions and sigma, pair set fixed), so sum sig dL/dsig + sum x . dL/dx = -L for an
+    isolated cluster; and translation invariance gives sum_k dL/dx_k = 0."""
+    rng = np.random.default_rng(3)
+    s, sp, P = _ka_small(5)
+    box = np.array([60.0, 60.0, 60.0])
+    pos = W.fcc_lattice(2, 2, 2, 1.35)[0] + 25.0 + rng.normal(scale=0.05, size=(32, 3))
+    sp = (np.arange(32) % 4 == 0).astype(np.int32)
+    P = O.LJParams(_KA["eps"], _KA["sig"], [[9.0, 9.0], [9.0, 9.0]], [1.0, 1.0])
+    G = rng.normal(size=(32, 3))
+    F = O.lj_forces(pos, box, P, sp)[0]
+    L = float((G * F).sum())
+    gx, ge, gs = O.lj_force_grad(pos, box, P, G, sp)
+    # each unordered species pair once: diagonal entries plus one off-diagonal entry
+    uniq = [(0, 0), (0, 1), (1, 1)]
+    assert sum(P.eps[a, b] * ge[a, b] for a, b in uniq) == pytest.approx(L, rel=1e-12)
+    assert sum(P.sig[a, b] * gs[a, b] for a, b in uniq) + float((pos * gx).sum()) == pytest.approx(
+        -L, rel=1e-10, abs=1e-10 * np.abs(G * F).sum())
+    assert np.abs(gx.sum(axis=0)).max() <= 1e-11 * np.abs(gx).sum()
+
+
+def test_energy_param_grad_identities():
+    """E is linear in eps (sum eps dE/deps = E) and, per pair, sig dE/dsig = d . f, so
+    sum sig dE/dsig equals the virial trace W_xx + W_yy + W_zz (periodic system)."""
+    s, sp, P = _ka_small(7)
+    _, pe, vir = O.lj_forces(s.pos, s.box, P, sp)
+    de, ds = O.lj_energy_param_grad(s.pos, s.box, P, sp)
+    uniq = [(0, 0), (0, 1), (1, 1)]
+    assert sum(P.eps[a, b] * de[a, b] for a, b in uniq) == pytest.approx(pe, rel=1e-12)
+    assert sum(P.sig[a, b] * ds[a, b] for a, b in uniq) == pytest.approx(vir[0] + vir[1] + vir[2], rel=1e-12)
