@@ -409,6 +409,7 @@ def comparisons(args, sysm, M, stream, value, list_len_hom):
                                 "mean_list_length_homogeneous": list_len_hom,
                                 "per_atom_cost_vs_homogeneous": ns_inh / ns_hom}
         s.close()
+    out["force_matching"] = force_matching_timing(M, stream)
     runs = []
     if args.precision == "mixed":
         runs.append(("fp64_gpu", M.MD_FP64, M.MD_LIST_FULL, 10, 2))
@@ -435,6 +436,56 @@ def comparisons(args, sysm, M, stream, value, list_len_hom):
     if "fp64_gpu" in out:
         out["speedup_mixed_vs_fp64_gpu"] = value / out["fp64_gpu"]["value"]
     return {"compare": out}
+
+
+def force_matching_timing(M, stream, n_snap=8):
+    """Forward + backward (md_forces, md_forces_backward) of the force-matching loss on
+    32,000-atom Kob-Andersen snapshots (fcc sites at rho* = 1.2, 80:20 species shuffle, 0.05
+    sigma jitter per snapshot seed), at parameters perturbed by 10 %, FP64 and mixed."""
+    import torch
+    from paper_1305_4196_gb300 import workloads as W
+    eps0 = np.array([[1.0, 1.5], [1.5, 0.5]])
+    sig0 = np.array([[1.0, 0.8], [0.8, 0.88]])
+    eps1 = eps0 * np.array([[1.1, 0.9], [0.9, 1.1]])
+    sig1 = sig0 * np.array([[0.9, 1.1], [1.1, 0.9]])
+    snaps = []
+    for k in range(n_snap):
+        w = W.lj_fcc(20, rho=1.2, seed=100 + k, jitter=0.05)
+        snaps.append((torch.as_tensor(w.pos, device="cuda"),
+                      torch.as_tensor(W.species_shuffle(w.n, 0.2, 100 + k), dtype=torch.int32, device="cuda")))
+    box = w.box
+    res = {"workload": "Kob-Andersen 80:20, 32,000 atoms per snapshot", "snapshots": n_snap}
+    for name, prec in [("fp64", M.MD_FP64), ("mixed", M.MD_MIXED)]:
+        s = M.System(w.n, box, r_cut=2.5 * 1.1, skin=0.3, eps=eps0, sigma=sig0, mass=[1.0, 1.0], precision=prec,
+                     rcut=2.5 * sig0 * 1.1, stream=stream.cuda_stream)
+        zeros = torch.zeros_like(snaps[0][0])
+        F = torch.empty_like(zeros)
+        T = torch.empty_like(zeros)
+        gpos = torch.empty_like(zeros)
+
+        def one(pos, sp):
+            # torch work below runs on the library's stream, so it is ordered with its kernels
+            s.set_params(eps0, sig0, 2.5 * sig0)
+            s.set_state(pos, zeros, sp)
+            s.forces(out=T)
+            s.set_params(eps1, sig1, 2.5 * sig1)
+            s.forces(out=F)
+            G = (2.0 / F.numel()) * (F - T)
+            return s.forces_backward(G, gpos)
+
+        torch.cuda.synchronize()
+        with torch.cuda.stream(stream):
+            one(*snaps[0])
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for pos, sp in snaps:
+                one(pos, sp)
+            torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        res[name] = {"ms_per_snapshot": 1e3 * dt / n_snap,
+                     "note": "target forces, perturbed forces and the backward pass per snapshot"}
+        s.close()
+    return res
 
 
 def main():

@@ -176,6 +176,47 @@ int md_step(md_system *s, int32_t n_steps);
 int md_energy_virial(md_system *s, double *pe, double *ke, double virial[6]);
 
 /*
+ * Replace the pair parameters (n_species x n_species row-major, symmetric; rcut
+ * may be NULL for the r_cut given at creation).  No cutoff may exceed the
+ * largest one the system was created with (the cell grid and list radius were
+ * sized from it).  The neighbour lists stay valid; forces are recomputed on the
+ * next call that needs them.  Host arrays.  Errors: MD_ERR_ARG.
+ * No counterpart in the paper (the parameter-derivative functions below are
+ * the force-matching extension).
+ */
+int md_set_params(md_system *s, const double *eps, const double *sigma, const double *rcut);
+
+/*
+ * Reverse-mode derivatives for force matching.  For a scalar loss L of the
+ * forces at the current state, with grad_f = dL/dF (N x 3, original order)
+ * given, writes
+ *   grad_pos   dL/dx (N x 3, original order), NULL to skip;
+ *   grad_eps   dL/deps, n_species x n_species, NULL to skip;
+ *   grad_sigma dL/dsigma, likewise;
+ * over the pairs inside their cutoffs, the pair set held fixed (the cutoff
+ * contributes no derivative).  Per pair (i,j), d = x_i - x_j, f_ij = g d and
+ * w = G_i - G_j: dL/dx_i += g w + 2 (dg/dr^2) (w.d) d and the negative on x_j;
+ * dL/deps_ab += (w.d) g/eps; dL/dsig_ab += (w.d) dg/dsig.  The tables are
+ * symmetric: entry [a][b] = [b][a] is the derivative with respect to the value
+ * shared by the species pair {a,b}.  Arithmetic: FP64 on MD_FP64 systems;
+ * FP32 pair terms (FP64 sums of the parameter terms) on MD_MIXED ones.  Needs
+ * MD_LIST_FULL.  grad_f and grad_pos are device pointers when device_ptrs != 0;
+ * the tables are host arrays.  Deterministic; synchronises.
+ * Errors: MD_ERR_ARG (half lists, NULL grad_f), MD_ERR_STATE, MD_ERR_CUDA.
+ */
+int md_forces_backward(md_system *s, const double *grad_f, int device_ptrs, double *grad_pos,
+                       double *grad_eps, double *grad_sigma);
+
+/*
+ * Derivatives of the potential energy with respect to the pair parameters at
+ * the current state: dE/deps_ab = sum 4 (s6^2 - s6), dE/dsig_ab = sum
+ * 24 eps (2 s6^2 - s6)/sig over the pairs inside their cutoffs (s6 =
+ * (sig/r)^6); same table convention and arithmetic as md_forces_backward.
+ * (dE/dx is minus the force, md_forces.)  Host outputs; synchronises.
+ */
+int md_energy_param_grad(md_system *s, double *de_deps, double *de_dsigma);
+
+/*
  * Copy the state out in original order: positions as stored (unwrapped since
  * the last build; add image * L for fully unwrapped coordinates), velocities
  * and image counters (N x 3 int32).  Any output may be NULL.

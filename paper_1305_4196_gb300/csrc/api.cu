@@ -26,6 +26,7 @@ struct md_system {
     TileOffsets to{};
     double box[3] = {0, 0, 0};
     double rcut = 0, skin = 0, rl = 0, rl2 = 0, dt = 0, lim2 = 0;
+    double rcut_default = 0;  // r_cut argument of md_create (pairs without a table entry)
     int precision = MD_MIXED, list_kind = MD_LIST_FULL, rebuild = MD_REBUILD_SKIN_HALF, rebuild_k = 10;
     int list_cap = 0, tile_cap = 0;
     DevState st[3]{};  // [0] the state, [1] scratch for the reorder gather, [2] snapshot for redo
@@ -347,6 +348,27 @@ int ensure_lists(md_system* s) {
     if (!s->has_state) return fail(s, MD_ERR_STATE, "no state: call md_set_state first");
     if (!s->lists_valid) return do_build(s);
     return MD_OK;
+}
+
+// LJ constants of every species pair (FP64 and the mixed path's FP32 copies); returns the
+// largest cutoff.  rcut may be NULL (r_cut for every pair).
+double fill_pair_table(PairTable& pt, const double* eps, const double* sigma, const double* rcut, double r_cut) {
+    double rcmax = 0.0;
+    for (int t = 0; t < pt.nsp * pt.nsp; ++t) {
+        const double e = eps[t], sg = sigma[t];
+        const double rc_t = rcut ? rcut[t] : r_cut;
+        rcmax = std::max(rcmax, rc_t);
+        pt.sig_d[t] = sg;
+        pt.sig2_d[t] = sg * sg;
+        pt.eps_d[t] = e;
+        pt.rc2_d[t] = rc_t * rc_t;
+        pt.sig2_f[t] = (float)(sg * sg);
+        pt.c48_f[t] = (float)(48.0 * e * 2048.0);
+        pt.c24_f[t] = (float)(24.0 * e * 2048.0);
+        pt.c4_f[t] = (float)(4.0 * e);
+        pt.rc2_f[t] = (float)(rc_t * rc_t);
+    }
+    return rcmax;
 }
 
 int validate_params(md_system* s, const md_params* p, double r_cut) {
@@ -755,6 +777,7 @@ int md_create(int64_t n, const double box[3], double r_cut, double skin, const m
     s->stream = static_cast<cudaStream_t>(p->stream);
     init_force_kernels();
     init_list_kernels();
+    init_grad_kernels();
     {
         const char* ng = std::getenv("MDGB_NO_GRAPHS");
         s->use_graphs = !(ng && ng[0] && ng[0] != '0');
@@ -773,26 +796,14 @@ int md_create(int64_t n, const double box[3], double r_cut, double skin, const m
     const int ns = p->n_species;
     PairTable& pt = s->pt;
     pt.nsp = ns;
-    double rcmax = 0.0;
-    for (int t = 0; t < ns * ns; ++t) {
-        const double e = p->eps[t], sg = p->sigma[t];
-        const double rc_t = p->rcut ? p->rcut[t] : r_cut;
-        rcmax = std::max(rcmax, rc_t);
-        pt.sig2_d[t] = sg * sg;
-        pt.eps_d[t] = e;
-        pt.rc2_d[t] = rc_t * rc_t;
-        pt.sig2_f[t] = (float)(sg * sg);
-        pt.c48_f[t] = (float)(48.0 * e * 2048.0);
-        pt.c24_f[t] = (float)(24.0 * e * 2048.0);
-        pt.c4_f[t] = (float)(4.0 * e);
-        pt.rc2_f[t] = (float)(rc_t * rc_t);
-    }
+    const double rcmax = fill_pair_table(pt, p->eps, p->sigma, p->rcut, r_cut);
     for (int a = 0; a < ns; ++a) {
         pt.mass[a] = p->mass[a];
         pt.hdtm[a] = (0.5 * p->dt) / p->mass[a];
         pt.hdtm_q[a] = pt.hdtm[a] * 0x1p-32;
     }
     s->rcut = rcmax;
+    s->rcut_default = r_cut;
     s->rl = rcmax + skin;
     s->rl2 = s->rl * s->rl;
     const double half_skin = 0.5 * skin;
@@ -1036,6 +1047,102 @@ int md_step(md_system* s, int32_t n_steps) {
     rc = sync_flags(s);
     if (rc) return rc;
     return check_err(s, ERR_NONFINITE | ERR_ESCAPE | ERR_SKIN);
+}
+
+int md_set_params(md_system* s, const double* eps, const double* sigma, const double* rcut) {
+    if (!s) return MD_ERR_ARG;
+    if (!eps || !sigma) return fail(s, MD_ERR_ARG, "eps and sigma are required");
+    const int ns = s->pt.nsp;
+    for (int a = 0; a < ns; ++a)
+        for (int b = 0; b < ns; ++b) {
+            const int t = a * ns + b, u = b * ns + a;
+            const double rc = rcut ? rcut[t] : s->rcut_default;
+            if (!(eps[t] >= 0.0) || !(sigma[t] > 0.0) || !(rc > 0.0) || !std::isfinite(eps[t]) ||
+                !std::isfinite(sigma[t]) || !std::isfinite(rc))
+                return fail(s, MD_ERR_ARG, "bad LJ parameters for pair (%d,%d)", a, b);
+            if (eps[t] != eps[u] || sigma[t] != sigma[u] || (rcut && rcut[t] != rcut[u]))
+                return fail(s, MD_ERR_ARG, "pair tables must be symmetric");
+            if (rc > s->rcut) return fail(s, MD_ERR_ARG, "cutoff %g exceeds the %g the lists were sized for", rc, s->rcut);
+        }
+    DeviceGuard dg(s->device);
+    // kernels read the table by value: queued work keeps the old one, captured graphs are redone
+    fill_pair_table(s->pt, eps, sigma, rcut, s->rcut_default);
+    s->forces_valid = false;
+    s->graphs_valid = false;
+    return MD_OK;
+}
+
+// dL/dx, dL/deps, dL/dsigma for dL/dF = grad_f, and/or dE/deps, dE/dsigma
+static int backward(md_system* s, const double* grad_f, int device_ptrs, double* grad_pos, double* grad_eps,
+                    double* grad_sigma, double* de_deps, double* de_dsig) {
+    if (!s) return MD_ERR_ARG;
+    DeviceGuard dg(s->device);
+    if (!s->has_state) return fail(s, MD_ERR_STATE, "no state: call md_set_state first");
+    if (half(s)) return fail(s, MD_ERR_ARG, "derivatives need full neighbour lists (MD_LIST_FULL)");
+    const int ns = s->pt.nsp;
+    const int ncol = ns * ns * 4;
+    std::vector<double> tot(ncol, 0.0);
+    if (s->n > 0) {
+        int rc = ensure_lists(s);
+        if (rc) return rc;
+        const int64_t n = s->n;
+        const int nparts = 256;
+        double* scratch = nullptr;
+        double *G = nullptr, *gx = nullptr;
+        CK(cudaMallocAsync(&scratch, sizeof(double) * backward_scratch_doubles(n, ns, nparts), s->stream));
+        if (grad_f) {
+            if (device_ptrs) {
+                G = const_cast<double*>(grad_f);
+            } else {
+                CK(cudaMallocAsync(&G, sizeof(double) * 3 * n, s->stream));
+                CK(cudaMemcpyAsync(G, grad_f, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, s->stream));
+            }
+        }
+        if (grad_pos) {
+            if (device_ptrs) gx = grad_pos;
+            else CK(cudaMallocAsync(&gx, sizeof(double) * 3 * n, s->stream));
+        }
+        const size_t smem = backward_smem_bytes(!mixed(s), s->tile_cap);
+        if (smem > 226 * 1024) return fail(s, MD_ERR_CELL_OVERFLOW, "tile of %d atoms exceeds shared memory", s->tile_cap);
+        launch_force_backward(s->st[0], s->g, s->pt, s->to, s->tile_cap, !mixed(s), G, gx, de_deps != nullptr, scratch,
+                              nparts, s->stream);
+        CKL();
+        s->launches += (G ? 1 : 0) + 1 + (gx ? 1 : 0) + 2;
+        const double* totals = scratch + backward_scratch_doubles(n, ns, nparts) - ncol;
+        CK(cudaMemcpyAsync(tot.data(), totals, sizeof(double) * ncol, cudaMemcpyDeviceToHost, s->stream));
+        if (grad_pos && !device_ptrs)
+            CK(cudaMemcpyAsync(grad_pos, gx, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, s->stream));
+        if (grad_f && !device_ptrs) CK(cudaFreeAsync(G, s->stream));
+        if (grad_pos && !device_ptrs) CK(cudaFreeAsync(gx, s->stream));
+        CK(cudaFreeAsync(scratch, s->stream));
+        if ((rc = sync_flags(s))) return rc;
+        if ((rc = check_err(s, ERR_NONFINITE | ERR_TILE_OVERFLOW))) return rc;
+    }
+    // column (s_i * ns + s_j) * 4 + q holds the terms of atoms of species s_i with neighbours
+    // of species s_j (each pair halved per side): the shared value of {a,b} gets both sides
+    for (int a = 0; a < ns; ++a)
+        for (int b = 0; b < ns; ++b) {
+            const double* ab = &tot[(a * ns + b) * 4];
+            const double* ba = &tot[(b * ns + a) * 4];
+            const int t = a * ns + b;
+            const double w = (a == b) ? 1.0 : 0.0;  // the diagonal entry already holds both sides
+            if (grad_eps) grad_eps[t] = ab[0] + (1.0 - w) * ba[0];
+            if (grad_sigma) grad_sigma[t] = ab[1] + (1.0 - w) * ba[1];
+            if (de_deps) de_deps[t] = ab[2] + (1.0 - w) * ba[2];
+            if (de_dsig) de_dsig[t] = ab[3] + (1.0 - w) * ba[3];
+        }
+    return MD_OK;
+}
+
+int md_forces_backward(md_system* s, const double* grad_f, int device_ptrs, double* grad_pos, double* grad_eps,
+                       double* grad_sigma) {
+    if (!s || !grad_f) return MD_ERR_ARG;
+    return backward(s, grad_f, device_ptrs, grad_pos, grad_eps, grad_sigma, nullptr, nullptr);
+}
+
+int md_energy_param_grad(md_system* s, double* de_deps, double* de_dsigma) {
+    if (!s || !de_deps || !de_dsigma) return MD_ERR_ARG;
+    return backward(s, nullptr, 0, nullptr, nullptr, nullptr, de_deps, de_dsigma);
 }
 
 int md_energy_virial(md_system* s, double* pe, double* ke, double virial[6]) {

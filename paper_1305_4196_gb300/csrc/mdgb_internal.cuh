@@ -45,7 +45,7 @@ struct Geometry {
 struct PairTable {
     int nsp;
     float sig2_f[MAX_PAIR], c48_f[MAX_PAIR], c24_f[MAX_PAIR], c4_f[MAX_PAIR], rc2_f[MAX_PAIR];
-    double sig2_d[MAX_PAIR], eps_d[MAX_PAIR], rc2_d[MAX_PAIR];
+    double sig_d[MAX_PAIR], sig2_d[MAX_PAIR], eps_d[MAX_PAIR], rc2_d[MAX_PAIR];
     double hdtm[MAX_SPECIES];  // (dt/2) / m per species
     double hdtm_q[MAX_SPECIES];  // (dt/2) / m * 2^-32: half kick per unit of Q31.32 force
     double mass[MAX_SPECIES];
@@ -164,6 +164,12 @@ void launch_pairs_out(const DevState& s, const Geometry& g, int half, unsigned l
                       int32_t* pairs, long long cap, cudaStream_t st);
 
 void init_force_kernels();
+void init_grad_kernels();
+size_t backward_smem_bytes(int fp64, int tile_cap);
+size_t backward_scratch_doubles(int64_t n, int nsp, int nparts);
+void launch_force_backward(const DevState& s, const Geometry& g, const PairTable& pt, const TileOffsets& to,
+                           int tile_cap, int fp64, const double* G, double* gx_orig, int want_energy,
+                           double* scratch, int nparts, cudaStream_t st);
 void init_list_kernels();
 
 // integrate modes

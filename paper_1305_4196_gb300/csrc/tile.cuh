@@ -132,4 +132,36 @@ __device__ __forceinline__ void tile_stage_f32(const TileMeta& m, const float4* 
     }
 }
 
+// Stage the FP64 tile of block b: coordinates relative to the block centre (periodic
+// images shifted by one box length where the tile wraps), species, and a dummy slot T
+// far outside every cutoff.
+__device__ __forceinline__ void tile_stage_f64(const DevState& s, const Geometry& g, const TileMeta& m, int b,
+                                               double* __restrict__ tx_, double* __restrict__ ty_,
+                                               double* __restrict__ tz_, int* __restrict__ tsp) {
+    int bx, by, bz;
+    block_coords(g, b, bx, by, bz);
+    const int T = m.prefix[64];
+    for (int u = threadIdx.x; u < T; u += blockDim.x) {
+        const int slot = tile_slot_of(m, u);
+        const int c = c_tiles.coord_of_idx[slot];
+        const int j = m.start[slot] + (u - m.prefix[slot]);
+        const int t3[3] = {c & 3, (c >> 2) & 3, c >> 4};
+        const int b3[3] = {bx, by, bz};
+        const double* X[3] = {s.x, s.y, s.z};
+        double* out[3] = {tx_, ty_, tz_};
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const int raw = 2 * b3[d] - 1 + t3[d];
+            const double shift = raw < 0 ? -g.L[d] : (raw >= g.nc[d] ? g.L[d] : 0.0);
+            const double centre = (2.0 * b3[d] + 1.0) * g.w[d];
+            out[d][u] = (X[d][j] + shift) - centre;
+        }
+        tsp[u] = s.species[j];
+    }
+    if (threadIdx.x == 0) {
+        tx_[T] = ty_[T] = tz_[T] = 1.0e4;
+        tsp[T] = 0;
+    }
+}
+
 }  // namespace mdgb

@@ -39,7 +39,8 @@ MD_REBUILD_EVERY_K = 1
 
 EXPORTED = ["md_create", "md_set_state", "md_bin_cells", "md_build_neighbors", "md_forces", "md_step",
             "md_energy_virial", "md_get_state", "md_get_neighbors", "md_get_cells", "md_get_info",
-            "md_set_timing", "md_last_error", "md_destroy", "md_kinetic_energy_noalloc"]
+            "md_set_timing", "md_last_error", "md_destroy", "md_kinetic_energy_noalloc", "md_set_params",
+            "md_forces_backward", "md_energy_param_grad"]
 
 
 class md_params(C.Structure):
@@ -87,6 +88,9 @@ def _load():
     lib.md_get_info.argtypes = [P, C.POINTER(md_info)]
     lib.md_set_timing.argtypes = [P, C.c_int]
     lib.md_kinetic_energy_noalloc.argtypes = [C.c_int64, P, P, C.POINTER(C.c_double), C.c_int32, P, P]
+    lib.md_set_params.argtypes = [P, P, P, P]
+    lib.md_forces_backward.argtypes = [P, P, C.c_int, P, P, P]
+    lib.md_energy_param_grad.argtypes = [P, P, P]
     lib.md_last_error.argtypes = [P, C.c_char_p, C.c_int64]
     lib.md_destroy.argtypes = [P]
     lib.md_destroy.restype = None
@@ -222,6 +226,33 @@ def md_kinetic_energy_noalloc(n, vel, species, mass, ke_out, stream=None):
                                           int(mass.shape[0]), op, C.c_void_p(stream) if stream else None)
 
 
+def md_set_params(handle, eps, sigma, rcut=None):
+    eps = np.ascontiguousarray(np.atleast_2d(eps), dtype=np.float64)
+    sigma = np.ascontiguousarray(np.atleast_2d(sigma), dtype=np.float64)
+    rc = None if rcut is None else np.ascontiguousarray(np.atleast_2d(rcut), dtype=np.float64)
+    _check(handle, _lib.md_set_params(handle, eps.ctypes.data, sigma.ctypes.data,
+                                      rc.ctypes.data if rc is not None else None))
+
+
+def md_forces_backward(handle, grad_f, grad_pos, nsp):
+    """dL/dx into grad_pos (same kind of array as grad_f: numpy or CUDA tensor, N x 3) and
+    (dL/deps, dL/dsigma) returned as nsp x nsp numpy tables."""
+    (gp, dev), (op, dev2) = _ptr(grad_f), _ptr(grad_pos)
+    if grad_pos is not None and bool(dev) != bool(dev2):
+        raise ValueError("grad_f and grad_pos must both be host or both be device arrays")
+    ge = np.zeros((nsp, nsp))
+    gs = np.zeros((nsp, nsp))
+    _check(handle, _lib.md_forces_backward(handle, gp, int(bool(dev)), op, ge.ctypes.data, gs.ctypes.data))
+    return ge, gs
+
+
+def md_energy_param_grad(handle, nsp):
+    de = np.zeros((nsp, nsp))
+    ds = np.zeros((nsp, nsp))
+    _check(handle, _lib.md_energy_param_grad(handle, de.ctypes.data, ds.ctypes.data))
+    return de, ds
+
+
 def md_destroy(handle):
     _lib.md_destroy(handle)
 
@@ -233,6 +264,7 @@ class System:
                  precision=MD_MIXED, list_kind=MD_LIST_FULL, rebuild=MD_REBUILD_SKIN_HALF, rebuild_k=10,
                  rcut=None, stream=None):
         self.n = int(n)
+        self.nsp = int(np.atleast_1d(mass).shape[0])
         self.handle = md_create(n, box, r_cut, skin, eps, sigma, mass, dt, precision, list_kind, rebuild,
                                 rebuild_k, rcut, stream)
 
@@ -282,3 +314,16 @@ class System:
 
     def set_timing(self, enable=True):
         md_set_timing(self.handle, enable)
+
+    def set_params(self, eps, sigma, rcut=None):
+        md_set_params(self.handle, eps, sigma, rcut)
+
+    def forces_backward(self, grad_f, grad_pos=None):
+        """(dL/dx, dL/deps, dL/dsigma) for dL/dF = grad_f (see md_forces_backward)."""
+        if grad_pos is None:
+            grad_pos = np.empty((self.n, 3)) if isinstance(grad_f, np.ndarray) else grad_f.new_empty((self.n, 3))
+        ge, gs = md_forces_backward(self.handle, grad_f, grad_pos, self.nsp)
+        return grad_pos, ge, gs
+
+    def energy_param_grad(self):
+        return md_energy_param_grad(self.handle, self.nsp)
