@@ -410,6 +410,11 @@ def comparisons(args, sysm, M, stream, value, list_len_hom):
                                 "per_atom_cost_vs_homogeneous": ns_inh / ns_hom}
         s.close()
     out["force_matching"] = force_matching_timing(M, stream)
+    # the paper's dependent wave schedule on the two workloads' cell grids, beside the
+    # 8 colour phases (host tool; no GPU work)
+    from paper_1305_4196_gb300 import waves as WV
+    out["wave_schedule"] = {f"{nc}^3 cells": {f"overlap_{ov}": WV.compare_with_colours(nc, ov) for ov in (27, 18)}
+                            for nc in (44, 52)}
     runs = []
     if args.precision == "mixed":
         runs.append(("fp64_gpu", M.MD_FP64, M.MD_LIST_FULL, 10, 2))
