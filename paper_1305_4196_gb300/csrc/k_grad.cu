@@ -13,7 +13,8 @@
 // (2 s6^2 - s6) / sig, come from the same pass.
 //
 // The kernel follows the full-list force kernels: one CTA per 2x2x2-cell block with
-// the block's 4x4x4-cell tile (coordinates and G) in shared memory, one thread per
+// the block's 4x4x4-cell tile (coordinates, species and global index) in shared
+// memory, G read from the cell-ordered global copy (L2-resident); one thread per
 // atom accumulating only its own dL/dx_i (each pair is seen from both sides, which
 // also gives the negative term on x_j).  Parameter terms are accumulated per atom by
 // neighbour species and summed in a fixed order afterwards, so every result is
@@ -28,23 +29,16 @@ constexpr int G_QUANT = 4;  // per species pair: dL/deps, dL/dsig, dE/deps, dE/d
 
 template <typename T>
 struct GradTile {
-    T *x, *y, *z, *gx, *gy, *gz;
-    int* sp;
+    T *x, *y, *z;
+    int *sp, *gid;  // species, cell-ordered global index (the dummy slot: -1)
 };
 
-// Upstream gradient of the tile atoms (cell-ordered G, 3 x n), one warp per tile cell.
-template <typename T>
-__device__ __forceinline__ void stage_grad(const TileMeta& m, const double* __restrict__ G, int64_t n,
-                                           GradTile<T>& t) {
+// Global index of every tile atom, one warp per tile cell.
+__device__ __forceinline__ void stage_gid(const TileMeta& m, int* __restrict__ gid) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     for (int slot = warp; slot < 64; slot += nw) {
         const int u0 = m.prefix[slot], cnt = m.prefix[slot + 1] - u0, j0 = m.start[slot];
-        for (int e = lane; e < cnt; e += 32) {
-            const int64_t j = j0 + e;
-            t.gx[u0 + e] = G ? (T)G[j] : T(0);
-            t.gy[u0 + e] = G ? (T)G[n + j] : T(0);
-            t.gz[u0 + e] = G ? (T)G[2 * n + j] : T(0);
-        }
+        for (int e = lane; e < cnt; e += 32) gid[u0 + e] = j0 + e;
     }
 }
 
@@ -79,10 +73,8 @@ __global__ void __launch_bounds__(G_THREADS) k_force_backward(DevState s, Geomet
     t.x = reinterpret_cast<T*>(smem);
     t.y = t.x + tile_cap;
     t.z = t.y + tile_cap;
-    t.gx = t.z + tile_cap;
-    t.gy = t.gx + tile_cap;
-    t.gz = t.gy + tile_cap;
-    t.sp = reinterpret_cast<int*>(t.gz + tile_cap);
+    t.sp = reinterpret_cast<int*>(t.z + tile_cap);
+    t.gid = t.sp + tile_cap;
     if constexpr (sizeof(T) == 8) {
         tile_stage_f64(s, g, m, b, t.x, t.y, t.z, t.sp);
     } else {
@@ -105,8 +97,8 @@ __global__ void __launch_bounds__(G_THREADS) k_force_backward(DevState s, Geomet
             t.sp[T_] = 0;
         }
     }
-    stage_grad<T>(m, G, s.n, t);
-    if (threadIdx.x == 0) t.gx[T_] = t.gy[T_] = t.gz[T_] = T(0);
+    stage_gid(m, t.gid);
+    if (threadIdx.x == 0) t.gid[T_] = -1;
     __syncthreads();
     const int nsp = pt.nsp;
     const int ncol = nsp * nsp * G_QUANT;
@@ -115,7 +107,7 @@ __global__ void __launch_bounds__(G_THREADS) k_force_backward(DevState s, Geomet
     for (int ui = threadIdx.x; ui < nown; ui += blockDim.x) {
         const int64_t gi = blk0 + ui;
         const T xi = t.x[ui], yi = t.y[ui], zi = t.z[ui];
-        const T Gx = t.gx[ui], Gy = t.gy[ui], Gz = t.gz[ui];
+        const T Gx = G ? (T)G[gi] : T(0), Gy = G ? (T)G[n + gi] : T(0), Gz = G ? (T)G[2 * n + gi] : T(0);
         const int si = t.sp[ui];
         T ax = 0, ay = 0, az = 0;
         double P[MAX_SPECIES][G_QUANT] = {};
@@ -136,7 +128,9 @@ __global__ void __launch_bounds__(G_THREADS) k_force_backward(DevState s, Geomet
             const T s6 = sr2 * sr2 * sr2;
             const T gq = T(24) * e * (T(2) * s6 * s6 - s6) * inv;
             const T gp = T(24) * e * (T(4) * s6 - T(14) * s6 * s6) * inv * inv;
-            const T wx = Gx - t.gx[u], wy = Gy - t.gy[u], wz = Gz - t.gz[u];
+            const int gj = t.gid[u];
+            const T wx = Gx - (G ? (T)G[gj] : T(0)), wy = Gy - (G ? (T)G[n + gj] : T(0)),
+                    wz = Gz - (G ? (T)G[2 * n + gj] : T(0));
             const T wd = wx * dx + wy * dy + wz * dz;
             const T two_gp_wd = T(2) * gp * wd;
             ax += gq * wx + two_gp_wd * dx;
@@ -226,7 +220,7 @@ __global__ void k_grad_out(DevState s, const double* __restrict__ gc, double* __
 }
 
 size_t backward_smem_bytes(int fp64, int tile_cap) {
-    return (size_t)tile_cap * (6 * (fp64 ? sizeof(double) : sizeof(float)) + sizeof(int));
+    return (size_t)tile_cap * (3 * (fp64 ? sizeof(double) : sizeof(float)) + 2 * sizeof(int));
 }
 
 size_t backward_scratch_doubles(int64_t n, int nsp, int nparts) {
