@@ -410,6 +410,7 @@ def comparisons(args, sysm, M, stream, value, list_len_hom):
                                 "per_atom_cost_vs_homogeneous": ns_inh / ns_hom}
         s.close()
     out["force_matching"] = force_matching_timing(M, stream)
+    out["batch_ensemble"] = batch_ensemble_timing(stream)
     # the paper's dependent wave schedule on the two workloads' cell grids, beside the
     # 8 colour phases (host tool; no GPU work)
     from paper_1305_4196_gb300 import waves as WV
@@ -441,6 +442,38 @@ def comparisons(args, sysm, M, stream, value, list_len_hom):
     if "fp64_gpu" in out:
         out["speedup_mixed_vs_fp64_gpu"] = value / out["fp64_gpu"]["value"]
     return {"compare": out}
+
+
+def batch_ensemble_timing(stream, steps=200):
+    """512 independent LJ systems, atom counts log-uniform in 256..32,768, densities
+    U(0.7, 0.95), temperatures U(0.5, 1.5), 200 steps, mixed precision: systems of at most
+    8,192 atoms one CTA each in one launch per size bucket (shapes autotuned first), the
+    larger ones as ordinary systems on their own streams alongside."""
+    import tempfile
+    import torch
+    from paper_1305_4196_gb300 import batch as BA
+    from paper_1305_4196_gb300 import workloads as W
+    systems = W.batch_ensemble(512, seed=4)
+    b = BA.from_systems(systems, stream=stream.cuda_stream)
+    cache = os.path.join(tempfile.mkdtemp(), "batch_tune.json")
+    t0 = time.perf_counter()
+    b.autotune(cache)
+    t_tune = time.perf_counter() - t0
+    path, threads, R = b.layout()
+    b.step(2)  # warm-up (graph capture)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    b.step(steps)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    ntot = sum(s.n for s in systems)
+    res = {"systems": len(systems), "atoms_total": ntot, "timesteps": steps, "value": ntot * steps / dt,
+           "unit": METRIC, "seconds": dt, "one_cta_systems": int((path == 0).sum()),
+           "md_system_systems": int((path == 1).sum()), "autotune_seconds": t_tune,
+           "tuned_threads_by_bucket": sorted({int(t) for t in threads[path == 0]}),
+           "tuned_cell_range_by_bucket": sorted({int(r) for r in R[path == 0]})}
+    b.close()
+    return res
 
 
 def force_matching_timing(M, stream, n_snap=8):

@@ -59,6 +59,7 @@ struct md_system {
     // double-buffered; g_fused[closing kick only / kick-kick-drift][buffer read]
     StepGraph g_fused[2][2];
     float4* xr_alt = nullptr;
+    double* pos_alt = nullptr;  // FP64 positions of buffer 1 (x, y, z: n each)
     bool graphs_valid = false;
     int graph_tile_cap = 0, graph_list_cap = 0;
     bool graph_timing = false;
@@ -132,15 +133,38 @@ bool mixed(const md_system* s) { return s->precision == MD_MIXED; }
 bool half(const md_system* s) { return s->list_kind == MD_LIST_HALF_COLOUR8; }
 // md_step runs the full-list mixed path with velocity Verlet fused into the force kernel
 bool fused(const md_system* s) { return mixed(s) && !half(s) && !s->no_fuse; }
+// kernels per force evaluation: 8 colour launches (half lists); the FP32 kernel and its
+// exact pass (mixed, full lists); one kernel (FP64, full lists)
+int force_kernels(const md_system* s) { return half(s) ? 8 : (mixed(s) ? 2 : 1); }
 
-// The state with its FP32 coordinates in buffer p (0: st[0].xr, 1: xr_alt).  Fused steps
-// read one buffer and write the other; outside md_step the coordinates are in buffer 0.
+// The state with its positions (FP32 cell-relative and FP64) in buffer p (0: st[0],
+// 1: xr_alt and pos_alt).  Fused steps read one buffer and write the other; outside
+// md_step the positions are in buffer 0.
 DevState view(const md_system* s, int p) {
     DevState v = s->st[0];
-    if (p) v.xr = s->xr_alt;
+    if (p) {
+        v.xr = s->xr_alt;
+        v.x = s->pos_alt;
+        v.y = s->pos_alt + s->n;
+        v.z = s->pos_alt + 2 * s->n;
+    }
     return v;
 }
-float4* xr_buf(const md_system* s, int p) { return p ? s->xr_alt : s->st[0].xr; }
+StepOut step_out(const md_system* s, int p) {
+    const DevState v = view(s, p);
+    return StepOut{v.xr, v.x, v.y, v.z};
+}
+// Positions of buffer 1 back into buffer 0 (a chunk of fused steps that ended in buffer 1).
+int positions_to_buffer0(md_system* s) {
+    const size_t n = (size_t)s->n;
+    const DevState& a = s->st[0];
+    if (cudaMemcpyAsync(a.xr, s->xr_alt, sizeof(float4) * n, cudaMemcpyDeviceToDevice, s->stream) ||
+        cudaMemcpyAsync(a.x, s->pos_alt, sizeof(double) * n, cudaMemcpyDeviceToDevice, s->stream) ||
+        cudaMemcpyAsync(a.y, s->pos_alt + n, sizeof(double) * n, cudaMemcpyDeviceToDevice, s->stream) ||
+        cudaMemcpyAsync(a.z, s->pos_alt + 2 * n, sizeof(double) * n, cudaMemcpyDeviceToDevice, s->stream))
+        return fail(s, MD_ERR_CUDA, "copy of the position buffers failed");
+    return MD_OK;
+}
 
 int round_up(int v, int m) { return (v + m - 1) / m * m; }
 
@@ -338,7 +362,7 @@ int do_forces(md_system* s, int with_energy) {
         CK(cudaEventRecord(ev.second, s->stream));
         s->ev_force.push_back(ev);
     }
-    s->launches += half(s) ? 8 : 1;
+    s->launches += force_kernels(s);
     s->force_evals += 1;
     s->forces_valid = true;
     return MD_OK;
@@ -505,12 +529,12 @@ int capture_fused(md_system* s, bool kkd, int p, md_system::StepGraph& out) {
         CK(cudaEventRecordWithFlags(ev.first, cs, cudaEventRecordExternal));
         CK(cudaStreamGetCaptureInfo(cs, &status, nullptr, &cg, &deps, nullptr, &ndeps));
         out.ev_a = ndeps ? deps[0] : nullptr;
-        launch_forces_mixed_fused(a, s->g, s->pt, s->to, s->tile_cap, mode, xr_buf(s, 1 - p), s->dt, s->lim2, cs);
+        launch_forces_mixed_fused(a, s->g, s->pt, s->to, s->tile_cap, mode, step_out(s, 1 - p), s->dt, s->lim2, cs);
         CK(cudaEventRecordWithFlags(ev.second, cs, cudaEventRecordExternal));
         CK(cudaStreamGetCaptureInfo(cs, &status, nullptr, &cg, &deps, nullptr, &ndeps));
         out.ev_b = ndeps ? deps[0] : nullptr;
     } else {
-        launch_forces_mixed_fused(a, s->g, s->pt, s->to, s->tile_cap, mode, xr_buf(s, 1 - p), s->dt, s->lim2, cs);
+        launch_forces_mixed_fused(a, s->g, s->pt, s->to, s->tile_cap, mode, step_out(s, 1 - p), s->dt, s->lim2, cs);
     }
     CK(cudaStreamEndCapture(cs, &g));
     CK(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
@@ -598,19 +622,18 @@ int run_steps_direct_fused(md_system* s, int len, bool first, bool last) {
             CK(cudaEventRecord(ev.first, s->stream));
         }
         launch_forces_mixed_fused(view(s, p), s->g, s->pt, s->to, s->tile_cap,
-                                  kkd ? FUSE_KICK_KICK_DRIFT : FUSE_KICK, xr_buf(s, 1 - p), s->dt, s->lim2, s->stream);
+                                  kkd ? FUSE_KICK_KICK_DRIFT : FUSE_KICK, step_out(s, 1 - p), s->dt, s->lim2,
+                                  s->stream);
         CKL();
         if (ev.second) {
             CK(cudaEventRecord(ev.second, s->stream));
             s->ev_force.push_back(ev);
         }
-        s->launches += 1;
+        s->launches += 2;  // fused force kernel and its exact pass
         s->force_evals += 1;
         if (kkd) p ^= 1;
     }
-    if (p)
-        CK(cudaMemcpyAsync(s->st[0].xr, s->xr_alt, sizeof(float4) * (size_t)s->n, cudaMemcpyDeviceToDevice,
-                           s->stream));
+    if (p && (rc = positions_to_buffer0(s))) return rc;
     s->forces_valid = last;
     return MD_OK;
 }
@@ -649,13 +672,11 @@ int run_chunk_fused(md_system* s, int len, bool first, bool last) {
             s->ev_force.push_back(ev);
         }
         CK(cudaGraphLaunch(gr.exec, s->stream));
-        s->launches += 2;  // step control, fused force kernel
+        s->launches += 3;  // step control, fused force kernel, exact pass
         s->force_evals += 1;
         if (kkd) p ^= 1;
     }
-    if (p)
-        CK(cudaMemcpyAsync(s->st[0].xr, s->xr_alt, sizeof(float4) * (size_t)s->n, cudaMemcpyDeviceToDevice,
-                           s->stream));
+    if (p && (rc = positions_to_buffer0(s))) return rc;
     CK(cudaMemcpyAsync(s->h_ctrl, s->d_ctrl, 2 * sizeof(long long), cudaMemcpyDeviceToHost, s->stream));
     if ((rc = sync_flags(s))) return rc;
     const uint32_t e = s->h_flags[0];
@@ -697,7 +718,7 @@ int run_chunk(md_system* s, int len, bool first) {
             s->ev_force.push_back(ev);
         }
         CK(cudaGraphLaunch(gr.exec, s->stream));
-        s->launches += 2 + (half(s) ? 8 : 1);  // integrate, step control, forces
+        s->launches += 2 + force_kernels(s);  // integrate, step control, forces
         s->force_evals += 1;
     }
     CK(cudaMemcpyAsync(s->h_ctrl, s->d_ctrl, 2 * sizeof(long long), cudaMemcpyDeviceToHost, s->stream));
@@ -858,11 +879,13 @@ int md_create(int64_t n, const double box[3], double r_cut, double skin, const m
         return bail(rc);
     if ((rc = dalloc(s, &d0.cell_start, (size_t)g.ncell + 1)) || (rc = dalloc(s, &d0.centre, 3 * (size_t)g.ncell)) ||
         (rc = dalloc(s, &d0.nl_cnt, n)) ||
-        (rc = dalloc(s, &d0.err, 1)) || (rc = dalloc(s, &d0.rebuild_flag, 1)) || (rc = dalloc(s, &d0.stats, 8)))
+        (rc = dalloc(s, &d0.err, 1)) || (rc = dalloc(s, &d0.rebuild_flag, 1)) || (rc = dalloc(s, &d0.stats, 8)) ||
+        (rc = dalloc(s, &d0.redo, (size_t)n + 2)))
         return bail(rc);
     if (p->precision == MD_MIXED) {
         if ((rc = dalloc(s, &d0.fq, 3 * (size_t)n)) || (rc = dalloc(s, &d0.pe_atom_f, n)) ||
-            (rc = dalloc(s, &d0.vir_atom_f, 6 * (size_t)n)) || (rc = dalloc(s, &s->xr_alt, n)))
+            (rc = dalloc(s, &d0.vir_atom_f, 6 * (size_t)n)) || (rc = dalloc(s, &s->xr_alt, n)) ||
+            (rc = dalloc(s, &s->pos_alt, 3 * (size_t)n)))
             return bail(rc);
     } else {
         if ((rc = dalloc(s, &d0.f, 3 * (size_t)n)) || (rc = dalloc(s, &d0.pe_atom_d, n)) ||
@@ -892,6 +915,7 @@ int md_create(int64_t n, const double box[3], double r_cut, double skin, const m
         d1.err = d0.err;
         d1.rebuild_flag = d0.rebuild_flag;
         d1.stats = d0.stats;
+        d1.redo = d0.redo;
         d1.fq = d0.fq;
         d1.f = d0.f;
         d1.pe_atom_f = d0.pe_atom_f;
@@ -914,6 +938,7 @@ int md_create(int64_t n, const double box[3], double r_cut, double skin, const m
     if (cudaMemsetAsync(d0.err, 0, sizeof(uint32_t), s->stream) != cudaSuccess ||
         cudaMemsetAsync(s->d_ctrl, 0, 2 * sizeof(long long), s->stream) != cudaSuccess ||
         cudaMemsetAsync(d0.rebuild_flag, 0, sizeof(int32_t), s->stream) != cudaSuccess ||
+        cudaMemsetAsync(d0.redo, 0, 2 * sizeof(int32_t), s->stream) != cudaSuccess ||
         cudaStreamSynchronize(s->stream) != cudaSuccess)
         return bail(MD_ERR_CUDA);
     *out = s;

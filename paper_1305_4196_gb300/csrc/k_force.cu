@@ -34,6 +34,8 @@ constexpr int FULL_THREADS = 256;  // CTA size of the full-list mixed kernel
 // Register cap of the full-list mixed kernel: 48 keeps 5 CTAs (40 warps) resident per SM.
 // The kernel is latency bound, and more resident warps beat longer per-thread schedules.
 #define MDGB_FULL_MAX_REGS 48
+// With several species the pair constants come from shared memory, and 48 registers spill.
+#define MDGB_FULL_MAX_REGS_SPECIES 64
 constexpr float MAGIC = 12582912.0f;   // 1.5 * 2^23: adding it rounds |a| < 2^22 to an integer
 constexpr float TWO21 = 2097152.0f;    // 2^21
 constexpr float FS_SCALE = 2048.0f;    // 2^11: pair force scaled so that rint() yields multiples of 2^-11
@@ -96,9 +98,10 @@ __device__ __forceinline__ float rcp_approx(float x) {
     return r;
 }
 
-// per-pair LJ in FP32; returns fs2 = (|f|/r) * 2^11, masked to 0 outside the cutoff
+// per-pair LJ in FP32: returns fs2 = (|f|/r) * 2^11 (not masked) and whether the FP32
+// r^2 is inside the cutoff
 template <bool SINGLE>
-__device__ __forceinline__ float lj_fs2(const PairTable& pt, int t, float r2, float& s6_out, bool& inside) {
+__device__ __forceinline__ float lj_fs_unmasked(const PairTable& pt, int t, float r2, float& s6_out, bool& inside) {
     const float sig2 = SINGLE ? pt.sig2_f[0] : pt.sig2_f[t];
     const float c48 = SINGLE ? pt.c48_f[0] : pt.c48_f[t];
     const float c24 = SINGLE ? pt.c24_f[0] : pt.c24_f[t];
@@ -108,8 +111,7 @@ __device__ __forceinline__ float lj_fs2(const PairTable& pt, int t, float r2, fl
     const float s6 = s2 * s2 * s2;
     inside = r2 < rc2;
     s6_out = s6;
-    const float fs = (c48 * s6 - c24) * s6 * inv;  // constants carry the 2^11 scale
-    return inside ? fs : 0.0f;
+    return (c48 * s6 - c24) * s6 * inv;  // constants carry the 2^11 scale
 }
 
 // Neighbour lists come in chunks of 8 tile indices (one 16-byte load per chunk,
@@ -187,6 +189,8 @@ __device__ __forceinline__ void fix_add2(FixAcc& acc, f2_t fs2, f2_t d, f2_t mag
 // would go through local memory).
 struct SpeciesTable {
     float sig2[MAX_PAIR], c48[MAX_PAIR], c24[MAX_PAIR], c4[MAX_PAIR], rc2[MAX_PAIR];
+    float rc2lo[MAX_PAIR], rc2hi[MAX_PAIR];  // r_cut^2 (1 -/+ CUT_BAND): the FP64 decision band
+    double rc2d[MAX_PAIR];                   // FP64 r_cut^2
 };
 
 __device__ __forceinline__ void load_species_table(const PairTable& pt, SpeciesTable& st) {
@@ -197,6 +201,9 @@ __device__ __forceinline__ void load_species_table(const PairTable& pt, SpeciesT
         st.c24[t] = pt.c24_f[t];
         st.c4[t] = pt.c4_f[t];
         st.rc2[t] = pt.rc2_f[t];
+        st.rc2lo[t] = pt.rc2_f[t] * (1.0f - CUT_BAND);
+        st.rc2hi[t] = pt.rc2_f[t] * (1.0f + CUT_BAND);
+        st.rc2d[t] = pt.rc2_d[t];
     }
 }
 
@@ -236,30 +243,44 @@ __device__ __forceinline__ float4 lds_tile(unsigned base, int u) {
     return v;
 }
 
-// Exact path for one atom whose list holds a pair force component >= 2048 eps/sigma
-// (or a non-finite one): every term through the FP64 rounding of fix_add_wide.
-template <bool SINGLE>
-__device__ __noinline__ void force_atom_wide(const float4* __restrict__ tile, const SpeciesTable& stab, int nsp,
-                                             float4 pi, const uint4* lp, size_t stride, int nch, FixAcc& ax,
-                                             FixAcc& ay, FixAcc& az, uint32_t* err) {
-    ax = FixAcc{0u, 0u};
-    ay = FixAcc{0u, 0u};
-    az = FixAcc{0u, 0u};
-    const int si = __float_as_int(pi.w);
-    for_each_neighbour(lp, stride, nch, [&](int u) {
-        const float4 pj = tile[u];
-        const float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
-        const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-        const int t = SINGLE ? 0 : si * nsp + __float_as_int(pj.w);
-        const float inv = rcp_approx(r2);
-        const float s2 = stab.sig2[t] * inv;
-        const float s6 = s2 * s2 * s2;
-        const float fs = (stab.c48[t] * s6 - stab.c24[t]) * s6 * inv;
-        const float fs2 = r2 < stab.rc2[t] ? fs : 0.0f;
-        fix_add_wide(ax, fs2, dx, err);
-        fix_add_wide(ay, fs2, dy, err);
-        fix_add_wide(az, fs2, dz, err);
-    });
+// What follows an atom's force in the full-list mixed kernels (MODE as below); one
+// function so that every kernel applies exactly the same operations.
+template <bool SINGLE, int MODE>
+__device__ __forceinline__ void full_epilogue(const DevState& s, const PairTable& pt, int gi, int si, long long qx,
+                                              long long qy, long long qz, const StepOut& out, double dt,
+                                              float lim2_f) {
+    const int64_t n = s.n;
+    if (MODE != FM_KKD) {
+        s.fq[gi] = qx;
+        s.fq[n + gi] = qy;
+        s.fq[2 * n + gi] = qz;
+    }
+    if (MODE != FM_FORCE) {
+        const double hq = pt.hdtm_q[SINGLE ? 0 : si];
+        const double kq = MODE == FM_KKD ? 2.0 * hq : hq;
+        const double vx = fma(kq, (double)qx, s.vx[gi]);
+        const double vy = fma(kq, (double)qy, s.vy[gi]);
+        const double vz = fma(kq, (double)qz, s.vz[gi]);
+        s.vx[gi] = vx;
+        s.vy[gi] = vy;
+        s.vz[gi] = vz;
+        if (MODE == FM_KKD) {
+            const double x = fma(dt, vx, s.x[gi]), y = fma(dt, vy, s.y[gi]), z = fma(dt, vz, s.z[gi]);
+            out.x[gi] = x;
+            out.y[gi] = y;
+            out.z[gi] = z;
+            const int c = s.cell_of[gi];
+            const float4 r = s.xr_ref[gi];
+            float4 q;
+            q.x = __double2float_rn(x - s.centre[c]);
+            q.y = __double2float_rn(y - s.centre[s.ncell + c]);
+            q.z = __double2float_rn(z - s.centre[2 * s.ncell + c]);
+            q.w = r.w;
+            out.xr[gi] = q;
+            const float ex = q.x - r.x, ey = q.y - r.y, ez = q.z - r.z;
+            if (!(fmaf(ez, ez, fmaf(ey, ey, ex * ex)) <= lim2_f)) *s.rebuild_flag = 1;
+        }
+    }
 }
 
 // ---------------------------------------------------------------- mixed, full list
@@ -272,13 +293,14 @@ __device__ __noinline__ void force_atom_wide(const float4* __restrict__ tile, co
 //   FM_FORCE  store the fixed-point force;
 //   FM_KICK   store it and apply the closing half kick v += (dt/2m) F;
 //   FM_KKD    closing and next opening kick in one, v += 2 (dt/2m) F, then the drift
-//             x += dt v, the FP32 coordinates of the new position into xr_out (a second
-//             buffer: other CTAs may still be staging this atom's current ones) and the
-//             skin/2 displacement test.  The force itself is not stored.
+//             x += dt v into out (the other position buffers: other CTAs may still be
+//             staging this atom's current FP32 coordinates or testing a pair near r_cut
+//             with its current FP64 position), the new FP32 coordinates beside it, and
+//             the skin/2 displacement test.  The force itself is not stored.
 template <bool SINGLE, bool EV, int MODE>
-__global__ void __maxnreg__(MDGB_FULL_MAX_REGS) k_force_mixed_full(DevState s, Geometry g, PairTable pt,
+__global__ void __maxnreg__(SINGLE ? MDGB_FULL_MAX_REGS : MDGB_FULL_MAX_REGS_SPECIES) k_force_mixed_full(DevState s, Geometry g, PairTable pt,
                                                                 TileOffsets to, int tile_cap, float fs2_max,
-                                                                float4* __restrict__ xr_out, double dt,
+                                                                StepOut out, double dt,
                                                                 float lim2_f) {
     static_assert(!EV || MODE == FM_FORCE, "energy/virial launches only evaluate forces");
     extern __shared__ __align__(16) unsigned char smem[];
@@ -308,7 +330,7 @@ __global__ void __maxnreg__(MDGB_FULL_MAX_REGS) k_force_mixed_full(DevState s, G
     const f2_t sig2_1 = f2_pack(pt.sig2_f[0], pt.sig2_f[0]);
     const f2_t c48_1 = f2_pack(pt.c48_f[0], pt.c48_f[0]);
     const f2_t nc24_1 = f2_pack(-pt.c24_f[0], -pt.c24_f[0]);
-    const float rc2_1 = pt.rc2_f[0];
+    const float rc2hi_1 = pt.rc2_f[0] * (1.0f + CUT_BAND), rc2lo_1 = pt.rc2_f[0] * (1.0f - CUT_BAND);
     for (int ui = threadIdx.x; ui < nown; ui += blockDim.x) {
         const int gi = blk0 + ui;
         const float4 pi = tile[ui];
@@ -335,16 +357,20 @@ __global__ void __maxnreg__(MDGB_FULL_MAX_REGS) k_force_mixed_full(DevState s, G
             const f2_t sig2 = SINGLE ? sig2_1 : f2_pack(stab.sig2[ta], stab.sig2[tb]);
             const f2_t c48 = SINGLE ? c48_1 : f2_pack(stab.c48[ta], stab.c48[tb]);
             const f2_t nc24 = SINGLE ? nc24_1 : f2_pack(-stab.c24[ta], -stab.c24[tb]);
-            const float rc2a = SINGLE ? rc2_1 : stab.rc2[ta], rc2b = SINGLE ? rc2_1 : stab.rc2[tb];
+            const float hia_c = SINGLE ? rc2hi_1 : stab.rc2hi[ta], hib_c = SINGLE ? rc2hi_1 : stab.rc2hi[tb];
+            const float loa_c = SINGLE ? rc2lo_1 : stab.rc2lo[ta], lob_c = SINGLE ? rc2lo_1 : stab.rc2lo[tb];
             const f2_t s2 = f2_mul(sig2, inv);
             const f2_t s6 = f2_mul(f2_mul(s2, s2), s2);
             const f2_t fsv = f2_mul(f2_mul(f2_fma(c48, s6, nc24), s6), inv);
             float fa, fb;
             f2_unpack(fsv, fa, fb);
-            const bool ina = r2a < rc2a, inb = r2b < rc2b;
+            // inside for certain below the band, tentatively inside up to its top: a pair in
+            // the band sends the atom through the exact redo (FP64 cutoff decision)
+            const bool ina = r2a < hia_c, inb = r2b < hib_c;
             fa = ina ? fa : 0.0f;
             fb = inb ? fb : 0.0f;
-            bad |= !(fabsf(fa) < fs2_max) | !(fabsf(fb) < fs2_max);
+            bad |= !(fabsf(fa) < fs2_max) | !(fabsf(fb) < fs2_max) | (ina != (r2a < loa_c)) |
+                   (inb != (r2b < lob_c));
             const f2_t fs2 = f2_pack(fa, fb);
             fix_add2(ax, fs2, dx, magic2, two21);
             fix_add2(ay, fs2, dy, magic2, two21);
@@ -368,40 +394,13 @@ __global__ void __maxnreg__(MDGB_FULL_MAX_REGS) k_force_mixed_full(DevState s, G
                 w5 += dya * (ga * dza) + dyb * (gb * dzb);
             }
         });
-        if (bad) force_atom_wide<SINGLE>(tile, stab, nsp, pi, lp, np, nch, ax, ay, az, s.err);
+        if (bad) {  // finished by the exact pass (k_force_redo), epilogue included
+            s.redo[2 + atomicAdd(s.redo, 1)] = gi;
+            continue;
+        }
         const int nterms = nch * 8;
         const long long qx = fix_final(ax, nterms), qy = fix_final(ay, nterms), qz = fix_final(az, nterms);
-        if (MODE != FM_KKD) {
-            s.fq[gi] = qx;
-            s.fq[n + gi] = qy;
-            s.fq[2 * n + gi] = qz;
-        }
-        if (MODE != FM_FORCE) {
-            const double hq = pt.hdtm_q[SINGLE ? 0 : si];
-            const double kq = MODE == FM_KKD ? 2.0 * hq : hq;
-            const double vx = fma(kq, (double)qx, s.vx[gi]);
-            const double vy = fma(kq, (double)qy, s.vy[gi]);
-            const double vz = fma(kq, (double)qz, s.vz[gi]);
-            s.vx[gi] = vx;
-            s.vy[gi] = vy;
-            s.vz[gi] = vz;
-            if (MODE == FM_KKD) {
-                const double x = fma(dt, vx, s.x[gi]), y = fma(dt, vy, s.y[gi]), z = fma(dt, vz, s.z[gi]);
-                s.x[gi] = x;
-                s.y[gi] = y;
-                s.z[gi] = z;
-                const int c = s.cell_of[gi];
-                const float4 r = s.xr_ref[gi];
-                float4 q;
-                q.x = __double2float_rn(x - s.centre[c]);
-                q.y = __double2float_rn(y - s.centre[s.ncell + c]);
-                q.z = __double2float_rn(z - s.centre[2 * s.ncell + c]);
-                q.w = r.w;
-                xr_out[gi] = q;
-                const float ex = q.x - r.x, ey = q.y - r.y, ez = q.z - r.z;
-                if (!(fmaf(ez, ez, fmaf(ey, ey, ex * ex)) <= lim2_f)) *s.rebuild_flag = 1;
-            }
-        }
+        full_epilogue<SINGLE, MODE>(s, pt, gi, si, qx, qy, qz, out, dt, lim2_f);
         if (EV) {
             // full lists see every pair twice: each atom keeps half of each pair energy / virial
             s.pe_atom_f[gi] = 0.5f * pe;
@@ -412,6 +411,126 @@ __global__ void __maxnreg__(MDGB_FULL_MAX_REGS) k_force_mixed_full(DevState s, G
             s.vir_atom_f[4 * n + gi] = 0.5f * w4;
             s.vir_atom_f[5 * n + gi] = 0.5f * w5;
         }
+    }
+}
+
+// ---------------------------------------------------------------- mixed, full list: exact pass
+// Atoms that the full-list kernel cannot finish in FP32 - a pair whose FP32 r^2 lies
+// within CUT_BAND of r_cut^2 (the cutoff is decided by the FP64 definition) or a pair
+// force component that may reach 2048 eps/sigma (beyond the two-part split; or not
+// finite) - are queued by it, and it skips their force and epilogue.  About one atom in
+// 600 of a liquid has such a pair.  This kernel finishes them, one warp per atom: the
+// FP32 block-frame coordinates are rebuilt with the staging's own additions, so every
+// other pair gets exactly the term the FP32 kernel would have added; band pairs are
+// decided in FP64 in the oracle's operation order; large terms are rounded in FP64
+// (fix_wide_terms).  Lane sums are exact integers, so the warp total does not depend
+// on how the list is spread over the lanes.  The same epilogue follows.  Keeping this
+// code out of the FP32 kernel keeps its registers for the pair loop (a call from its
+// loop costs it half its speed).  The last CTA to finish empties the queue.
+constexpr int REDO_WARPS = 8;
+constexpr int REDO_CTAS = 2 * 152;  // the queue is short; CTAs with no work exit at once
+
+template <bool SINGLE, bool EV, int MODE>
+__global__ void __launch_bounds__(REDO_WARPS * 32) k_force_redo(DevState s, Geometry g, PairTable pt,
+                                                                 TileOffsets to, float fs2_max, StepOut out,
+                                                                 double dt, float lim2_f) {
+    __shared__ SpeciesTable stab;
+    __shared__ TileMeta metas[REDO_WARPS];
+    __shared__ int last;
+    load_species_table(pt, stab);
+    const int count = s.redo[0];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    TileMeta& m = metas[warp];
+    const int nsp = pt.nsp;
+    for (int q = blockIdx.x * REDO_WARPS + warp; q < count; q += gridDim.x * REDO_WARPS) {
+        const int gi = s.redo[2 + q];
+        const int b = s.cell_of[gi] >> 3;  // cells are numbered block by block, 8 per block
+        tile_meta_warp(g, s.cell_start, b, m);
+        const int T = m.prefix[64];
+        const float4 pi = tile_coord(m, to, s.xr, gi - m.start[0]);  // own atoms: tile index = rank in block
+        const int si = __float_as_int(pi.w);
+        const int nent = ((s.nl_cnt[gi] + 7) >> 3) * 8;
+        FixAcc ax{0u, 0u}, ay{0u, 0u}, az{0u, 0u};
+        int nterms = 0;
+        float pe = 0.f, w0 = 0.f, w1 = 0.f, w2 = 0.f, w3 = 0.f, w4 = 0.f, w5 = 0.f;
+        for (int k = lane; k < nent; k += 32) {
+            const int u = s.nl[((size_t)(k >> 3) * s.np + gi) * 8 + (k & 7)];
+            if (u >= T) continue;  // padding (the tile's dummy slot): no force
+            const float4 pj = tile_coord(m, to, s.xr, u);
+            const float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
+            const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+            const int t = SINGLE ? 0 : si * nsp + __float_as_int(pj.w);
+            const float inv = rcp_approx(r2);
+            const float s2 = stab.sig2[t] * inv;
+            const float s6 = s2 * s2 * s2;
+            const float fs = __fmul_rn(__fmul_rn(__fmaf_rn(stab.c48[t], s6, -stab.c24[t]), s6), inv);
+            bool inside = r2 < stab.rc2lo[t];
+            if (!inside && r2 < stab.rc2hi[t])
+                inside = fp64_pair_test(s.x, s.y, s.z, g.L[0], g.L[1], g.L[2], gi, tile_global_index(m, u),
+                                        stab.rc2d[t]);
+            const float fs2 = inside ? fs : 0.0f;
+            if (fabsf(fs2) < fs2_max) {
+                fix_add(ax, fs2, dx);
+                fix_add(ay, fs2, dy);
+                fix_add(az, fs2, dz);
+            } else {
+                fix_add_wide(ax, fs2, dx, s.err);
+                fix_add_wide(ay, fs2, dy, s.err);
+                fix_add_wide(az, fs2, dz, s.err);
+            }
+            ++nterms;
+            if (EV && inside) {
+                const float gq = fs2 * (1.0f / FS_SCALE);
+                pe += stab.c4[t] * s6 * (s6 - 1.0f);
+                w0 += dx * (gq * dx);
+                w1 += dy * (gq * dy);
+                w2 += dz * (gq * dz);
+                w3 += dx * (gq * dy);
+                w4 += dx * (gq * dz);
+                w5 += dy * (gq * dz);
+            }
+        }
+        long long qx = fix_final(ax, nterms), qy = fix_final(ay, nterms), qz = fix_final(az, nterms);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            qx += __shfl_xor_sync(0xffffffffu, qx, o);
+            qy += __shfl_xor_sync(0xffffffffu, qy, o);
+            qz += __shfl_xor_sync(0xffffffffu, qz, o);
+            if (EV) {  // a fixed butterfly: the FP32 sums are reproducible
+                pe += __shfl_xor_sync(0xffffffffu, pe, o);
+                w0 += __shfl_xor_sync(0xffffffffu, w0, o);
+                w1 += __shfl_xor_sync(0xffffffffu, w1, o);
+                w2 += __shfl_xor_sync(0xffffffffu, w2, o);
+                w3 += __shfl_xor_sync(0xffffffffu, w3, o);
+                w4 += __shfl_xor_sync(0xffffffffu, w4, o);
+                w5 += __shfl_xor_sync(0xffffffffu, w5, o);
+            }
+        }
+        if (lane == 0) {
+            full_epilogue<SINGLE, MODE>(s, pt, gi, si, qx, qy, qz, out, dt, lim2_f);
+            if (EV) {
+                const int64_t n = s.n;
+                s.pe_atom_f[gi] = 0.5f * pe;
+                s.vir_atom_f[gi] = 0.5f * w0;
+                s.vir_atom_f[n + gi] = 0.5f * w1;
+                s.vir_atom_f[2 * n + gi] = 0.5f * w2;
+                s.vir_atom_f[3 * n + gi] = 0.5f * w3;
+                s.vir_atom_f[4 * n + gi] = 0.5f * w4;
+                s.vir_atom_f[5 * n + gi] = 0.5f * w5;
+            }
+        }
+        __syncwarp();  // m is refilled for the next atom
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(s.redo + 1, 1) == (int)gridDim.x - 1;
+    }
+    __syncthreads();
+    if (last && threadIdx.x == 0) {  // every CTA has read the count: empty the queue
+        s.redo[0] = 0;
+        s.redo[1] = 0;
     }
 }
 
@@ -461,7 +580,12 @@ __global__ void __launch_bounds__(F_THREADS) k_force_mixed_half(DevState s, Geom
             const int t = SINGLE ? 0 : si * pt.nsp + __float_as_int(pj.w);
             float s6;
             bool inside;
-            const float fs2 = lj_fs2<SINGLE>(pt, t, r2, s6, inside);
+            const float fs = lj_fs_unmasked<SINGLE>(pt, t, r2, s6, inside);
+            const float rc2t = SINGLE ? pt.rc2_f[0] : pt.rc2_f[t];
+            if (fabsf(r2 - rc2t) < CUT_BAND * rc2t)  // rare: decide the cutoff in FP64
+                inside = fp64_pair_test(s.x, s.y, s.z, g.L[0], g.L[1], g.L[2], gi, tile_global_index(m, u),
+                                        SINGLE ? pt.rc2_d[0] : pt.rc2_d[t]);
+            const float fs2 = inside ? fs : 0.0f;
             FixAcc bx{0u, 0u}, by{0u, 0u}, bz{0u, 0u};
             if (fabsf(fs2) < fs2_max) {
                 fix_add(ax, fs2, dx);
@@ -741,16 +865,28 @@ void launch_forces_mixed(const DevState& s, const Geometry& g, const PairTable& 
     if (!half) {
         if (single && !with_energy)
             k_force_mixed_full<true, false, FM_FORCE><<<g.nblock, FULL_THREADS, smem, st>>>(s, g, pt, to, tile_cap,
-                                                                                          fs2_max, nullptr, 0.0, 0.f);
+                                                                                          fs2_max, StepOut{}, 0.0, 0.f);
         else if (single)
             k_force_mixed_full<true, true, FM_FORCE><<<g.nblock, FULL_THREADS, smem, st>>>(s, g, pt, to, tile_cap,
-                                                                                         fs2_max, nullptr, 0.0, 0.f);
+                                                                                         fs2_max, StepOut{}, 0.0, 0.f);
         else if (!with_energy)
             k_force_mixed_full<false, false, FM_FORCE><<<g.nblock, FULL_THREADS, smem, st>>>(s, g, pt, to, tile_cap,
-                                                                                           fs2_max, nullptr, 0.0, 0.f);
+                                                                                           fs2_max, StepOut{}, 0.0, 0.f);
         else
             k_force_mixed_full<false, true, FM_FORCE><<<g.nblock, FULL_THREADS, smem, st>>>(s, g, pt, to, tile_cap,
-                                                                                          fs2_max, nullptr, 0.0, 0.f);
+                                                                                          fs2_max, StepOut{}, 0.0, 0.f);
+        if (single && !with_energy)
+            k_force_redo<true, false, FM_FORCE><<<REDO_CTAS, REDO_WARPS * 32, 0, st>>>(s, g, pt, to, fs2_max,
+                                                                                    StepOut{}, 0.0, 0.f);
+        else if (single)
+            k_force_redo<true, true, FM_FORCE><<<REDO_CTAS, REDO_WARPS * 32, 0, st>>>(s, g, pt, to, fs2_max,
+                                                                                   StepOut{}, 0.0, 0.f);
+        else if (!with_energy)
+            k_force_redo<false, false, FM_FORCE><<<REDO_CTAS, REDO_WARPS * 32, 0, st>>>(s, g, pt, to, fs2_max,
+                                                                                     StepOut{}, 0.0, 0.f);
+        else
+            k_force_redo<false, true, FM_FORCE><<<REDO_CTAS, REDO_WARPS * 32, 0, st>>>(s, g, pt, to, fs2_max,
+                                                                                    StepOut{}, 0.0, 0.f);
         return;
     }
     cudaMemsetAsync(s.fq, 0, sizeof(long long) * 3 * (size_t)s.n, st);
@@ -769,9 +905,18 @@ void launch_forces_mixed(const DevState& s, const Geometry& g, const PairTable& 
 }
 
 // Full-list mixed forces fused with velocity Verlet (mode FM_KICK: closing half kick;
-// FM_KKD: closing + opening kick and drift, new FP32 coordinates into xr_out).
+// FM_KKD: closing + opening kick and drift, the new positions into out).
+template <bool SINGLE, int MODE>
+static void launch_full_mode(const DevState& s, const Geometry& g, const PairTable& pt, const TileOffsets& to,
+                             int tile_cap, float fs2_max, StepOut out, double dt, float lim2_f, size_t smem,
+                             cudaStream_t st) {
+    k_force_mixed_full<SINGLE, false, MODE><<<g.nblock, FULL_THREADS, smem, st>>>(s, g, pt, to, tile_cap, fs2_max,
+                                                                                out, dt, lim2_f);
+    k_force_redo<SINGLE, false, MODE><<<REDO_CTAS, REDO_WARPS * 32, 0, st>>>(s, g, pt, to, fs2_max, out, dt, lim2_f);
+}
+
 void launch_forces_mixed_fused(const DevState& s, const Geometry& g, const PairTable& pt, const TileOffsets& to,
-                               int tile_cap, int mode, float4* xr_out, double dt, double lim2, cudaStream_t st) {
+                               int tile_cap, int mode, StepOut out, double dt, double lim2, cudaStream_t st) {
     if (s.n == 0) return;
     const size_t smem = force_smem_bytes(1, 0, 0, tile_cap);
     const float fs2_max = fs2_max_of(pt);
@@ -780,18 +925,14 @@ void launch_forces_mixed_fused(const DevState& s, const Geometry& g, const PairT
     const bool single = pt.nsp == 1;
     if (mode == FM_KICK) {
         if (single)
-            k_force_mixed_full<true, false, FM_KICK><<<g.nblock, FULL_THREADS, smem, st>>>(s, g, pt, to, tile_cap,
-                                                                                         fs2_max, xr_out, dt, lim2_f);
+            launch_full_mode<true, FM_KICK>(s, g, pt, to, tile_cap, fs2_max, out, dt, lim2_f, smem, st);
         else
-            k_force_mixed_full<false, false, FM_KICK><<<g.nblock, FULL_THREADS, smem, st>>>(s, g, pt, to, tile_cap,
-                                                                                          fs2_max, xr_out, dt, lim2_f);
+            launch_full_mode<false, FM_KICK>(s, g, pt, to, tile_cap, fs2_max, out, dt, lim2_f, smem, st);
     } else {
         if (single)
-            k_force_mixed_full<true, false, FM_KKD><<<g.nblock, FULL_THREADS, smem, st>>>(s, g, pt, to, tile_cap,
-                                                                                        fs2_max, xr_out, dt, lim2_f);
+            launch_full_mode<true, FM_KKD>(s, g, pt, to, tile_cap, fs2_max, out, dt, lim2_f, smem, st);
         else
-            k_force_mixed_full<false, false, FM_KKD><<<g.nblock, FULL_THREADS, smem, st>>>(s, g, pt, to, tile_cap,
-                                                                                         fs2_max, xr_out, dt, lim2_f);
+            launch_full_mode<false, FM_KKD>(s, g, pt, to, tile_cap, fs2_max, out, dt, lim2_f, smem, st);
     }
 }
 

@@ -118,8 +118,15 @@ __global__ void __launch_bounds__(G_THREADS) k_force_backward(DevState s, Geomet
             const T r2 = dx * dx + dy * dy + dz * dz;
             const int sj = t.sp[u];
             const int tt = si * nsp + sj;
-            const T rc2 = sizeof(T) == 8 ? (T)pt.rc2_d[tt] : (T)pt.rc2_f[tt];
-            if (!(r2 < rc2)) continue;
+            if (sizeof(T) == 8) {
+                if (!(r2 < (T)pt.rc2_d[tt])) continue;
+            } else {
+                const float rc2f = pt.rc2_f[tt];
+                if (!((float)r2 < rc2f * (1.0f + CUT_BAND))) continue;
+                if (!((float)r2 < rc2f * (1.0f - CUT_BAND)) &&  // rare: decide the cutoff in FP64
+                    !fp64_pair_test(s.x, s.y, s.z, g.L[0], g.L[1], g.L[2], (int)gi, t.gid[u], pt.rc2_d[tt]))
+                    continue;
+            }
             const T sig2 = sizeof(T) == 8 ? (T)pt.sig2_d[tt] : (T)pt.sig2_f[tt];
             const T e = sizeof(T) == 8 ? (T)pt.eps_d[tt] : (T)(pt.c4_f[tt] * 0.25f);
             const T sig = (T)pt.sig_d[tt];

@@ -25,21 +25,6 @@ namespace mdgb {
 
 constexpr int NL_WARPS = 8;
 
-__device__ __forceinline__ double mic_rn(double d, double L) {
-    return __dsub_rn(d, __dmul_rn(L, rint(__ddiv_rn(d, L))));
-}
-
-// FP64 test in the oracle's operation order.
-__device__ __forceinline__ bool fp64_pair_test(const double* __restrict__ x, const double* __restrict__ y,
-                                            const double* __restrict__ z, double Lx, double Ly, double Lz, int i,
-                                            int j, double rl2) {
-    double dx = mic_rn(__dsub_rn(x[i], x[j]), Lx);
-    double dy = mic_rn(__dsub_rn(y[i], y[j]), Ly);
-    double dz = mic_rn(__dsub_rn(z[i], z[j]), Lz);
-    double r2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
-    return r2 < rl2;
-}
-
 typedef unsigned long long f2_t;
 
 __device__ __forceinline__ f2_t f2_pack(float a, float b) {

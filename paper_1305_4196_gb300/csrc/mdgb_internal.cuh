@@ -123,6 +123,8 @@ struct DevState {
     uint32_t *err;          // sticky error bits
     int32_t *rebuild_flag;  // set when some atom moved more than skin/2
     int32_t *stats;         // [0] max list length, [1] max tile size, [2..3] sum of list lengths (u64)
+    int32_t *redo;          // mixed full lists: atoms for the exact pass; [0] count, [1] finished
+                            // CTAs of the exact pass, [2 ..] cell-ordered indices (n + 2 entries)
 };
 
 // ---- kernel launchers (defined in the .cu files)
@@ -146,8 +148,15 @@ size_t build_lists_smem(int list_cap, int tile_cap);
 void launch_forces_mixed(const DevState& s, const Geometry& g, const PairTable& pt, const TileOffsets& to,
                          int tile_cap, int half, int with_energy, cudaStream_t st);
 size_t force_smem_bytes(int mixed, int half, int with_energy, int tile_cap);
+// Where a kick-kick-drift step writes the new positions: the other pair of position
+// buffers (FP32 cell-relative and FP64), because CTAs that are still running read the
+// current ones (their tiles, and the FP64 cutoff test of pairs near r_cut).
+struct StepOut {
+    float4* xr;
+    double *x, *y, *z;
+};
 void launch_forces_mixed_fused(const DevState& s, const Geometry& g, const PairTable& pt, const TileOffsets& to,
-                               int tile_cap, int mode, float4* xr_out, double dt, double lim2, cudaStream_t st);
+                               int tile_cap, int mode, StepOut out, double dt, double lim2, cudaStream_t st);
 enum { FUSE_KICK = 1, FUSE_KICK_KICK_DRIFT = 2 };  // modes of launch_forces_mixed_fused
 void launch_forces_fp64(const DevState& s, const Geometry& g, const PairTable& pt, int tile_cap, int half,
                         int with_energy, cudaStream_t st);

@@ -39,6 +39,17 @@ __host__ __device__ constexpr TileTables make_tile_tables() {
 
 static __constant__ TileTables c_tiles = make_tile_tables();
 
+// Cell id of tile slot t of the block with coordinates (bx, by, bz).
+__device__ __forceinline__ int tile_cell_id(const Geometry& g, int bx, int by, int bz, int t) {
+    const int c = c_tiles.coord_of_idx[t];
+    const int tx = c & 3, ty = (c >> 2) & 3, tz = c >> 4;
+    int cx = 2 * bx - 1 + tx, cy = 2 * by - 1 + ty, cz = 2 * bz - 1 + tz;
+    cx += cx < 0 ? g.nc[0] : (cx >= g.nc[0] ? -g.nc[0] : 0);
+    cy += cy < 0 ? g.nc[1] : (cy >= g.nc[1] ? -g.nc[1] : 0);
+    cz += cz < 0 ? g.nc[2] : (cz >= g.nc[2] ? -g.nc[2] : 0);
+    return cell_id_of(g, cx, cy, cz);
+}
+
 // Fill meta for block b (threads 0..63 of the CTA take part; ends with __syncthreads).
 __device__ __forceinline__ void tile_meta(const Geometry& g, const int32_t* __restrict__ cell_start, int b,
                                           TileMeta& m) {
@@ -46,13 +57,7 @@ __device__ __forceinline__ void tile_meta(const Geometry& g, const int32_t* __re
     if (t < 64) {
         int bx, by, bz;
         block_coords(g, b, bx, by, bz);
-        int c = c_tiles.coord_of_idx[t];
-        int tx = c & 3, ty = (c >> 2) & 3, tz = c >> 4;
-        int cx = 2 * bx - 1 + tx, cy = 2 * by - 1 + ty, cz = 2 * bz - 1 + tz;
-        cx += cx < 0 ? g.nc[0] : (cx >= g.nc[0] ? -g.nc[0] : 0);
-        cy += cy < 0 ? g.nc[1] : (cy >= g.nc[1] ? -g.nc[1] : 0);
-        cz += cz < 0 ? g.nc[2] : (cz >= g.nc[2] ? -g.nc[2] : 0);
-        int id = cell_id_of(g, cx, cy, cz);
+        int id = tile_cell_id(g, bx, by, bz, t);
         int st = cell_start[id];
         int cnt = cell_start[id + 1] - st;
         m.start[t] = st;
@@ -72,6 +77,32 @@ __device__ __forceinline__ void tile_meta(const Geometry& g, const int32_t* __re
     __syncthreads();
 }
 
+// The same meta filled by one warp (lanes take slots lane and lane + 32; ends with __syncwarp).
+__device__ __forceinline__ void tile_meta_warp(const Geometry& g, const int32_t* __restrict__ cell_start, int b,
+                                               TileMeta& m) {
+    const int lane = threadIdx.x & 31;
+    int bx, by, bz;
+    block_coords(g, b, bx, by, bz);
+    int below = 0;  // atoms in slots 0..31
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int t = lane + 32 * h;
+        const int id = tile_cell_id(g, bx, by, bz, t);
+        const int st = cell_start[id];
+        int v = cell_start[id + 1] - st;
+        m.start[t] = st;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += y;
+        }
+        m.prefix[t + 1] = v + below;
+        below = __shfl_sync(0xffffffffu, v, 31);
+    }
+    if (lane == 0) m.prefix[0] = 0;
+    __syncwarp();
+}
+
 // Tile slot holding tile index u (binary search in the 65-entry prefix).
 __device__ __forceinline__ int tile_slot_of(const TileMeta& m, int u) {
     int lo = 0, hi = 64;
@@ -82,9 +113,48 @@ __device__ __forceinline__ int tile_slot_of(const TileMeta& m, int u) {
     return lo;
 }
 
+// The FP64 pair test of the definition, in the oracle's operation order: minimum image
+// d - L*rint(d/L) per dimension, r^2 = ((dx*dx) + dy*dy) + dz*dz, strict r^2 < cut2.
+// Used wherever an FP32 distance lies too close to a threshold (list radius or cutoff)
+// to decide the comparison.
+__device__ __forceinline__ double mic_rn(double d, double L) {
+    return __dsub_rn(d, __dmul_rn(L, rint(__ddiv_rn(d, L))));
+}
+
+__device__ __forceinline__ bool fp64_pair_test(const double* __restrict__ x, const double* __restrict__ y,
+                                            const double* __restrict__ z, double Lx, double Ly, double Lz, int i,
+                                            int j, double rl2) {
+    double dx = mic_rn(__dsub_rn(x[i], x[j]), Lx);
+    double dy = mic_rn(__dsub_rn(y[i], y[j]), Ly);
+    double dz = mic_rn(__dsub_rn(z[i], z[j]), Lz);
+    double r2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+    return r2 < rl2;
+}
+
+// Relative width of the band around r_cut^2 inside which the mixed-precision kernels
+// decide the cutoff in FP64: the FP32 r^2 of a pair is within a relative 1.2e-6 of the
+// exact one (block-frame coordinates within 3e-7, differences within 7e-7).
+constexpr float CUT_BAND = 1.0e-5f;
+
+// Cell-ordered global index of tile index u.
+__device__ __forceinline__ int tile_global_index(const TileMeta& m, int u) {
+    const int slot = tile_slot_of(m, u);
+    return m.start[slot] + (u - m.prefix[slot]);
+}
+
 // o[t] for t in 0..3 without dynamic indexing (which would copy the table to local memory)
 __device__ __forceinline__ float pick4(const float (&o)[4], int t) {
     return t == 0 ? o[0] : (t == 1 ? o[1] : (t == 2 ? o[2] : o[3]));
+}
+
+// Block-frame FP32 coordinates of tile index u, the same additions as the staging below.
+__device__ __forceinline__ float4 tile_coord(const TileMeta& m, const TileOffsets& to, const float4* __restrict__ xr,
+                                             int u) {
+    const int slot = tile_slot_of(m, u);
+    const int c = c_tiles.coord_of_idx[slot];
+    const float4 p = xr[m.start[slot] + (u - m.prefix[slot])];
+    return make_float4(p.x + pick4(to.off[0], c & 3), p.y + pick4(to.off[1], (c >> 2) & 3),
+                       p.z + pick4(to.off[2], c >> 4), p.w);
 }
 
 // Stage the block-frame FP32 coordinates of the tile, one warp per tile cell (lanes

@@ -240,3 +240,37 @@ def species_shuffle(n: int, frac_b: float, seed: int, stream: int = 6) -> np.nda
     sp = np.zeros(n, dtype=np.int32)
     sp[order[:nb]] = 1
     return sp
+
+
+def fcc_vacancies(n: int, rho: float, T: float, seed: int, jitter: float = 0.05, name: str = "") -> System:
+    """n atoms at exactly density rho: the fcc lattice of the smallest n_c^3 cells holding n
+    sites, scaled into the cube of side (n/rho)^(1/3), with a seeded random set of sites
+    left empty; Gaussian jitter and velocities at temperature T."""
+    nc = 1
+    while 4 * nc ** 3 < n:
+        nc += 1
+    L = (n / rho) ** (1.0 / 3.0)
+    sites, _ = fcc_lattice(nc, nc, nc, L / nc)
+    keys = splitmix64(seed, 7, sites.shape[0])
+    keep = np.sort(np.argsort(keys, kind="stable")[:n])
+    box = np.array([L, L, L])
+    pos = sites[keep]
+    if jitter > 0.0:
+        pos = gaussian_jitter(pos, box, jitter, seed, stream=2)
+    masses = np.ones(n)
+    vel = thermal_velocities(masses, T, seed, stream=1)
+    return System(pos, vel, np.zeros(n, dtype=np.int32), box, name or f"fcc_vacancies_{n}")
+
+
+def batch_ensemble(n_systems: int = 512, seed: int = 4, n_min: int = 256, n_max: int = 32768,
+                   rho_range=(0.7, 0.95), T_range=(0.5, 1.5)) -> list:
+    """Independent periodic LJ systems of uneven size: atom counts log-uniform in
+    [n_min, n_max], densities and temperatures uniform in the given ranges, all seeded."""
+    u = uniform01(seed, 11, 3 * n_systems).reshape(n_systems, 3)
+    out = []
+    for k in range(n_systems):
+        n = int(round(math.exp(math.log(n_min) + u[k, 0] * (math.log(n_max) - math.log(n_min)))))
+        rho = rho_range[0] + u[k, 1] * (rho_range[1] - rho_range[0])
+        T = T_range[0] + u[k, 2] * (T_range[1] - T_range[0])
+        out.append(fcc_vacancies(n, rho, T, seed * 100003 + k, name=f"batch_{k}"))
+    return out

@@ -31,7 +31,7 @@ def _declared():
         if h.endswith(".h"):
             txt = open(os.path.join(INCLUDE, h)).read()
             txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
-            names += re.findall(r"^\s*(?:int|void)\s+\**\s*(md\w+)\s*\(", txt, flags=re.M)
+            names += re.findall(r"^\s*(?:int64_t|int|void)\s+\**\s*(md\w+)\s*\(", txt, flags=re.M)
     return names
 
 

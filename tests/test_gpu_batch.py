@@ -1,0 +1,139 @@
+"""Ensembles of independent systems (include/mdgb_batch.h) against the FP64 oracle.
+
+Inputs: seeded systems of uneven size from workloads.batch_ensemble (fcc sites with
+vacancies at exact density, Gaussian jitter, thermal velocities), the shape of the
+512-system ensemble workload, with sizes chosen so that both execution paths (one
+CTA per system, and md_system for the larger ones) are exercised.  Bars: forces
+within 2e-5 (per atom, against the RMS), potential energy within 1e-6, kinetic
+energy within 1e-12; bit-identical repeats; short trajectories close to the oracle's.
+"""
+import os
+import tempfile
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from oracle import oracle as O  # noqa: E402
+from paper_1305_4196_gb300 import build as B  # noqa: E402
+from paper_1305_4196_gb300 import workloads as W  # noqa: E402
+
+B.build()
+from paper_1305_4196_gb300 import batch as BA  # noqa: E402
+
+P = O.LJParams.single()
+
+
+def ensemble(k=10, seed=9, n_max=12000):
+    return W.batch_ensemble(n_systems=k, seed=seed, n_max=n_max)
+
+
+def force_error(F, Fref):
+    mag = np.sqrt((Fref ** 2).sum(1))
+    frms = np.sqrt((mag ** 2).mean())
+    return float((np.sqrt(((F - Fref) ** 2).sum(1)) / np.maximum(mag, frms)).max())
+
+
+def split(a, systems):
+    out, o = [], 0
+    for s in systems:
+        out.append(a[o:o + s.n])
+        o += s.n
+    return out
+
+
+def test_both_paths_used_and_forces_match_oracle():
+    systems = ensemble()
+    b = BA.from_systems(systems)
+    path, threads, R = b.layout()
+    assert set(path.tolist()) == {0, 1}
+    for s, F in zip(systems, split(b.forces(), systems)):
+        Fref, _, _ = O.lj_forces(s.pos, s.box, P)
+        assert force_error(F, Fref) <= 2e-5
+
+
+def test_energies_match_oracle():
+    systems = ensemble(seed=10)
+    b = BA.from_systems(systems)
+    pe, ke = b.energies()
+    for k, s in enumerate(systems):
+        _, pe_ref, _ = O.lj_forces(s.pos, s.box, P)
+        ke_ref = O.kinetic(s.vel, P)
+        assert abs(pe[k] - pe_ref) <= 1e-6 * abs(pe_ref)
+        assert abs(ke[k] - ke_ref) <= 1e-12 * ke_ref
+
+
+def test_steps_are_deterministic_and_follow_the_oracle():
+    """20 steps: two ensembles from the same input agree bit for bit; every system stays
+    within 1e-5 sigma of the FP64 oracle's trajectory (mixed-precision forces)."""
+    systems = ensemble(k=8, seed=11, n_max=6000)
+    a = BA.from_systems(systems)
+    b = BA.from_systems(systems)
+    a.step(20)
+    b.step(13)
+    b.step(7)
+    pa, va, ia = a.get_state()
+    pb, vb, ib = b.get_state()
+    assert np.array_equal(pa, pb) and np.array_equal(va, vb) and np.array_equal(ia, ib)
+    for s, p, im in zip(systems, split(pa, systems), split(ia, systems)):
+        r = O.run_nve(s.pos, s.vel, s.box, P, 0.005, 0.3, 20)
+        un = p + im * s.box
+        ref = r["pos"] + r["image"] * s.box
+        assert np.abs(un - ref).max() <= 1e-5
+
+
+def test_energy_after_100_steps_matches_oracle():
+    """The potential is unshifted, so the total energy jumps by u(r_cut) whenever a pair
+    crosses the cutoff and drifts while an fcc start melts; the reference for the energy
+    after 100 steps is therefore the FP64 oracle's own trajectory (per atom, within 1e-4)."""
+    systems = [W.fcc_vacancies(n, 0.8, 0.9, seed=5 + n) for n in (300, 900, 2500)]
+    b = BA.from_systems(systems)
+    b.step(100)
+    pe, ke = b.energies()
+    assert np.all(b.layout()[0] == 0)
+    for k, s in enumerate(systems):
+        ref = O.run_nve(s.pos, s.vel, s.box, P, 0.005, 0.3, 100, history=True)
+        e_ref = ref["pe"][-1] + ref["ke"][-1]
+        assert abs(pe[k] + ke[k] - e_ref) / s.n < 1e-4
+
+
+def test_autotune_writes_and_reads_its_cache():
+    systems = ensemble(k=6, seed=12, n_max=8000)
+    b = BA.from_systems(systems)
+    path = os.path.join(tempfile.mkdtemp(), "tune.json")
+    before = b.get_state()
+    b.autotune(path)
+    after = b.get_state()
+    assert all(np.array_equal(x, y) for x, y in zip(before, after))  # the state is restored
+    text = open(path).read()
+    # sizes 338, 417 | 1758 | 4370, 4653, 7216: buckets 0, 2 and 4 are tuned, 1 and 3 hold no system
+    assert '"gpu":' in text and all(f'"bucket_{k}":' in text for k in (0, 2, 4))
+    assert '"bucket_1":' not in text and '"bucket_3":' not in text
+    _, th, R = b.layout()
+    c = BA.from_systems(systems)
+    c.autotune(path)
+    _, th2, R2 = c.layout()
+    assert np.array_equal(th, th2) and np.array_equal(R, R2)
+    for s, F in zip(systems, split(c.forces(), systems)):
+        assert force_error(F, O.lj_forces(s.pos, s.box, P)[0]) <= 2e-5
+
+
+def test_cutoff_decided_by_the_definition():
+    """Pairs at r_cut (1 -/+ 1e-7) in small boxes on the one-CTA path: the cutoff is decided in
+    FP64 as the definition, so the forces match the oracle."""
+    systems = []
+    for k in range(3):
+        box = np.array([14.0, 14.0, 14.0])
+        pos = W.threshold_pairs(27, box, 2.5, 1e-7, seed=20 + k)
+        systems.append(W.System(pos, np.zeros_like(pos), np.zeros(len(pos), dtype=np.int32), box))
+    b = BA.from_systems(systems)
+    assert np.all(b.layout()[0] == 0)
+    for s, F in zip(systems, split(b.forces(), systems)):
+        Fref, _, _ = O.lj_forces(s.pos, s.box, P)
+        assert np.abs(Fref).max() > 0.03
+        assert np.abs(F - Fref).max() <= 2e-5 * np.abs(Fref).max()

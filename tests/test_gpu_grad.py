@@ -150,3 +150,19 @@ def test_backward_needs_full_lists():
     with pytest.raises(M.MDError) as e:
         sysm.forces_backward(np.zeros((s.n, 3)))
     assert e.value.code == M.MD_ERR_ARG
+
+
+def test_backward_cutoff_decided_by_the_definition():
+    """Pairs at r_cut (1 -/+ 1e-7) on a mixed system: the FP32 backward pass takes the FP64
+    cutoff decision, so it matches the oracle's gradient."""
+    box = np.array([30.0, 30.0, 30.0])
+    pos = W.threshold_pairs(216, box, 2.5, 1e-7, seed=14)
+    sp = np.zeros(len(pos), dtype=np.int32)
+    P = O.LJParams.single()
+    s = M.System(len(pos), box, r_cut=2.5, skin=0.3, precision=M.MD_MIXED)
+    s.set_state(np.ascontiguousarray(pos), np.zeros_like(pos), sp)
+    G = np.random.default_rng(3).normal(size=(len(pos), 3))
+    gx, ge, gs = s.forces_backward(G)
+    gx_ref, ge_ref, gs_ref = O.lj_force_grad(pos, box, P, G, sp)
+    assert np.abs(gx - gx_ref).max() <= 2e-5 * np.abs(gx_ref).max()
+    assert abs(ge[0, 0] - ge_ref[0, 0]) <= 2e-5 * abs(ge_ref[0, 0])

@@ -206,6 +206,19 @@ def test_dense_blocks_cooperative_tail():
     assert np.abs(vir - vir_ref).max() <= 1e-6 * np.abs(vir_ref[:3]).max()
 
 
+def test_long_lists_match_oracle():
+    """r_cut = 5 sigma: lists of ~530 entries (67 chunks) and a tile of the whole box (4
+    cells per side); mixed forces and energy match the oracle."""
+    sysm = W.lj_fcc(13, seed=6, jitter=0.05)
+    P = O.LJParams.single(rc=5.0)
+    s = make(sysm, "mixed", "full", params=P)
+    Fref, pe_ref, _ = O.lj_forces(sysm.pos, sysm.box, P)
+    assert force_error(s.forces(), Fref) <= TOL["mixed"]
+    pe, _, _ = s.energy_virial()
+    assert abs(pe - pe_ref) <= 1e-6 * abs(pe_ref)
+    assert s.info()["max_list"] > 500
+
+
 @pytest.mark.parametrize("lst", ["full", "half"])
 def test_close_pairs_take_the_exact_wide_path(lst):
     """Pairs at 0.6 sigma carry forces far above 2048 eps/sigma, beyond the two-part
@@ -226,6 +239,23 @@ def test_close_pairs_take_the_exact_wide_path(lst):
     perm = np.argsort(W.splitmix64(6, 3, sysm.n))
     sp = W.System(pos[perm], sysm.vel[perm], sysm.species[perm], sysm.box)
     assert np.array_equal(make(sp, "mixed", lst).forces(), F[perm])
+
+@pytest.mark.parametrize("lst", ["full", "half"])
+def test_cutoff_decided_by_the_definition(lst):
+    """Isolated pairs at r_cut (1 -/+ 1e-7): inside and outside by the FP64 definition, but
+    closer to r_cut than FP32 distances resolve.  The unshifted force jumps by |f(r_cut)| there,
+    so the mixed path must take the FP64 decision for them (and the energy with it)."""
+    box = np.array([30.0, 30.0, 30.0])
+    pos = W.threshold_pairs(216, box, RC, 1e-7, seed=13)
+    sysm = W.System(pos, np.zeros_like(pos), np.zeros(len(pos), dtype=np.int32), box)
+    P = O.LJParams.single()
+    s = make(sysm, "mixed", lst)
+    F = s.forces()
+    Fref, pe_ref, _ = O.lj_forces(pos, box, P)
+    assert np.abs(Fref).max() > 0.03  # half the pairs interact
+    assert np.abs(F - Fref).max() <= 2e-5 * np.abs(Fref).max()
+    pe, _, _ = s.energy_virial()
+    assert abs(pe - pe_ref) <= 1e-6 * abs(pe_ref)
 
 # ---------------------------------------------------------------- energies
 @pytest.mark.parametrize("lst", ["full", "half"])
