@@ -428,6 +428,111 @@ void orc_lj_grad(int64_t n, const double *x, const double *box, const int32_t *s
         }
 }
 
+/* ------------------------------------------------------- many-body (TB-SMA) */
+
+/*
+ * The tight-binding second-moment potential of Cleri and Rosato (Phys. Rev. B 48,
+ * 22 (1993)), the potential of all of the paper's benchmarks (Sec. III):
+ *   E = sum_i [ sum_j phi(r_ij) - sqrt(rho_i) ],  rho_i = sum_j psi(r_ij),
+ *   phi(r) = A exp(-p (r / r0 - 1)),  psi(r) = xi^2 exp(-2 q (r / r0 - 1)),
+ * both sums over the neighbours j of i closer than r_cut (strict <).  The force on i,
+ * -dE/dx_i, is a sum over the same pairs with d = x_i - x_j:
+ *   F_i = sum_j [ (2 p / r0) phi - (q / r0) psi (1 / sqrt(rho_i) + 1 / sqrt(rho_j)) ] d / r
+ * (the repulsion of a pair enters E twice, once per atom; the band term of atom k
+ * depends on every neighbour's distance).  An atom with no neighbour has rho = 0 and
+ * no force.  Two passes in the definition's order: the densities, then the forces.
+ * Per-atom energy: sum_j phi - sqrt(rho_i); the virial is sum over pairs of d_a f_b.
+ * prm = {A, xi, p, q, r0}.
+ */
+typedef struct {
+    const double *prm;
+    double rc;
+    double *rho;       /* N, accumulated */
+    csum *rho_acc;     /* N compensated sums */
+    csum rep;
+    double *f;
+    const double *inv; /* N: 1 / sqrt(rho), 0 without neighbours */
+    double *e_atom;    /* nullable */
+    csum vir[6];
+} tb_acc;
+
+static void tb_density_pair(void *ctx, int64_t i, int64_t j, const double d[3], double r2)
+{
+    tb_acc *a = (tb_acc *)ctx;
+    (void)d;
+    if (!(r2 < a->rc * a->rc)) return;
+    const double A = a->prm[0], xi = a->prm[1], p = a->prm[2], q = a->prm[3], r0 = a->prm[4];
+    double r = sqrt(r2);
+    double psi = xi * xi * exp(-2.0 * q * (r / r0 - 1.0));
+    double phi = A * exp(-p * (r / r0 - 1.0));
+    csum_add(&a->rho_acc[i], psi);
+    csum_add(&a->rho_acc[j], psi);
+    csum_add(&a->rep, 2.0 * phi);
+    if (a->e_atom) {
+        a->e_atom[i] += phi;
+        a->e_atom[j] += phi;
+    }
+}
+
+static void tb_force_pair(void *ctx, int64_t i, int64_t j, const double d[3], double r2)
+{
+    tb_acc *a = (tb_acc *)ctx;
+    if (!(r2 < a->rc * a->rc)) return;
+    const double A = a->prm[0], xi = a->prm[1], p = a->prm[2], q = a->prm[3], r0 = a->prm[4];
+    double r = sqrt(r2);
+    double psi = xi * xi * exp(-2.0 * q * (r / r0 - 1.0));
+    double phi = A * exp(-p * (r / r0 - 1.0));
+    double fr = (2.0 * p / r0) * phi - (q / r0) * psi * (a->inv[i] + a->inv[j]); /* along d / r */
+    double g = fr / r;
+    for (int k = 0; k < 3; ++k) {
+        a->f[3 * i + k] += g * d[k];
+        a->f[3 * j + k] -= g * d[k];
+    }
+    csum_add(&a->vir[0], d[0] * (g * d[0]));
+    csum_add(&a->vir[1], d[1] * (g * d[1]));
+    csum_add(&a->vir[2], d[2] * (g * d[2]));
+    csum_add(&a->vir[3], d[0] * (g * d[1]));
+    csum_add(&a->vir[4], d[0] * (g * d[2]));
+    csum_add(&a->vir[5], d[1] * (g * d[2]));
+}
+
+/*
+ * Forces (N x 3, overwritten), densities rho (nullable, N), per-atom energies
+ * (nullable, N), total energy and virial (nullable) at x.
+ */
+void orc_tbsma_forces(int64_t n, const double *x, const double *box, const double *prm, double rc, int brute,
+                      double *f, double *rho_out, double *e_atom, double *energy, double *vir)
+{
+    tb_acc a;
+    memset(&a, 0, sizeof(a));
+    a.prm = prm;
+    a.rc = rc;
+    a.rho_acc = (csum *)calloc((size_t)(n > 0 ? n : 1), sizeof(csum));
+    double *inv = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    a.e_atom = e_atom;
+    if (e_atom) memset(e_atom, 0, sizeof(double) * (size_t)n);
+    for_each_pair(n, x, box, rc, brute, tb_density_pair, &a);
+    csum band;
+    memset(&band, 0, sizeof(band));
+    for (int64_t i = 0; i < n; ++i) {
+        double rho = csum_get(&a.rho_acc[i]);
+        double sq = sqrt(rho);
+        inv[i] = rho > 0.0 ? 1.0 / sq : 0.0;
+        csum_add(&band, -sq);
+        if (rho_out) rho_out[i] = rho;
+        if (e_atom) e_atom[i] -= sq;
+    }
+    memset(f, 0, sizeof(double) * 3 * (size_t)n);
+    a.f = f;
+    a.inv = inv;
+    for_each_pair(n, x, box, rc, brute, tb_force_pair, &a);
+    if (energy) *energy = csum_get(&a.rep) + csum_get(&band);
+    if (vir)
+        for (int k = 0; k < 6; ++k) vir[k] = csum_get(&a.vir[k]);
+    free(a.rho_acc);
+    free(inv);
+}
+
 /* ------------------------------------------------------- integration */
 
 /* Kinetic energy 1/2 sum m v^2 (mass per species). */

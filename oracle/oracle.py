@@ -68,6 +68,9 @@ def _configure(lib):
     lib.orc_lj_grad.restype = None
     lib.orc_lj_grad.argtypes = [C.c_int64, _dp, _dp, C.c_void_p, C.c_int32, _dp, _dp, _dp, C.c_void_p,
                                 C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+    lib.orc_tbsma_forces.restype = None
+    lib.orc_tbsma_forces.argtypes = [C.c_int64, _dp, _dp, _dp, C.c_double, C.c_int, _dp, C.c_void_p, C.c_void_p,
+                                     C.c_void_p, C.c_void_p]
     lib.orc_run_nve.restype = C.c_int64
     lib.orc_run_nve.argtypes = [C.c_int64, _dp, _dp, _ip, _dp, C.c_void_p, C.c_int32, _dp, _dp, _dp,
                                 _dp, C.c_double, C.c_double, C.c_int32, C.c_int32, C.c_int64,
@@ -162,6 +165,45 @@ def lj_forces(pos, box, params: LJParams, species=None, brute=False, per_atom=Fa
     if per_atom:
         return f, float(pe[0]), vir, pea
     return f, float(pe[0]), vir
+
+
+class TBSMAParams:
+    """Tight-binding second-moment potential of Cleri and Rosato (1993): A, xi (energy),
+    p, q (dimensionless), r0 (nearest-neighbour distance) and the cutoff r_cut."""
+
+    def __init__(self, A, xi, p, q, r0, rc):
+        self.A, self.xi, self.p, self.q, self.r0, self.rc = (float(v) for v in (A, xi, p, q, r0, rc))
+
+    def array(self):
+        return np.array([self.A, self.xi, self.p, self.q, self.r0])
+
+    @staticmethod
+    def copper(rc=None):
+        """Cu of Cleri and Rosato (eV, Angstrom): fitted to the fcc lattice constant 3.615 A and
+        cohesive energy 3.544 eV with sums over five neighbour shells; the default cutoff lies
+        halfway between the fifth and sixth shells, sqrt(5) r0 and sqrt(6) r0."""
+        r0 = 3.615 / np.sqrt(2.0)
+        return TBSMAParams(0.0855, 1.224, 10.960, 2.278, r0,
+                           rc if rc is not None else 0.5 * (np.sqrt(5.0) + np.sqrt(6.0)) * r0)
+
+
+def tbsma_forces(pos, box, params: TBSMAParams, brute=False, per_atom=False):
+    """(F (N,3), E, virial[6]) of the whole system; with per_atom also (rho, E per atom)."""
+    lib = _load()
+    pos = _c(pos, np.float64)
+    box = _c(box, np.float64)
+    n = pos.shape[0]
+    f = np.zeros((n, 3))
+    e = np.zeros(1)
+    vir = np.zeros(6)
+    rho = np.zeros(n) if per_atom else None
+    ea = np.zeros(n) if per_atom else None
+    lib.orc_tbsma_forces(n, pos.ravel(), box, params.array(), params.rc, int(brute), f.ravel(),
+                         rho.ctypes.data if per_atom else None, ea.ctypes.data if per_atom else None,
+                         e.ctypes.data, vir.ctypes.data)
+    if per_atom:
+        return f, float(e[0]), vir, rho, ea
+    return f, float(e[0]), vir
 
 
 def lj_force_grad(pos, box, params: LJParams, G, species=None):

@@ -39,6 +39,12 @@ MUTATIONS = {
                           "csum_add(&a->esig[u], 24.0 * e * (s6 * s6 - s6) / s);"),
     "grad_pair_index_unordered": ("int32_t u = si <= sj ? si * a->nsp + sj : sj * a->nsp + si;",
                                   "int32_t u = si * a->nsp + sj;"),
+    "tbsma_repulsion_once": ("csum_add(&a->rep, 2.0 * phi);", "csum_add(&a->rep, phi);"),
+    "tbsma_density_exponent_q": ("double psi = xi * xi * exp(-2.0 * q * (r / r0 - 1.0));\n    double phi = A * exp(-p * (r / r0 - 1.0));\n    csum_add(&a->rho_acc[i], psi);",
+                                 "double psi = xi * xi * exp(-q * (r / r0 - 1.0));\n    double phi = A * exp(-p * (r / r0 - 1.0));\n    csum_add(&a->rho_acc[i], psi);"),
+    "tbsma_embedding_own_atom_only": ("(a->inv[i] + a->inv[j])", "(2.0 * a->inv[i])"),
+    "tbsma_repulsive_force_factor": ("double fr = (2.0 * p / r0) * phi", "double fr = (p / r0) * phi"),
+    "tbsma_band_force_sign": ("- (q / r0) * psi * (a->inv[i] + a->inv[j]);", "+ (q / r0) * psi * (a->inv[i] + a->inv[j]);"),
 }
 
 

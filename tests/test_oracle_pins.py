@@ -478,3 +478,96 @@ def test_energy_param_grad_identities():
     uniq = [(0, 0), (0, 1), (1, 1)]
     assert sum(P.eps[a, b] * de[a, b] for a, b in uniq) == pytest.approx(pe, rel=1e-12)
     assert sum(P.sig[a, b] * ds[a, b] for a, b in uniq) == pytest.approx(vir[0] + vir[1] + vir[2], rel=1e-12)
+
+
+# ---------------------------------------------------------------- many-body (TB-SMA, Cleri-Rosato)
+CU = O.TBSMAParams.copper()
+
+
+def _cu_crystal(n_cells=5, a=3.615, jitter=0.0, seed=0):
+    pos, box = W.fcc_lattice(n_cells, n_cells, n_cells, a)
+    if jitter > 0.0:
+        pos = W.gaussian_jitter(pos, box, jitter, seed, stream=2)
+    return pos, box
+
+
+def test_tbsma_copper_cohesive_energy_and_lattice_constant():
+    """Cleri and Rosato fitted the Cu parameters to the fcc lattice constant 3.615 A and
+    the cohesive energy 3.544 eV (sums over five neighbour shells): the oracle's energy per
+    atom of the perfect crystal is -3.544 eV, smallest at a = 3.615 A, with no force on any
+    site and an isotropic virial."""
+    pos, box = _cu_crystal()
+    F, E, vir = O.tbsma_forces(pos, box, CU)
+    n = len(pos)
+    assert abs(E / n + 3.544) < 1e-3
+    assert np.abs(F).max() < 1e-12
+    assert np.allclose(vir[:3], vir[0], atol=1e-9 * n) and np.abs(vir[3:]).max() < 1e-9 * n
+    e = [O.tbsma_forces(*_cu_crystal(a=a), CU)[1] / n for a in (3.600, 3.615, 3.630)]
+    assert e[1] < e[0] and e[1] < e[2]
+
+
+def test_tbsma_dimer_closed_form():
+    """Two atoms at distance r: rho = psi(r) for both, so E = 2 A exp(-p(r/r0-1)) -
+    2 xi exp(-q(r/r0-1)) and the force is -dE/dr along the bond."""
+    r0, A, xi, p, q = CU.r0, CU.A, CU.xi, CU.p, CU.q
+    box = np.array([40.0, 40.0, 40.0])
+    for r in (2.2, 2.556, 3.1, 4.4):
+        pos = np.array([[10.0, 10.0, 10.0], [10.0 + r * 0.6, 10.0 + r * 0.8, 10.0]])
+        F, E, _ = O.tbsma_forces(pos, box, CU)
+        x = r / r0 - 1.0
+        E_ref = 2 * A * math.exp(-p * x) - 2 * xi * math.exp(-q * x)
+        dEdr = -2 * A * p / r0 * math.exp(-p * x) + 2 * xi * q / r0 * math.exp(-q * x)
+        assert abs(E - E_ref) <= 1e-13 * abs(E_ref)
+        u = np.array([0.6, 0.8, 0.0])
+        assert np.allclose(F[0], -dEdr * -u, atol=1e-13, rtol=1e-12)  # F_0 = -dE/dx_0, dr/dx_0 = -u
+        assert np.allclose(F[1], -F[0], atol=1e-15)
+
+
+def test_tbsma_force_is_minus_gradient_of_energy():
+    """Central differences of the total energy on a thermally disordered periodic crystal."""
+    pos, box = _cu_crystal(n_cells=4, jitter=0.08, seed=3)
+    F, _, _ = O.tbsma_forces(pos, box, CU)
+    h = 1e-5
+    for i in (0, 17, 101, 200):
+        for k in range(3):
+            xp = pos.copy()
+            xm = pos.copy()
+            xp[i, k] += h
+            xm[i, k] -= h
+            fd = -(O.tbsma_forces(xp, box, CU)[1] - O.tbsma_forces(xm, box, CU)[1]) / (2 * h)
+            assert abs(fd - F[i, k]) <= 1e-6 * max(1.0, abs(F[i, k])), (i, k, fd, F[i, k])
+
+
+def test_tbsma_virial_is_minus_strain_derivative():
+    """W_aa = -dE/d(epsilon_aa) under a homogeneous strain of positions and box."""
+    pos, box = _cu_crystal(n_cells=4, jitter=0.08, seed=4)
+    _, _, vir = O.tbsma_forces(pos, box, CU)
+    h = 1e-6
+    for k in range(3):
+        s = np.ones(3)
+        s[k] = 1 + h
+        ep = O.tbsma_forces(pos * s, box * s, CU)[1]
+        s[k] = 1 - h
+        em = O.tbsma_forces(pos * s, box * s, CU)[1]
+        assert abs(-(ep - em) / (2 * h) - vir[k]) <= 1e-6 * max(1.0, abs(vir[k]))
+
+
+def test_tbsma_invariances_and_brute_force():
+    pos, box = _cu_crystal(n_cells=4, jitter=0.08, seed=5)
+    F, E, vir, rho, ea = O.tbsma_forces(pos, box, CU, per_atom=True)
+    Fb, Eb, _ = O.tbsma_forces(pos, box, CU, brute=True)
+    assert np.abs(F - Fb).max() < 1e-12 and abs(E - Eb) < 1e-10
+    assert np.abs(F.sum(0)).max() < 1e-10
+    assert abs(ea.sum() - E) < 1e-9
+    assert np.all(rho > 0)
+    shift = np.array([1.3, -0.7, 2.9])
+    F2, E2, _ = O.tbsma_forces(W.wrap(pos + shift, box), box, CU)
+    assert np.abs(F2 - F).max() < 1e-10 and abs(E2 - E) < 1e-9
+    perm = np.random.default_rng(1).permutation(len(pos))
+    F3, E3, _ = O.tbsma_forces(pos[perm], box, CU)
+    assert np.abs(F3 - F[perm]).max() < 1e-10 and abs(E3 - E) < 1e-9
+    # an atom far from all others has no density, energy or force
+    big = box * 2.0  # the crystal fills [0, L)^3 of a (2L)^3 box; the far atom sits at 1.5 L
+    far = np.vstack([pos, [1.5 * box]])
+    F4, _, _, rho4, ea4 = O.tbsma_forces(far, big, CU, per_atom=True)
+    assert rho4[-1] == 0.0 and ea4[-1] == 0.0 and np.all(F4[-1] == 0.0)
