@@ -36,6 +36,15 @@ int mdgb_block_colour(const int32_t nc[3], int32_t block, int32_t *colour_out);
  * linear cell indices cx + nc[0]*(cy + nc[1]*cz). */
 int mdgb_tile_cells(const int32_t nc[3], int32_t block, int32_t cells_out[64]);
 
+/* The mixed path's FP64 decision band around r_cut^2: pairs whose FP32 r^2 lies
+ * within r_cut^2 (1 -/+ band) are decided by the FP64 definition (Sec. I: the pair
+ * set is fixed by |r| < r_cut).  frame 0: the tile frame of md_system (cells of
+ * width up to w_max, atoms at most half_skin from where they were binned); frame 1:
+ * the cell frame of the ensemble kernel (cells of width up to w_max, neighbour cells
+ * up to R away; half_skin unused).  The band is twice a worst-case bound on
+ * |r2_fp32 - r2| / r_cut^2, plus the rounding of the FP32 thresholds. */
+int mdgb_cut_band(int32_t frame, double w_max, double half_skin, int32_t R, double r_cut, double *band_out);
+
 #ifdef __cplusplus
 }
 #endif

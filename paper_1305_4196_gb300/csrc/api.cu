@@ -133,9 +133,8 @@ bool mixed(const md_system* s) { return s->precision == MD_MIXED; }
 bool half(const md_system* s) { return s->list_kind == MD_LIST_HALF_COLOUR8; }
 // md_step runs the full-list mixed path with velocity Verlet fused into the force kernel
 bool fused(const md_system* s) { return mixed(s) && !half(s) && !s->no_fuse; }
-// kernels per force evaluation: 8 colour launches (half lists); the FP32 kernel and its
-// exact pass (mixed, full lists); one kernel (FP64, full lists)
-int force_kernels(const md_system* s) { return half(s) ? 8 : (mixed(s) ? 2 : 1); }
+// kernels per force evaluation: 8 colour launches (half lists), else one
+int force_kernels(const md_system* s) { return half(s) ? 8 : 1; }
 
 // The state with its positions (FP32 cell-relative and FP64) in buffer p (0: st[0],
 // 1: xr_alt and pos_alt).  Fused steps read one buffer and write the other; outside
@@ -395,6 +394,16 @@ double fill_pair_table(PairTable& pt, const double* eps, const double* sigma, co
     return rcmax;
 }
 
+// The mixed kernels' FP64 decision band around r_cut^2, from the cell width, the skin and
+// the smallest pair cutoff (tile_frame_cut_band).
+void set_cut_band(md_system* s) {
+    double rc2_min = s->pt.rc2_d[0];
+    for (int t = 1; t < s->pt.nsp * s->pt.nsp; ++t) rc2_min = std::min(rc2_min, s->pt.rc2_d[t]);
+    const double wmax = std::max(s->g.w[0], std::max(s->g.w[1], s->g.w[2]));
+    s->pt.cut_band = (float)tile_frame_cut_band(wmax, 0.5 * s->skin, std::sqrt(rc2_min));
+    set_band_thresholds(s->pt);
+}
+
 int validate_params(md_system* s, const md_params* p, double r_cut) {
     if (!p) return fail(s, MD_ERR_ARG, "params is NULL");
     if (p->n_species < 1 || p->n_species > MAX_SPECIES)
@@ -629,7 +638,7 @@ int run_steps_direct_fused(md_system* s, int len, bool first, bool last) {
             CK(cudaEventRecord(ev.second, s->stream));
             s->ev_force.push_back(ev);
         }
-        s->launches += 2;  // fused force kernel and its exact pass
+        s->launches += 1;
         s->force_evals += 1;
         if (kkd) p ^= 1;
     }
@@ -672,7 +681,7 @@ int run_chunk_fused(md_system* s, int len, bool first, bool last) {
             s->ev_force.push_back(ev);
         }
         CK(cudaGraphLaunch(gr.exec, s->stream));
-        s->launches += 3;  // step control, fused force kernel, exact pass
+        s->launches += 2;  // step control, fused force kernel
         s->force_evals += 1;
         if (kkd) p ^= 1;
     }
@@ -850,6 +859,7 @@ int md_create(int64_t n, const double box[3], double r_cut, double skin, const m
     }
     g.nblock = (g.nc[0] / 2) * (g.nc[1] / 2) * (g.nc[2] / 2);
     g.ncell = g.nblock * 8;
+    set_cut_band(s);
     // initial capacities from the mean density (regrown on overflow)
     const double vol = box[0] * box[1] * box[2];
     const double rho = (double)n / vol;
@@ -879,8 +889,7 @@ int md_create(int64_t n, const double box[3], double r_cut, double skin, const m
         return bail(rc);
     if ((rc = dalloc(s, &d0.cell_start, (size_t)g.ncell + 1)) || (rc = dalloc(s, &d0.centre, 3 * (size_t)g.ncell)) ||
         (rc = dalloc(s, &d0.nl_cnt, n)) ||
-        (rc = dalloc(s, &d0.err, 1)) || (rc = dalloc(s, &d0.rebuild_flag, 1)) || (rc = dalloc(s, &d0.stats, 8)) ||
-        (rc = dalloc(s, &d0.redo, (size_t)n + 2)))
+        (rc = dalloc(s, &d0.err, 1)) || (rc = dalloc(s, &d0.rebuild_flag, 1)) || (rc = dalloc(s, &d0.stats, 8)))
         return bail(rc);
     if (p->precision == MD_MIXED) {
         if ((rc = dalloc(s, &d0.fq, 3 * (size_t)n)) || (rc = dalloc(s, &d0.pe_atom_f, n)) ||
@@ -915,7 +924,6 @@ int md_create(int64_t n, const double box[3], double r_cut, double skin, const m
         d1.err = d0.err;
         d1.rebuild_flag = d0.rebuild_flag;
         d1.stats = d0.stats;
-        d1.redo = d0.redo;
         d1.fq = d0.fq;
         d1.f = d0.f;
         d1.pe_atom_f = d0.pe_atom_f;
@@ -938,7 +946,6 @@ int md_create(int64_t n, const double box[3], double r_cut, double skin, const m
     if (cudaMemsetAsync(d0.err, 0, sizeof(uint32_t), s->stream) != cudaSuccess ||
         cudaMemsetAsync(s->d_ctrl, 0, 2 * sizeof(long long), s->stream) != cudaSuccess ||
         cudaMemsetAsync(d0.rebuild_flag, 0, sizeof(int32_t), s->stream) != cudaSuccess ||
-        cudaMemsetAsync(d0.redo, 0, 2 * sizeof(int32_t), s->stream) != cudaSuccess ||
         cudaStreamSynchronize(s->stream) != cudaSuccess)
         return bail(MD_ERR_CUDA);
     *out = s;
@@ -1092,6 +1099,7 @@ int md_set_params(md_system* s, const double* eps, const double* sigma, const do
     DeviceGuard dg(s->device);
     // kernels read the table by value: queued work keeps the old one, captured graphs are redone
     fill_pair_table(s->pt, eps, sigma, rcut, s->rcut_default);
+    set_cut_band(s);
     s->forces_valid = false;
     s->graphs_valid = false;
     return MD_OK;

@@ -324,6 +324,15 @@ int md_batch_create(int32_t n_systems, const int64_t* n_atoms, const double* box
             b->big_ids.push_back(k);
         }
     }
+    // FP64 decision band: the widest any system needs, for either cell divisor
+    double band = 0.0;
+    for (int k = 0; k < n_systems; ++k)
+        for (int R = 1; R <= 2; ++R) {
+            const BatchSys y = make_sys(b, k, R);
+            band = std::max(band, cell_frame_cut_band(std::max(y.w[0], std::max(y.w[1], y.w[2])), R, r_cut));
+        }
+    b->pt.cut_band = (float)band;
+    set_band_thresholds(b->pt);
     int rc;
     BatchState& st = b->st;
     st.ntot = b->ntot;

@@ -36,6 +36,14 @@ int mdgb_grid_shape(const double box[3], double r_list, int32_t nc_out[3]) {
     return MD_OK;
 }
 
+int mdgb_cut_band(int32_t frame, double w_max, double half_skin, int32_t R, double r_cut, double* band_out) {
+    if (!band_out || !(w_max > 0.0) || !(half_skin >= 0.0) || !(r_cut > 0.0) || (frame != 0 && frame != 1) ||
+        (frame == 1 && (R < 1 || R > 2)))
+        return MD_ERR_ARG;
+    *band_out = frame == 0 ? tile_frame_cut_band(w_max, half_skin, r_cut) : cell_frame_cut_band(w_max, R, r_cut);
+    return MD_OK;
+}
+
 int mdgb_num_blocks(const int32_t nc[3], int32_t* nblock_out) {
     Geometry g{};
     if (!nblock_out || !make_geometry(nc, g)) return MD_ERR_ARG;

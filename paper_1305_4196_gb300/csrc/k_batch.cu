@@ -184,7 +184,7 @@ __device__ void batch_forces(const BatchSys& y, BatchState st, const PairTable& 
                              float* __restrict__ pe_out) {
     const int n = y.n, R = y.R;
     const float sig2 = pt.sig2_f[0], c48 = pt.c48_f[0], c24 = pt.c24_f[0], c4 = pt.c4_f[0];
-    const float rc2_lo = pt.rc2_f[0] * (1.0f - CUT_BAND), rc2_hi = pt.rc2_f[0] * (1.0f + CUT_BAND);
+    const float rc2_lo = pt.rc2lo_f[0], rc2_hi = pt.rc2hi_f[0];
     for (int p = threadIdx.x; p < n; p += blockDim.x) {
         const int a = sm.perm[p];
         const float4 pi = sm.xr[p];

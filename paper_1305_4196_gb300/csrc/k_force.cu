@@ -189,7 +189,7 @@ __device__ __forceinline__ void fix_add2(FixAcc& acc, f2_t fs2, f2_t d, f2_t mag
 // would go through local memory).
 struct SpeciesTable {
     float sig2[MAX_PAIR], c48[MAX_PAIR], c24[MAX_PAIR], c4[MAX_PAIR], rc2[MAX_PAIR];
-    float rc2lo[MAX_PAIR], rc2hi[MAX_PAIR];  // r_cut^2 (1 -/+ CUT_BAND): the FP64 decision band
+    float rc2lo[MAX_PAIR], rc2hi[MAX_PAIR];  // r_cut^2 (1 -/+ cut_band): the FP64 decision band
     double rc2d[MAX_PAIR];                   // FP64 r_cut^2
 };
 
@@ -201,8 +201,8 @@ __device__ __forceinline__ void load_species_table(const PairTable& pt, SpeciesT
         st.c24[t] = pt.c24_f[t];
         st.c4[t] = pt.c4_f[t];
         st.rc2[t] = pt.rc2_f[t];
-        st.rc2lo[t] = pt.rc2_f[t] * (1.0f - CUT_BAND);
-        st.rc2hi[t] = pt.rc2_f[t] * (1.0f + CUT_BAND);
+        st.rc2lo[t] = pt.rc2lo_f[t];
+        st.rc2hi[t] = pt.rc2hi_f[t];
         st.rc2d[t] = pt.rc2_d[t];
     }
 }
@@ -283,6 +283,99 @@ __device__ __forceinline__ void full_epilogue(const DevState& s, const PairTable
     }
 }
 
+// Exact finish of one atom by one warp (all 32 lanes), for an atom that the FP32 loop
+// below cannot finish: a pair whose FP32 r^2 lies within the band around r_cut^2 (the
+// cutoff is decided by the FP64 definition) or a pair force component that may reach
+// 2048 eps/sigma (beyond the two-part split; or not finite).  About one atom in 1,500 of
+// a liquid.  The neighbours come from the CTA's tile, so every other pair gets exactly
+// the term the FP32 loop adds; band pairs are decided in FP64 in the oracle's operation
+// order; large terms are rounded in FP64 (fix_wide_terms).  Lane sums are exact
+// integers, so the warp total does not depend on how the list is spread over the lanes.
+// The same epilogue follows.  This runs after the loop, not inside it: a call from the
+// loop cost the kernel half its speed.
+template <bool SINGLE, bool EV, int MODE>
+__device__ __forceinline__ void finish_atom_warp(const DevState& s, const Geometry& g, const PairTable& pt,
+                                                 const float4* __restrict__ tile, const SpeciesTable& stab,
+                                                 const TileMeta& m, int ui, float fs2_max, const StepOut& out,
+                                                 double dt, float lim2_f) {
+    const int lane = threadIdx.x & 31;
+    const int T = m.prefix[64];
+    const int gi = m.start[0] + ui;
+    const float4 pi = tile[ui];
+    const int si = __float_as_int(pi.w);
+    const int nsp = pt.nsp;
+    const int nent = ((s.nl_cnt[gi] + 7) >> 3) * 8;
+    FixAcc ax{0u, 0u}, ay{0u, 0u}, az{0u, 0u};
+    int nterms = 0;
+    float pe = 0.f, w0 = 0.f, w1 = 0.f, w2 = 0.f, w3 = 0.f, w4 = 0.f, w5 = 0.f;
+    for (int k = lane; k < nent; k += 32) {
+        const int u = s.nl[((size_t)(k >> 3) * s.np + gi) * 8 + (k & 7)];
+        if (u >= T) continue;  // padding (the tile's dummy slot): no force
+        const float4 pj = tile[u];
+        const float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
+        const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+        const int t = SINGLE ? 0 : si * nsp + __float_as_int(pj.w);
+        const float inv = rcp_approx(r2);
+        const float s2 = stab.sig2[t] * inv;
+        const float s6 = s2 * s2 * s2;
+        const float fs = __fmul_rn(__fmul_rn(__fmaf_rn(stab.c48[t], s6, -stab.c24[t]), s6), inv);
+        bool inside = r2 < stab.rc2lo[t];
+        if (!inside && r2 < stab.rc2hi[t])
+            inside = fp64_pair_test(s.x, s.y, s.z, g.L[0], g.L[1], g.L[2], gi, tile_global_index(m, u),
+                                    stab.rc2d[t]);
+        const float fs2 = inside ? fs : 0.0f;
+        if (fabsf(fs2) < fs2_max) {
+            fix_add(ax, fs2, dx);
+            fix_add(ay, fs2, dy);
+            fix_add(az, fs2, dz);
+        } else {
+            fix_add_wide(ax, fs2, dx, s.err);
+            fix_add_wide(ay, fs2, dy, s.err);
+            fix_add_wide(az, fs2, dz, s.err);
+        }
+        ++nterms;
+        if (EV && inside) {
+            const float gq = fs2 * (1.0f / FS_SCALE);
+            pe += stab.c4[t] * s6 * (s6 - 1.0f);
+            w0 += dx * (gq * dx);
+            w1 += dy * (gq * dy);
+            w2 += dz * (gq * dz);
+            w3 += dx * (gq * dy);
+            w4 += dx * (gq * dz);
+            w5 += dy * (gq * dz);
+        }
+    }
+    long long qx = fix_final(ax, nterms), qy = fix_final(ay, nterms), qz = fix_final(az, nterms);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        qx += __shfl_xor_sync(0xffffffffu, qx, o);
+        qy += __shfl_xor_sync(0xffffffffu, qy, o);
+        qz += __shfl_xor_sync(0xffffffffu, qz, o);
+        if (EV) {  // a fixed butterfly: the FP32 sums are reproducible
+            pe += __shfl_xor_sync(0xffffffffu, pe, o);
+            w0 += __shfl_xor_sync(0xffffffffu, w0, o);
+            w1 += __shfl_xor_sync(0xffffffffu, w1, o);
+            w2 += __shfl_xor_sync(0xffffffffu, w2, o);
+            w3 += __shfl_xor_sync(0xffffffffu, w3, o);
+            w4 += __shfl_xor_sync(0xffffffffu, w4, o);
+            w5 += __shfl_xor_sync(0xffffffffu, w5, o);
+        }
+    }
+    if (lane == 0) {
+        full_epilogue<SINGLE, MODE>(s, pt, gi, si, qx, qy, qz, out, dt, lim2_f);
+        if (EV) {
+            const int64_t n = s.n;
+            s.pe_atom_f[gi] = 0.5f * pe;
+            s.vir_atom_f[gi] = 0.5f * w0;
+            s.vir_atom_f[n + gi] = 0.5f * w1;
+            s.vir_atom_f[2 * n + gi] = 0.5f * w2;
+            s.vir_atom_f[3 * n + gi] = 0.5f * w3;
+            s.vir_atom_f[4 * n + gi] = 0.5f * w4;
+            s.vir_atom_f[5 * n + gi] = 0.5f * w5;
+        }
+    }
+}
+
 // ---------------------------------------------------------------- mixed, full list
 // One thread per atom, two neighbours per iteration in packed FP32x2 arithmetic; each
 // neighbour is one 128-bit shared-memory load.
@@ -306,9 +399,12 @@ __global__ void __maxnreg__(SINGLE ? MDGB_FULL_MAX_REGS : MDGB_FULL_MAX_REGS_SPE
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ TileMeta m;
     __shared__ SpeciesTable stab;
+    __shared__ int nqueued;
     float4* tile = reinterpret_cast<float4*>(smem);
+    uint16_t* queued = reinterpret_cast<uint16_t*>(tile + tile_cap);  // own atoms left to finish_atom_warp
     const int b = blockIdx.x;
     load_species_table(pt, stab);
+    if (threadIdx.x == 0) nqueued = 0;
     tile_meta(g, s.cell_start, b, m);
     const int T = m.prefix[64];
     if (T + 1 > tile_cap) {
@@ -330,7 +426,7 @@ __global__ void __maxnreg__(SINGLE ? MDGB_FULL_MAX_REGS : MDGB_FULL_MAX_REGS_SPE
     const f2_t sig2_1 = f2_pack(pt.sig2_f[0], pt.sig2_f[0]);
     const f2_t c48_1 = f2_pack(pt.c48_f[0], pt.c48_f[0]);
     const f2_t nc24_1 = f2_pack(-pt.c24_f[0], -pt.c24_f[0]);
-    const float rc2hi_1 = pt.rc2_f[0] * (1.0f + CUT_BAND), rc2lo_1 = pt.rc2_f[0] * (1.0f - CUT_BAND);
+    const float rc2hi_1 = pt.rc2hi_f[0], rc2lo_1 = pt.rc2lo_f[0];  // kernel parameters: constant-bank operands
     for (int ui = threadIdx.x; ui < nown; ui += blockDim.x) {
         const int gi = blk0 + ui;
         const float4 pi = tile[ui];
@@ -365,7 +461,7 @@ __global__ void __maxnreg__(SINGLE ? MDGB_FULL_MAX_REGS : MDGB_FULL_MAX_REGS_SPE
             float fa, fb;
             f2_unpack(fsv, fa, fb);
             // inside for certain below the band, tentatively inside up to its top: a pair in
-            // the band sends the atom through the exact redo (FP64 cutoff decision)
+            // the band leaves the atom to finish_atom_warp (FP64 cutoff decision)
             const bool ina = r2a < hia_c, inb = r2b < hib_c;
             fa = ina ? fa : 0.0f;
             fb = inb ? fb : 0.0f;
@@ -394,8 +490,8 @@ __global__ void __maxnreg__(SINGLE ? MDGB_FULL_MAX_REGS : MDGB_FULL_MAX_REGS_SPE
                 w5 += dya * (ga * dza) + dyb * (gb * dzb);
             }
         });
-        if (bad) {  // finished by the exact pass (k_force_redo), epilogue included
-            s.redo[2 + atomicAdd(s.redo, 1)] = gi;
+        if (bad) {  // finished after the loop by finish_atom_warp, epilogue included
+            queued[atomicAdd(&nqueued, 1)] = (uint16_t)ui;
             continue;
         }
         const int nterms = nch * 8;
@@ -412,126 +508,10 @@ __global__ void __maxnreg__(SINGLE ? MDGB_FULL_MAX_REGS : MDGB_FULL_MAX_REGS_SPE
             s.vir_atom_f[5 * n + gi] = 0.5f * w5;
         }
     }
-}
-
-// ---------------------------------------------------------------- mixed, full list: exact pass
-// Atoms that the full-list kernel cannot finish in FP32 - a pair whose FP32 r^2 lies
-// within CUT_BAND of r_cut^2 (the cutoff is decided by the FP64 definition) or a pair
-// force component that may reach 2048 eps/sigma (beyond the two-part split; or not
-// finite) - are queued by it, and it skips their force and epilogue.  About one atom in
-// 600 of a liquid has such a pair.  This kernel finishes them, one warp per atom: the
-// FP32 block-frame coordinates are rebuilt with the staging's own additions, so every
-// other pair gets exactly the term the FP32 kernel would have added; band pairs are
-// decided in FP64 in the oracle's operation order; large terms are rounded in FP64
-// (fix_wide_terms).  Lane sums are exact integers, so the warp total does not depend
-// on how the list is spread over the lanes.  The same epilogue follows.  Keeping this
-// code out of the FP32 kernel keeps its registers for the pair loop (a call from its
-// loop costs it half its speed).  The last CTA to finish empties the queue.
-constexpr int REDO_WARPS = 8;
-constexpr int REDO_CTAS = 2 * 152;  // the queue is short; CTAs with no work exit at once
-
-template <bool SINGLE, bool EV, int MODE>
-__global__ void __launch_bounds__(REDO_WARPS * 32) k_force_redo(DevState s, Geometry g, PairTable pt,
-                                                                 TileOffsets to, float fs2_max, StepOut out,
-                                                                 double dt, float lim2_f) {
-    __shared__ SpeciesTable stab;
-    __shared__ TileMeta metas[REDO_WARPS];
-    __shared__ int last;
-    load_species_table(pt, stab);
-    const int count = s.redo[0];
     __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    TileMeta& m = metas[warp];
-    const int nsp = pt.nsp;
-    for (int q = blockIdx.x * REDO_WARPS + warp; q < count; q += gridDim.x * REDO_WARPS) {
-        const int gi = s.redo[2 + q];
-        const int b = s.cell_of[gi] >> 3;  // cells are numbered block by block, 8 per block
-        tile_meta_warp(g, s.cell_start, b, m);
-        const int T = m.prefix[64];
-        const float4 pi = tile_coord(m, to, s.xr, gi - m.start[0]);  // own atoms: tile index = rank in block
-        const int si = __float_as_int(pi.w);
-        const int nent = ((s.nl_cnt[gi] + 7) >> 3) * 8;
-        FixAcc ax{0u, 0u}, ay{0u, 0u}, az{0u, 0u};
-        int nterms = 0;
-        float pe = 0.f, w0 = 0.f, w1 = 0.f, w2 = 0.f, w3 = 0.f, w4 = 0.f, w5 = 0.f;
-        for (int k = lane; k < nent; k += 32) {
-            const int u = s.nl[((size_t)(k >> 3) * s.np + gi) * 8 + (k & 7)];
-            if (u >= T) continue;  // padding (the tile's dummy slot): no force
-            const float4 pj = tile_coord(m, to, s.xr, u);
-            const float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
-            const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-            const int t = SINGLE ? 0 : si * nsp + __float_as_int(pj.w);
-            const float inv = rcp_approx(r2);
-            const float s2 = stab.sig2[t] * inv;
-            const float s6 = s2 * s2 * s2;
-            const float fs = __fmul_rn(__fmul_rn(__fmaf_rn(stab.c48[t], s6, -stab.c24[t]), s6), inv);
-            bool inside = r2 < stab.rc2lo[t];
-            if (!inside && r2 < stab.rc2hi[t])
-                inside = fp64_pair_test(s.x, s.y, s.z, g.L[0], g.L[1], g.L[2], gi, tile_global_index(m, u),
-                                        stab.rc2d[t]);
-            const float fs2 = inside ? fs : 0.0f;
-            if (fabsf(fs2) < fs2_max) {
-                fix_add(ax, fs2, dx);
-                fix_add(ay, fs2, dy);
-                fix_add(az, fs2, dz);
-            } else {
-                fix_add_wide(ax, fs2, dx, s.err);
-                fix_add_wide(ay, fs2, dy, s.err);
-                fix_add_wide(az, fs2, dz, s.err);
-            }
-            ++nterms;
-            if (EV && inside) {
-                const float gq = fs2 * (1.0f / FS_SCALE);
-                pe += stab.c4[t] * s6 * (s6 - 1.0f);
-                w0 += dx * (gq * dx);
-                w1 += dy * (gq * dy);
-                w2 += dz * (gq * dz);
-                w3 += dx * (gq * dy);
-                w4 += dx * (gq * dz);
-                w5 += dy * (gq * dz);
-            }
-        }
-        long long qx = fix_final(ax, nterms), qy = fix_final(ay, nterms), qz = fix_final(az, nterms);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            qx += __shfl_xor_sync(0xffffffffu, qx, o);
-            qy += __shfl_xor_sync(0xffffffffu, qy, o);
-            qz += __shfl_xor_sync(0xffffffffu, qz, o);
-            if (EV) {  // a fixed butterfly: the FP32 sums are reproducible
-                pe += __shfl_xor_sync(0xffffffffu, pe, o);
-                w0 += __shfl_xor_sync(0xffffffffu, w0, o);
-                w1 += __shfl_xor_sync(0xffffffffu, w1, o);
-                w2 += __shfl_xor_sync(0xffffffffu, w2, o);
-                w3 += __shfl_xor_sync(0xffffffffu, w3, o);
-                w4 += __shfl_xor_sync(0xffffffffu, w4, o);
-                w5 += __shfl_xor_sync(0xffffffffu, w5, o);
-            }
-        }
-        if (lane == 0) {
-            full_epilogue<SINGLE, MODE>(s, pt, gi, si, qx, qy, qz, out, dt, lim2_f);
-            if (EV) {
-                const int64_t n = s.n;
-                s.pe_atom_f[gi] = 0.5f * pe;
-                s.vir_atom_f[gi] = 0.5f * w0;
-                s.vir_atom_f[n + gi] = 0.5f * w1;
-                s.vir_atom_f[2 * n + gi] = 0.5f * w2;
-                s.vir_atom_f[3 * n + gi] = 0.5f * w3;
-                s.vir_atom_f[4 * n + gi] = 0.5f * w4;
-                s.vir_atom_f[5 * n + gi] = 0.5f * w5;
-            }
-        }
-        __syncwarp();  // m is refilled for the next atom
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        last = atomicAdd(s.redo + 1, 1) == (int)gridDim.x - 1;
-    }
-    __syncthreads();
-    if (last && threadIdx.x == 0) {  // every CTA has read the count: empty the queue
-        s.redo[0] = 0;
-        s.redo[1] = 0;
-    }
+    const int nq = nqueued;
+    for (int k = threadIdx.x >> 5; k < nq; k += blockDim.x >> 5)
+        finish_atom_warp<SINGLE, EV, MODE>(s, g, pt, tile, stab, m, queued[k], fs2_max, out, dt, lim2_f);
 }
 
 // ---------------------------------------------------------------- mixed, half list, one colour
@@ -581,8 +561,7 @@ __global__ void __launch_bounds__(F_THREADS) k_force_mixed_half(DevState s, Geom
             float s6;
             bool inside;
             const float fs = lj_fs_unmasked<SINGLE>(pt, t, r2, s6, inside);
-            const float rc2t = SINGLE ? pt.rc2_f[0] : pt.rc2_f[t];
-            if (fabsf(r2 - rc2t) < CUT_BAND * rc2t)  // rare: decide the cutoff in FP64
+            if (r2 < pt.rc2hi_f[t] && !(r2 < pt.rc2lo_f[t]))  // rare: decide the cutoff in FP64
                 inside = fp64_pair_test(s.x, s.y, s.z, g.L[0], g.L[1], g.L[2], gi, tile_global_index(m, u),
                                         SINGLE ? pt.rc2_d[0] : pt.rc2_d[t]);
             const float fs2 = inside ? fs : 0.0f;
@@ -811,6 +790,7 @@ size_t force_smem_bytes(int mixed, int half, int with_energy, int tile_cap) {
     if (mixed) {
         size_t b = (size_t)tile_cap * sizeof(float4);
         if (half) b += (size_t)tile_cap * 7 * sizeof(int);
+        else b += ((size_t)tile_cap * sizeof(uint16_t) + 15) & ~(size_t)15;  // queue of own atoms
         return b;
     }
     size_t b = (size_t)tile_cap * (3 * sizeof(double) + sizeof(int));
@@ -875,18 +855,6 @@ void launch_forces_mixed(const DevState& s, const Geometry& g, const PairTable& 
         else
             k_force_mixed_full<false, true, FM_FORCE><<<g.nblock, FULL_THREADS, smem, st>>>(s, g, pt, to, tile_cap,
                                                                                           fs2_max, StepOut{}, 0.0, 0.f);
-        if (single && !with_energy)
-            k_force_redo<true, false, FM_FORCE><<<REDO_CTAS, REDO_WARPS * 32, 0, st>>>(s, g, pt, to, fs2_max,
-                                                                                    StepOut{}, 0.0, 0.f);
-        else if (single)
-            k_force_redo<true, true, FM_FORCE><<<REDO_CTAS, REDO_WARPS * 32, 0, st>>>(s, g, pt, to, fs2_max,
-                                                                                   StepOut{}, 0.0, 0.f);
-        else if (!with_energy)
-            k_force_redo<false, false, FM_FORCE><<<REDO_CTAS, REDO_WARPS * 32, 0, st>>>(s, g, pt, to, fs2_max,
-                                                                                     StepOut{}, 0.0, 0.f);
-        else
-            k_force_redo<false, true, FM_FORCE><<<REDO_CTAS, REDO_WARPS * 32, 0, st>>>(s, g, pt, to, fs2_max,
-                                                                                    StepOut{}, 0.0, 0.f);
         return;
     }
     cudaMemsetAsync(s.fq, 0, sizeof(long long) * 3 * (size_t)s.n, st);
@@ -912,7 +880,6 @@ static void launch_full_mode(const DevState& s, const Geometry& g, const PairTab
                              cudaStream_t st) {
     k_force_mixed_full<SINGLE, false, MODE><<<g.nblock, FULL_THREADS, smem, st>>>(s, g, pt, to, tile_cap, fs2_max,
                                                                                 out, dt, lim2_f);
-    k_force_redo<SINGLE, false, MODE><<<REDO_CTAS, REDO_WARPS * 32, 0, st>>>(s, g, pt, to, fs2_max, out, dt, lim2_f);
 }
 
 void launch_forces_mixed_fused(const DevState& s, const Geometry& g, const PairTable& pt, const TileOffsets& to,

@@ -121,9 +121,8 @@ __global__ void __launch_bounds__(G_THREADS) k_force_backward(DevState s, Geomet
             if (sizeof(T) == 8) {
                 if (!(r2 < (T)pt.rc2_d[tt])) continue;
             } else {
-                const float rc2f = pt.rc2_f[tt];
-                if (!((float)r2 < rc2f * (1.0f + CUT_BAND))) continue;
-                if (!((float)r2 < rc2f * (1.0f - CUT_BAND)) &&  // rare: decide the cutoff in FP64
+                if (!((float)r2 < pt.rc2hi_f[tt])) continue;
+                if (!((float)r2 < pt.rc2lo_f[tt]) &&  // rare: decide the cutoff in FP64
                     !fp64_pair_test(s.x, s.y, s.z, g.L[0], g.L[1], g.L[2], (int)gi, t.gid[u], pt.rc2_d[tt]))
                     continue;
             }

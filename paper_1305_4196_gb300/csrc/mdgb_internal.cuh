@@ -16,6 +16,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cmath>
+
 namespace mdgb {
 
 // device error bits (sticky, OR-ed into a device word, read by the host)
@@ -49,7 +51,57 @@ struct PairTable {
     double hdtm[MAX_SPECIES];  // (dt/2) / m per species
     double hdtm_q[MAX_SPECIES];  // (dt/2) / m * 2^-32: half kick per unit of Q31.32 force
     double mass[MAX_SPECIES];
+    float cut_band;  // mixed path: pairs with FP32 r^2 within r_cut^2 (1 -/+ cut_band) are decided in FP64
+    float rc2lo_f[MAX_PAIR], rc2hi_f[MAX_PAIR];  // r_cut^2 (1 -/+ cut_band) in FP32
 };
+
+// The FP32 thresholds of the band (after pt.cut_band and pt.rc2_f are set).
+inline void set_band_thresholds(PairTable& pt) {
+    for (int t = 0; t < pt.nsp * pt.nsp; ++t) {
+        pt.rc2lo_f[t] = (float)((double)pt.rc2_f[t] * (1.0 - (double)pt.cut_band));
+        pt.rc2hi_f[t] = (float)((double)pt.rc2_f[t] * (1.0 + (double)pt.cut_band));
+    }
+}
+
+// ---- the FP64 decision band around r_cut^2 (host)
+// Half an FP32 ulp of the numbers of magnitude up to v > 0: 2^(floor(log2 v) - 24).
+inline double f32_half_ulp(double v) {
+    int e = 0;
+    std::frexp(v, &e);
+    return std::ldexp(1.0, e - 25);
+}
+
+// |r2_fp32 - r2| bound for a pair at distance up to ~r_cut whose FP32 displacement
+// components each carry at most e_d of error, relative to r_cut^2: the error of
+// d.d through the components (2 |d|_1 e_d + 3 e_d^2, |d|_1 <= sqrt(3) |d|) and the three
+// roundings of r2 = fma(dz, dz, fma(dy, dy, dx * dx)).
+inline double r2_rel_bound(double e_d, double rc) {
+    const double dmax = rc * 1.001;
+    const double err = 2.0 * std::sqrt(3.0) * dmax * e_d + 3.0 * e_d * e_d + 3.0 * f32_half_ulp(dmax * dmax);
+    return err / (rc * rc);
+}
+
+// Band for the tile frame of the list, force and backward kernels: a coordinate is the
+// FP32 rounding of its offset from the build cell's centre (at most w/2 + skin/2 away,
+// as the skin/2 rule rebuilds before an atom moves further), plus the FP32 tile offset
+// (t - 3/2) w (at most 3w/2), rounded; the displacement is the FP32 difference of two
+// coordinates.  Twice the bound, for the smallest cutoff rc_min.
+inline double tile_frame_cut_band(double w_max, double half_skin, double rc_min) {
+    const double a = 0.5 * w_max + half_skin;
+    const double e_coord = f32_half_ulp(a) + f32_half_ulp(1.5 * w_max) + f32_half_ulp(1.5 * w_max + a);
+    const double e_d = 2.0 * e_coord + f32_half_ulp(rc_min * 1.001);
+    return 2.0 * r2_rel_bound(e_d, rc_min) + 3.0e-7;  // + the FP32 roundings of r_cut^2 (1 -/+ band)
+}
+
+// Band for the one-CTA-per-system ensemble kernel: coordinates relative to the centre of
+// the cell they were binned into this step (at most w/2 away), the neighbour cell's
+// shift k w with |k| <= R (FP32 w, exact multiples for |k| <= 2) added in FP32, then the
+// FP32 difference.  Twice the bound.
+inline double cell_frame_cut_band(double w_max, int R, double rc) {
+    const double e_d = 2.0 * f32_half_ulp(0.5 * w_max) + R * f32_half_ulp(w_max) +
+                       f32_half_ulp((0.5 + R) * w_max) + f32_half_ulp(rc * 1.001);
+    return 2.0 * r2_rel_bound(e_d, rc) + 3.0e-7;
+}
 
 __host__ __device__ inline int block_id_of(const Geometry& g, int bx, int by, int bz) {
     int col = (bx & 1) | ((by & 1) << 1) | ((bz & 1) << 2);
@@ -123,8 +175,6 @@ struct DevState {
     uint32_t *err;          // sticky error bits
     int32_t *rebuild_flag;  // set when some atom moved more than skin/2
     int32_t *stats;         // [0] max list length, [1] max tile size, [2..3] sum of list lengths (u64)
-    int32_t *redo;          // mixed full lists: atoms for the exact pass; [0] count, [1] finished
-                            // CTAs of the exact pass, [2 ..] cell-ordered indices (n + 2 entries)
 };
 
 // ---- kernel launchers (defined in the .cu files)

@@ -131,10 +131,6 @@ __device__ __forceinline__ bool fp64_pair_test(const double* __restrict__ x, con
     return r2 < rl2;
 }
 
-// Relative width of the band around r_cut^2 inside which the mixed-precision kernels
-// decide the cutoff in FP64: the FP32 r^2 of a pair is within a relative 1.2e-6 of the
-// exact one (block-frame coordinates within 3e-7, differences within 7e-7).
-constexpr float CUT_BAND = 1.0e-5f;
 
 // Cell-ordered global index of tile index u.
 __device__ __forceinline__ int tile_global_index(const TileMeta& m, int u) {
