@@ -52,6 +52,8 @@ def parse():
     p.add_argument("--no-extras", action="store_true", help="skip the FP64 / half-list comparison runs")
     p.add_argument("--cpu-steps", type=int, default=2, help="oracle time steps in the CPU baseline sample")
     p.add_argument("--e2e-steps", type=int, default=3)
+    p.add_argument("--many-body", action="store_true",
+                   help="only time the TB-SMA copper system (the many_body extra) and print it")
     return p.parse_args()
 
 
@@ -411,6 +413,7 @@ def comparisons(args, sysm, M, stream, value, list_len_hom):
         s.close()
     out["force_matching"] = force_matching_timing(M, stream)
     out["batch_ensemble"] = batch_ensemble_timing(stream)
+    out["many_body"] = many_body_timing(M, stream)
     # the paper's dependent wave schedule on the two workloads' cell grids, beside the
     # 8 colour phases (host tool; no GPU work)
     from paper_1305_4196_gb300 import waves as WV
@@ -476,6 +479,45 @@ def batch_ensemble_timing(stream, steps=200):
     return res
 
 
+def many_body_timing(M, stream, steps=200):
+    """The paper's bulk copper benchmark size, 1,000,188 atoms (63^3 fcc cells at 3.615 A),
+    with the Cleri-Rosato tight-binding second-moment potential (cut between the fifth and
+    sixth shells), room-temperature displacements and velocities (0.08 A, kT = 0.02585 eV),
+    skin 0.4 A, 1 fs steps: velocity Verlet with the density and force passes launched from
+    a CUDA graph per step.  Force time from the library's events (both passes)."""
+    import torch
+    from paper_1305_4196_gb300 import workloads as W
+    P = W.copper_tbsma()
+    mass, kT = P["mass"], 0.02585
+    pos, box = W.fcc_lattice(63, 63, 63, 3.615)
+    pos = W.gaussian_jitter(pos, box, 0.08, 11, stream=2)
+    vel = W.thermal_velocities(np.full(len(pos), mass), kT, 11, stream=1)
+    s = M.System(len(pos), box, r_cut=P["rc"], skin=0.4, mass=mass, dt=0.0982, precision=M.MD_MIXED,
+                 stream=stream.cuda_stream)
+    s.set_tbsma(P["A"], P["xi"], P["p"], P["q"], P["r0"], P["rc"])
+    s.set_state(pos, vel, np.zeros(len(pos), dtype=np.int32))
+    s.step(20)
+    torch.cuda.synchronize()
+    s.set_timing(True)
+    i0 = s.info()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    s.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    i1 = s.info()
+    s.set_timing(False)
+    ms = e0.elapsed_time(e1)
+    f_ms = (i1["force_ms"] - i0["force_ms"]) / max(i1["timed_force_evals"] - i0["timed_force_evals"], 1)
+    res = {"workload": "fcc Cu 1,000,188 atoms, TB-SMA (Cleri-Rosato), 300 K", "atoms": len(pos),
+           "timesteps": steps, "value": len(pos) * steps / (ms * 1e-3), "unit": METRIC,
+           "ns_per_atom_timestep": ms * 1e6 / (len(pos) * steps), "force_ms_avg": f_ms,
+           "rebuilds_per_timestep": (i1["n_builds"] - i0["n_builds"]) / steps,
+           "mean_list_length": i1["list_entries"] / len(pos)}
+    s.close()
+    return res
+
+
 def force_matching_timing(M, stream, n_snap=8):
     """Forward + backward (md_forces, md_forces_backward) of the force-matching loss on
     32,000-atom Kob-Andersen snapshots (fcc sites at rho* = 1.2, 80:20 species shuffle, 0.05
@@ -528,7 +570,14 @@ def force_matching_timing(M, stream, n_snap=8):
 
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.many_body:
+        import torch
+        from paper_1305_4196_gb300 import build as B
+        B.build()
+        from paper_1305_4196_gb300 import mdgb as M
+        stream = torch.cuda.Stream()
+        print(json.dumps({"many_body": many_body_timing(M, stream, steps=args.inner)}))
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

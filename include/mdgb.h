@@ -187,6 +187,27 @@ int md_energy_virial(md_system *s, double *pe, double *ke, double virial[6]);
 int md_set_params(md_system *s, const double *eps, const double *sigma, const double *rcut);
 
 /*
+ * Switch the system to the tight-binding second-moment many-body potential of
+ * Cleri and Rosato (1993), the potential of all of the paper's benchmarks
+ * (Sec. III; the paper gives no parameters):
+ *   E = sum_i [ sum_j A exp(-p (r_ij/r0 - 1)) - sqrt( sum_j xi^2 exp(-2q (r_ij/r0 - 1)) ) ]
+ * with both sums over the neighbours closer than r_cut (strict <; the pair set
+ * is decided by the FP64 definition as for the pair potential).  Forces are
+ * evaluated in two passes over the cell tasks (densities, then forces, which
+ * need 1/sqrt(rho) of both atoms of a pair); md_forces, md_step and
+ * md_energy_virial (per-atom energy sum_j phi - sqrt(rho)) use it until
+ * md_set_params switches back to the pair table.  Units are the caller's (eV,
+ * Angstrom and amu for the published copper set: A = 0.0855, xi = 1.224,
+ * p = 10.960, q = 2.278, r0 = 2.5562).  md_step then runs velocity Verlet
+ * with separate force and integration launches.  Requires one species,
+ * MD_MIXED, MD_LIST_FULL, r_cut no larger than the cutoff the system was
+ * created with (the lists' radius) and xi^2 exp(2q) < 2000 (the fixed-point
+ * density range).  Errors: MD_ERR_ARG.  No derivatives (md_forces_backward)
+ * for this potential.
+ */
+int md_set_tbsma(md_system *s, double A, double xi, double p, double q, double r0, double r_cut);
+
+/*
  * Reverse-mode derivatives for force matching.  For a scalar loss L of the
  * forces at the current state, with grad_f = dL/dF (N x 3, original order)
  * given, writes

@@ -59,6 +59,9 @@ struct md_system {
     // double-buffered; g_fused[closing kick only / kick-kick-drift][buffer read]
     StepGraph g_fused[2][2];
     float4* xr_alt = nullptr;
+    int potential = 0;       // 0: Lennard-Jones pair table; 1: TB-SMA many-body (md_set_tbsma)
+    TBTable tb{};
+    float* emb = nullptr;    // TB-SMA: 1/sqrt(rho) per atom (cell order)
     double* pos_alt = nullptr;  // FP64 positions of buffer 1 (x, y, z: n each)
     bool graphs_valid = false;
     int graph_tile_cap = 0, graph_list_cap = 0;
@@ -132,9 +135,9 @@ void dfree(md_system* s, void* p) {
 bool mixed(const md_system* s) { return s->precision == MD_MIXED; }
 bool half(const md_system* s) { return s->list_kind == MD_LIST_HALF_COLOUR8; }
 // md_step runs the full-list mixed path with velocity Verlet fused into the force kernel
-bool fused(const md_system* s) { return mixed(s) && !half(s) && !s->no_fuse; }
-// kernels per force evaluation: 8 colour launches (half lists), else one
-int force_kernels(const md_system* s) { return half(s) ? 8 : 1; }
+bool fused(const md_system* s) { return mixed(s) && !half(s) && !s->no_fuse && s->potential == 0; }
+// kernels per force evaluation: 8 colour launches (half lists), two passes (TB-SMA), else one
+int force_kernels(const md_system* s) { return half(s) ? 8 : (s->potential == 1 ? 2 : 1); }
 
 // The state with its positions (FP32 cell-relative and FP64) in buffer p (0: st[0],
 // 1: xr_alt and pos_alt).  Fused steps read one buffer and write the other; outside
@@ -335,7 +338,8 @@ int do_build(md_system* s, int p = 0) {
 
 void enqueue_forces(md_system* s, int with_energy, cudaStream_t st) {
     const DevState& a = s->st[0];
-    if (mixed(s)) launch_forces_mixed(a, s->g, s->pt, s->to, s->tile_cap, half(s), with_energy, st);
+    if (s->potential == 1) launch_tbsma(a, s->g, s->tb, s->to, s->tile_cap, s->emb, with_energy, st);
+    else if (mixed(s)) launch_forces_mixed(a, s->g, s->pt, s->to, s->tile_cap, half(s), with_energy, st);
     else launch_forces_fp64(a, s->g, s->pt, s->tile_cap, half(s), with_energy, st);
 }
 
@@ -347,7 +351,11 @@ int do_forces(md_system* s, int with_energy) {
         ev = take_events(s);
         CK(cudaEventRecord(ev.first, s->stream));
     }
-    if (mixed(s)) {
+    if (s->potential == 1) {
+        if (tbsma_smem_bytes(s->tile_cap) > 226 * 1024)
+            return fail(s, MD_ERR_CELL_OVERFLOW, "tile of %d atoms exceeds shared memory", s->tile_cap);
+        launch_tbsma(a, s->g, s->tb, s->to, s->tile_cap, s->emb, with_energy, s->stream);
+    } else if (mixed(s)) {
         if (force_smem_bytes(1, half(s), with_energy, s->tile_cap) > 226 * 1024)
             return fail(s, MD_ERR_CELL_OVERFLOW, "tile of %d atoms exceeds shared memory", s->tile_cap);
         launch_forces_mixed(a, s->g, s->pt, s->to, s->tile_cap, half(s), with_energy, s->stream);
@@ -808,6 +816,7 @@ int md_create(int64_t n, const double box[3], double r_cut, double skin, const m
     init_force_kernels();
     init_list_kernels();
     init_grad_kernels();
+    init_tbsma_kernels();
     {
         const char* ng = std::getenv("MDGB_NO_GRAPHS");
         s->use_graphs = !(ng && ng[0] && ng[0] != '0');
@@ -1100,6 +1109,42 @@ int md_set_params(md_system* s, const double* eps, const double* sigma, const do
     // kernels read the table by value: queued work keeps the old one, captured graphs are redone
     fill_pair_table(s->pt, eps, sigma, rcut, s->rcut_default);
     set_cut_band(s);
+    s->potential = 0;
+    s->forces_valid = false;
+    s->graphs_valid = false;
+    return MD_OK;
+}
+
+int md_set_tbsma(md_system* s, double A, double xi, double p, double q, double r0, double r_cut) {
+    if (!s) return MD_ERR_ARG;
+    const double v[6] = {A, xi, p, q, r0, r_cut};
+    for (double x : v)
+        if (!std::isfinite(x) || !(x > 0.0)) return fail(s, MD_ERR_ARG, "TB-SMA parameters must be positive");
+    if (!mixed(s) || half(s) || s->pt.nsp != 1)
+        return fail(s, MD_ERR_ARG, "TB-SMA needs one species, MD_MIXED and MD_LIST_FULL");
+    if (r_cut > s->rcut) return fail(s, MD_ERR_ARG, "cutoff %g exceeds the %g the lists were sized for", r_cut, s->rcut);
+    // the density terms go through the fixed-point split: psi(0) = xi^2 exp(2q) must stay below 2048
+    if (!(xi * xi * std::exp(2.0 * q) < 2000.0)) return fail(s, MD_ERR_ARG, "xi^2 exp(2q) must be below 2000");
+    DeviceGuard dg(s->device);
+    if (!s->emb) {
+        int rc = dalloc(s, &s->emb, (size_t)std::max<int64_t>(s->n, 1));
+        if (rc) return rc;
+    }
+    const double ln2 = std::log(2.0);
+    TBTable& tb = s->tb;
+    tb.r0 = (float)r0;
+    tb.kp = (float)(-p / (r0 * ln2));
+    tb.lp = (float)std::log2(A);
+    tb.kq = (float)(-2.0 * q / (r0 * ln2));
+    tb.lq = (float)(2.0 * std::log2(xi));
+    tb.c_rep = (float)(2.0 * p / r0);
+    tb.c_band = (float)(q / r0);
+    tb.rc2_d = r_cut * r_cut;
+    const double wmax = std::max(s->g.w[0], std::max(s->g.w[1], s->g.w[2]));
+    const double band = tile_frame_cut_band(wmax, 0.5 * s->skin, r_cut);
+    tb.rc2lo_f = (float)(r_cut * r_cut * (1.0 - band));
+    tb.rc2hi_f = (float)(r_cut * r_cut * (1.0 + band));
+    s->potential = 1;
     s->forces_valid = false;
     s->graphs_valid = false;
     return MD_OK;
@@ -1112,6 +1157,7 @@ static int backward(md_system* s, const double* grad_f, int device_ptrs, double*
     DeviceGuard dg(s->device);
     if (!s->has_state) return fail(s, MD_ERR_STATE, "no state: call md_set_state first");
     if (half(s)) return fail(s, MD_ERR_ARG, "derivatives need full neighbour lists (MD_LIST_FULL)");
+    if (s->potential != 0) return fail(s, MD_ERR_ARG, "derivatives are for the Lennard-Jones potential");
     const int ns = s->pt.nsp;
     const int ncol = ns * ns * 4;
     std::vector<double> tot(ncol, 0.0);

@@ -1,0 +1,112 @@
+// fixpt.cuh - Q31.32 fixed-point force sums and neighbour-list traversal shared by the
+// mixed-precision force kernels.
+//
+// Every pair force component q = rint(f * 2^32) is added through an exact split into a
+// high part (multiples of 2^-11, rounded by adding a "magic" 1.5 * 2^23 in an FMA) and the
+// exact remainder (units of 2^-32), each summed in a 32-bit integer.  Integer sums do not
+// depend on order, so a force is the same whatever order its pairs are visited in.
+#pragma once
+
+#include "mdgb_internal.cuh"
+
+namespace mdgb {
+
+constexpr float MAGIC = 12582912.0f;   // 1.5 * 2^23: adding it rounds |a| < 2^22 to an integer
+constexpr float TWO21 = 2097152.0f;    // 2^21
+constexpr float FS_SCALE = 2048.0f;    // 2^11: pair force scaled so that rint() yields multiples of 2^-11
+
+// Exact split of a * 2^21 (a = fs2 * d computed exactly inside the FMA) into
+// two integer parts: hi counts units of 2^-11, lo units of 2^-32 (both offset
+// by the bit pattern of MAGIC, which the caller removes once per term).
+struct FixAcc {
+    unsigned hi, lo;  // wrap-around sums; the true sums fit in 32 bits
+};
+
+__device__ __forceinline__ void fix_add(FixAcc& acc, float fs2, float d) {
+    float t1 = __fmaf_rn(fs2, d, MAGIC);
+    float h = __fsub_rn(t1, MAGIC);
+    float r = __fmaf_rn(fs2, d, -h);
+    float t2 = __fmaf_rn(r, TWO21, MAGIC);
+    acc.hi += __float_as_uint(t1);
+    acc.lo += __float_as_uint(t2);
+}
+
+__device__ __forceinline__ void fix_sub(FixAcc& acc, float fs2, float d) {
+    // contribution of -d: exact negation of fix_add's terms
+    float t1 = __fmaf_rn(fs2, -d, MAGIC);
+    float h = __fsub_rn(t1, MAGIC);
+    float r = __fmaf_rn(fs2, -d, -h);
+    float t2 = __fmaf_rn(r, TWO21, MAGIC);
+    acc.hi += __float_as_uint(t1);
+    acc.lo += __float_as_uint(t2);
+}
+
+// slow exact path for |fs2 * d| >= 2^22 (pair force component >= 2048 eps/sigma): add
+// rint(fs2 * d * 2^21) in the same two-part form (FP64 product of two floats is exact).
+static __device__ __noinline__ uint2 fix_wide_terms(float fs2, float d, uint32_t* err) {
+    double a = (double)fs2 * (double)d * 2097152.0;
+    if (!(fabs(a) < 9.0e15)) {
+        atomicOr(err, ERR_NONFINITE);
+        a = 0.0;
+    }
+    long long q = __double2ll_rn(a);
+    long long qh = q >> 21;
+    return make_uint2(__float_as_uint(MAGIC) + (unsigned)(int)qh,
+                      __float_as_uint(MAGIC) + (unsigned)(int)(q - qh * 2097152LL));
+}
+
+__device__ __forceinline__ void fix_add_wide(FixAcc& acc, float fs2, float d, uint32_t* err) {
+    const uint2 t = fix_wide_terms(fs2, d, err);
+    acc.hi += t.x;
+    acc.lo += t.y;
+}
+
+__device__ __forceinline__ long long fix_final(const FixAcc& acc, int nterms) {
+    const int hi = (int)(acc.hi - (unsigned)nterms * __float_as_uint(MAGIC));
+    const int lo = (int)(acc.lo - (unsigned)nterms * __float_as_uint(MAGIC));
+    return (long long)hi * 2097152LL + (long long)lo;
+}
+
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// Chunks 0, 1, ... nch-1 of one list, chunk c at lp[c * stride] (stride in uint4 units),
+// two entries per call of body; the next chunk is loaded while this one is used.
+template <typename Body>
+__device__ __forceinline__ void for_each_neighbour_pair(const uint4* __restrict__ lp, size_t stride, int nch,
+                                                        Body&& body) {
+    uint4 cur = make_uint4(0u, 0u, 0u, 0u);
+    if (nch > 0) cur = __ldcs(lp);
+    for (int c = 0; c < nch; ++c) {
+        uint4 nxt = cur;
+        if (c + 1 < nch) nxt = __ldcs(lp + (size_t)(c + 1) * stride);
+        body((int)(cur.x & 0xffffu), (int)(cur.x >> 16));
+        body((int)(cur.y & 0xffffu), (int)(cur.y >> 16));
+        body((int)(cur.z & 0xffffu), (int)(cur.z >> 16));
+        body((int)(cur.w & 0xffffu), (int)(cur.w >> 16));
+        cur = nxt;
+    }
+}
+
+template <typename Body>
+__device__ __forceinline__ void for_each_neighbour(const uint4* __restrict__ lp, size_t stride, int nch,
+                                                   Body&& body) {
+    for_each_neighbour_pair(lp, stride, nch, [&](int u0, int u1) {
+        body(u0);
+        body(u1);
+    });
+}
+
+// One tile entry with a single 128-bit shared-memory load (base = shared address of the tile).
+__device__ __forceinline__ float4 lds_tile(unsigned base, int u) {
+    float4 v;
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "r"(base + ((unsigned)u << 4)));
+    return v;
+}
+
+}  // namespace mdgb

@@ -63,6 +63,18 @@ inline void set_band_thresholds(PairTable& pt) {
     }
 }
 
+// Tight-binding second-moment potential (Cleri and Rosato 1993; the potential of the
+// paper's benchmarks, Sec. III), one species, mixed path.  With dr = r - r0:
+//   phi(r) = A exp(-p (r/r0 - 1)) = 2^(kp dr + lp),  psi(r) = xi^2 exp(-2q (r/r0 - 1)) = 2^(kq dr + lq)
+// E = sum_i [sum_j phi(r_ij) - sqrt(rho_i)], rho_i = sum_j psi(r_ij), and the force of pair
+// (i,j) on i along d / r is c_rep phi - c_band psi (1/sqrt(rho_i) + 1/sqrt(rho_j)).
+struct TBTable {
+    float r0, kp, lp, kq, lq;  // FP32 forms of the two exponentials
+    float c_rep, c_band;       // 2 p / r0, q / r0
+    float rc2lo_f, rc2hi_f;    // the FP64 decision band around r_cut^2
+    double rc2_d;              // r_cut^2
+};
+
 // ---- the FP64 decision band around r_cut^2 (host)
 // Half an FP32 ulp of the numbers of magnitude up to v > 0: 2^(floor(log2 v) - 24).
 inline double f32_half_ulp(double v) {
@@ -208,6 +220,13 @@ struct StepOut {
 void launch_forces_mixed_fused(const DevState& s, const Geometry& g, const PairTable& pt, const TileOffsets& to,
                                int tile_cap, int mode, StepOut out, double dt, double lim2, cudaStream_t st);
 enum { FUSE_KICK = 1, FUSE_KICK_KICK_DRIFT = 2 };  // modes of launch_forces_mixed_fused
+// TB-SMA forces (full lists, mixed): the density pass writes emb[i] = 1/sqrt(rho_i) (0 for an
+// atom without neighbours), the force pass the Q31.32 forces; with_energy also writes the
+// per-atom energies and virial shares.  Two launches.
+void launch_tbsma(const DevState& s, const Geometry& g, const TBTable& tb, const TileOffsets& to, int tile_cap,
+                  float* emb, int with_energy, cudaStream_t st);
+size_t tbsma_smem_bytes(int tile_cap);
+void init_tbsma_kernels();
 void launch_forces_fp64(const DevState& s, const Geometry& g, const PairTable& pt, int tile_cap, int half,
                         int with_energy, cudaStream_t st);
 void launch_integrate(const DevState& s, const Geometry& g, const PairTable& pt, int mode, int mixed,

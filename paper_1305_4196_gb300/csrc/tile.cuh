@@ -180,6 +180,17 @@ __device__ __forceinline__ void tile_stage_f32_cells(const TileMeta& m, const fl
     }
 }
 
+// One FP32 value per tile atom into the .w of its tile entry (a single-species tile does
+// not need the species there), one warp per tile cell.
+__device__ __forceinline__ void tile_stage_w(const TileMeta& m, const float* __restrict__ v,
+                                             float4* __restrict__ tile) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int slot = warp; slot < 64; slot += nw) {
+        const int u0 = m.prefix[slot], cnt = m.prefix[slot + 1] - u0, j0 = m.start[slot];
+        for (int e = lane; e < cnt; e += 32) tile[u0 + e].w = v[j0 + e];
+    }
+}
+
 // Stage the block-frame FP32 coordinates of the tile (T = m.prefix[64] <= cap).
 __device__ __forceinline__ void tile_stage_f32(const TileMeta& m, const float4* __restrict__ xr,
                                                const TileOffsets& to, float4* __restrict__ tile,

@@ -40,7 +40,7 @@ MD_REBUILD_EVERY_K = 1
 EXPORTED = ["md_create", "md_set_state", "md_bin_cells", "md_build_neighbors", "md_forces", "md_step",
             "md_energy_virial", "md_get_state", "md_get_neighbors", "md_get_cells", "md_get_info",
             "md_set_timing", "md_last_error", "md_destroy", "md_kinetic_energy_noalloc", "md_set_params",
-            "md_forces_backward", "md_energy_param_grad"]
+            "md_forces_backward", "md_energy_param_grad", "md_set_tbsma"]
 
 
 class md_params(C.Structure):
@@ -91,6 +91,7 @@ def _load():
     lib.md_set_params.argtypes = [P, P, P, P]
     lib.md_forces_backward.argtypes = [P, P, C.c_int, P, P, P]
     lib.md_energy_param_grad.argtypes = [P, P, P]
+    lib.md_set_tbsma.argtypes = [P] + [C.c_double] * 6
     lib.md_last_error.argtypes = [P, C.c_char_p, C.c_int64]
     lib.md_destroy.argtypes = [P]
     lib.md_destroy.restype = None
@@ -234,6 +235,10 @@ def md_set_params(handle, eps, sigma, rcut=None):
                                       rc.ctypes.data if rc is not None else None))
 
 
+def md_set_tbsma(handle, A, xi, p, q, r0, r_cut):
+    _check(handle, _lib.md_set_tbsma(handle, float(A), float(xi), float(p), float(q), float(r0), float(r_cut)))
+
+
 def md_forces_backward(handle, grad_f, grad_pos, nsp):
     """dL/dx into grad_pos (same kind of array as grad_f: numpy or CUDA tensor, N x 3) and
     (dL/deps, dL/dsigma) returned as nsp x nsp numpy tables."""
@@ -317,6 +322,10 @@ class System:
 
     def set_params(self, eps, sigma, rcut=None):
         md_set_params(self.handle, eps, sigma, rcut)
+
+    def set_tbsma(self, A, xi, p, q, r0, r_cut):
+        """Cleri-Rosato tight-binding second-moment many-body potential (md_set_tbsma)."""
+        md_set_tbsma(self.handle, A, xi, p, q, r0, r_cut)
 
     def forces_backward(self, grad_f, grad_pos=None):
         """(dL/dx, dL/deps, dL/dsigma) for dL/dF = grad_f (see md_forces_backward)."""

@@ -14,7 +14,8 @@ same bits on every machine and numpy version.
 The workloads mirror the paper's benchmark shapes (Sec. III: a homogeneous
 fcc bulk crystal of about 1e6 atoms, and strongly inhomogeneous systems - a
 nanoparticle in vacuum, porous sintered particles), with a Lennard-Jones
-fluid in place of the paper's copper potential.
+fluid, and the paper's copper crystal with Cleri and Rosato's published
+parameters of its many-body potential.
 """
 from __future__ import annotations
 
@@ -260,6 +261,15 @@ def fcc_vacancies(n: int, rho: float, T: float, seed: int, jitter: float = 0.05,
     masses = np.ones(n)
     vel = thermal_velocities(masses, T, seed, stream=1)
     return System(pos, vel, np.zeros(n, dtype=np.int32), box, name or f"fcc_vacancies_{n}")
+
+
+def copper_tbsma() -> dict:
+    """Cleri and Rosato's published tight-binding second-moment parameters for copper
+    (A, xi in eV; p, q; r0 the fcc nearest-neighbour distance at a = 3.615 A), the cutoff
+    halfway between the fifth and sixth fcc shells (A), and the mass (amu)."""
+    r0 = 3.615 / math.sqrt(2.0)
+    return dict(A=0.0855, xi=1.224, p=10.960, q=2.278, r0=r0, rc=0.5 * (math.sqrt(5.0) + math.sqrt(6.0)) * r0,
+                mass=63.546)
 
 
 def batch_ensemble(n_systems: int = 512, seed: int = 4, n_min: int = 256, n_max: int = 32768,
