@@ -355,7 +355,9 @@ def run_ours(args):
 
     extras = {}
     if not args.no_extras and rank == 0 and world == 1:
-        extras = comparisons(args, sysm, M, stream, value, info1["list_entries"] / sysm.n)
+        extras = comparisons(args, sysm, M, stream, value, info1["list_entries"] / sysm.n,
+                             hom={"force_ns_per_atom": f_ms * 1e6 / sysm.n, "build_ns_per_atom": build_ms * 1e6 / sysm.n,
+                                  "rebuilds_per_timestep": (info1["n_builds"] - info0["n_builds"]) / timesteps})
 
     s.close()
     if rank == 0:
@@ -374,7 +376,7 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def comparisons(args, sysm, M, stream, value, list_len_hom):
+def comparisons(args, sysm, M, stream, value, list_len_hom, hom=None):
     """Same workload on the FP64 GPU path and on the 8-colour half-list path (short runs), and
     the per-atom cost of the strongly inhomogeneous workload next to this one."""
     import torch
@@ -389,6 +391,7 @@ def comparisons(args, sysm, M, stream, value, list_len_hom):
         s.set_state(inh.pos, inh.vel, inh.species)
         s.forces()
         torch.cuda.synchronize()
+        s.set_timing(True)  # as in the homogeneous run: events around every force launch
         info0 = s.info()
         steps_inh = 500
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -399,8 +402,18 @@ def comparisons(args, sysm, M, stream, value, list_len_hom):
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1)
         info1 = s.info()
+        s.set_timing(False)
         ns_inh = ms * 1e6 / (inh.n * steps_inh)
         ns_hom = 1e9 / value
+        f_ms_inh = (info1["force_ms"] - info0["force_ms"]) / max(info1["timed_force_evals"] - info0["timed_force_evals"], 1)
+        s.set_timing(True)
+        b0 = s.info()
+        for _ in range(3):
+            s.build_neighbors()
+        torch.cuda.synchronize()
+        b1 = s.info()
+        s.set_timing(False)
+        build_ms_inh = (b1["build_ms"] - b0["build_ms"]) / max(b1["timed_builds"] - b0["timed_builds"], 1)
         out["inhomogeneous"] = {"workload": "slab_nanoparticles_1192114", "atoms": inh.n,
                                 "box_sigma": float(inh.box[0]), "timesteps": steps_inh,
                                 "value": inh.n * steps_inh / (ms * 1e-3), "unit": METRIC,
@@ -409,7 +422,10 @@ def comparisons(args, sysm, M, stream, value, list_len_hom):
                                 "redos": info1["n_redos"] - info0["n_redos"],
                                 "mean_list_length_end": info1["list_entries"] / inh.n,
                                 "mean_list_length_homogeneous": list_len_hom,
-                                "per_atom_cost_vs_homogeneous": ns_inh / ns_hom}
+                                "per_atom_cost_vs_homogeneous": ns_inh / ns_hom,
+                                "force_ns_per_atom": f_ms_inh * 1e6 / inh.n,
+                                "build_ns_per_atom": build_ms_inh * 1e6 / inh.n,
+                                "homogeneous": hom}
         s.close()
     out["force_matching"] = force_matching_timing(M, stream)
     out["batch_ensemble"] = batch_ensemble_timing(stream)
