@@ -217,6 +217,20 @@ def algorithmic_fused_bytes(n, entries):
     return n * (16 + 4 + 96 + 24) + 4 * entries
 
 
+def job_time_and_value(ms, atoms_per_rank, timesteps, world, device):
+    """The slowest rank's time in ms (every rank must call this) and the whole-job
+    throughput in atom-timesteps/s: each rank advances its own replica of the workload,
+    so the job processed world * atoms * timesteps units in that time."""
+    t_max = ms
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([ms], device=device, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    return t_max, world * atoms_per_rank * timesteps / (t_max * 1e-3)
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -267,13 +281,8 @@ def run_ours(args):
     ms = e0.elapsed_time(e1)
     info1 = s.info()
     s.set_timing(False)
-    t_max = ms
-    if world > 1:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
     timesteps = args.steps * args.inner
-    value = world * sysm.n * timesteps / (t_max * 1e-3)
+    t_max, value = job_time_and_value(ms, sysm.n, timesteps, world, "cuda")
     launches = info1["kernel_launches"] - info0["kernel_launches"]
 
     # roofline of the dominant kernel (the force evaluation; on the full-list mixed path the
@@ -345,12 +354,9 @@ def run_ours(args):
             M.md_get_state(s.handle, pos_h, vel_h, img_h)
             s.energy_virial()
         torch.cuda.synchronize()
-        t_e2e = time.perf_counter() - t0
-        if world > 1:
-            t = torch.tensor([t_e2e], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            t_e2e = float(t.item())
-        e2e = {"value": world * sysm.n * args.inner * args.e2e_steps / t_e2e, "unit": METRIC,
+        _, e2e_value = job_time_and_value(1e3 * (time.perf_counter() - t0), sysm.n, args.inner * args.e2e_steps,
+                                          world, "cuda")
+        e2e = {"value": e2e_value, "unit": METRIC,
                "h2d_bytes_per_step": sysm.n * (24 + 24 + 4), "d2h_bytes_per_step": sysm.n * (24 + 24 + 12) + 64}
 
     extras = {}

@@ -44,7 +44,10 @@ __global__ void k_bin_assign(DevState s, Geometry g, int32_t* __restrict__ atom_
     if (bad) atomicOr(s.err, bad);
     int id = cell_id_of(g, c[0], c[1], c[2]);
     atom_cell[i] = id;
-    atomicAdd(&cell_count[id], 1);
+    // atoms arrive in the previous cell order: most of a warp shares a cell, so one
+    // atomic per cell and warp instead of one per atom
+    const unsigned peers = __match_any_sync(__activemask(), id);
+    if ((int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&cell_count[id], __popc(peers));
 }
 
 void launch_bin_assign(const DevState& s, const Geometry& g, int32_t* atom_cell, int32_t* cell_count,
@@ -152,7 +155,14 @@ __global__ void k_scatter(DevState s, const int32_t* __restrict__ atom_cell,
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= s.n) return;
     int c = atom_cell[i];
-    int slot = cell_start[c] + atomicAdd(&cursor[c], 1);
+    // one atomic per cell and warp; the order within a cell is set by k_cell_sort
+    const unsigned act = __activemask();
+    const unsigned peers = __match_any_sync(act, c);
+    const int lane = (int)(threadIdx.x & 31), leader = __ffs(peers) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(&cursor[c], __popc(peers));
+    base = __shfl_sync(act, base, leader);
+    int slot = cell_start[c] + base + __popc(peers & ((1u << lane) - 1u));
     slot_key[slot] = s.orig[i];
     slot_src[slot] = (int32_t)i;
 }
