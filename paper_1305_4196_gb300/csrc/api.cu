@@ -58,6 +58,9 @@ struct md_system {
     // full-list mixed path: force kernel fused with velocity Verlet, FP32 coordinates
     // double-buffered; g_fused[closing kick only / kick-kick-drift][buffer read]
     StepGraph g_fused[2][2];
+    // MULTI_STEPS kick-kick-drift steps from buffer 0 in one graph (even: back in buffer 0),
+    // for md_step calls without timing events: fewer graph launches per step
+    StepGraph g_multi;
     float4* xr_alt = nullptr;
     int potential = 0;       // 0: Lennard-Jones pair table; 1: TB-SMA many-body (md_set_tbsma)
     TBTable tb{};
@@ -565,6 +568,59 @@ int capture_fused(md_system* s, bool kkd, int p, md_system::StepGraph& out) {
     return MD_OK;
 }
 
+// MULTI_STEPS fused kick-kick-drift steps in one graph: the sequence of capture_fused,
+// step after step, each with its own conditional rebuild node and alternating buffers.
+constexpr int MULTI_STEPS = 8;
+
+int capture_fused_multi(md_system* s, md_system::StepGraph& out) {
+    destroy_graph(out);
+    cudaStream_t cs = s->cap_stream;
+    cudaGraph_t g = nullptr;
+    CK(cudaGraphCreate(&g, 0));
+    out.graph = g;
+    std::vector<cudaGraphNode_t> tail;
+    for (int j = 0; j < MULTI_STEPS; ++j) {
+        const int p = j & 1;
+        cudaGraphConditionalHandle h;
+        CK(cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault));
+        CK(cudaStreamBeginCaptureToGraph(cs, g, tail.empty() ? nullptr : tail.data(), nullptr, tail.size(),
+                                         cudaStreamCaptureModeThreadLocal));
+        const DevState a = view(s, p);
+        launch_step_ctrl(s->rebuild == MD_REBUILD_EVERY_K ? 1 : 0, s->rebuild_k, a.rebuild_flag, s->d_ctrl,
+                         s->d_ctrl + 1, a.err, h, cs);
+        cudaStreamCaptureStatus status;
+        const cudaGraphNode_t* deps = nullptr;
+        size_t ndeps = 0;
+        cudaGraph_t cg = nullptr;
+        CK(cudaStreamGetCaptureInfo(cs, &status, nullptr, &cg, &deps, nullptr, &ndeps));
+        alignas(cudaGraphNodeParams) unsigned char cp_raw[sizeof(cudaGraphNodeParams)];
+        std::memset(cp_raw, 0, sizeof(cp_raw));  // all reserved bytes must be zero
+        cudaGraphNodeParams& cp = *reinterpret_cast<cudaGraphNodeParams*>(cp_raw);
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = h;
+        cp.conditional.type = cudaGraphCondTypeIf;
+        cp.conditional.size = 1;
+        cudaGraphNode_t cnode;
+        CK(cudaGraphAddNode(&cnode, cg, deps, nullptr, ndeps, &cp));
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        CK(cudaStreamUpdateCaptureDependencies(cs, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies));
+        launch_forces_mixed_fused(a, s->g, s->pt, s->to, s->tile_cap, FUSE_KICK_KICK_DRIFT, step_out(s, 1 - p), s->dt,
+                                  s->lim2, cs);
+        CK(cudaStreamGetCaptureInfo(cs, &status, nullptr, &cg, &deps, nullptr, &ndeps));
+        tail.assign(deps, deps + ndeps);
+        CK(cudaStreamEndCapture(cs, &g));
+        CK(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+        enqueue_bin(s, a, cs);
+        cudaMemsetAsync(a.stats, 0, 4 * sizeof(int32_t), cs);
+        launch_build_lists(a, s->g, s->to, s->rl2, s->list_cap, s->tile_cap, 0, cs);
+        launch_count_build(s->d_ctrl + 1, cs);
+        CK(cudaStreamEndCapture(cs, &body));
+    }
+    CKL();
+    CK(cudaGraphInstantiate(&out.exec, g, 0));
+    return MD_OK;
+}
+
 int ensure_graphs(md_system* s) {
     if (s->graphs_valid && s->graph_tile_cap == s->tile_cap && s->graph_list_cap == s->list_cap &&
         s->graph_timing == s->timing)
@@ -574,6 +630,7 @@ int ensure_graphs(md_system* s) {
         for (int k = 0; k < 2; ++k)
             for (int p = 0; p < 2; ++p)
                 if ((rc = capture_fused(s, k == 1, p, s->g_fused[k][p]))) return rc;
+        if (!s->timing && (rc = capture_fused_multi(s, s->g_multi))) return rc;
     } else {
         if ((rc = capture_step(s, INT_KICK_DRIFT, s->g_first))) return rc;
         if ((rc = capture_step(s, INT_KICK_KICK_DRIFT, s->g_mid))) return rc;
@@ -679,7 +736,15 @@ int run_chunk_fused(md_system* s, int len, bool first, bool last) {
         s->launches += 1;
     }
     int p = 0;
+    const int n_kkd = last ? len - 1 : len;  // steps that end with the next opening kick and drift
     for (int k = 0; k < len; ++k) {
+        if (!s->timing && s->g_multi.exec && p == 0 && k + MULTI_STEPS <= n_kkd) {
+            CK(cudaGraphLaunch(s->g_multi.exec, s->stream));  // MULTI_STEPS steps; back in buffer 0
+            s->launches += 2 * MULTI_STEPS;
+            s->force_evals += MULTI_STEPS;
+            k += MULTI_STEPS - 1;
+            continue;
+        }
         const bool kkd = !(last && k == len - 1);
         md_system::StepGraph& gr = s->g_fused[kkd ? 1 : 0][p];
         if (s->timing && gr.ev_a && gr.ev_b) {
@@ -1381,6 +1446,7 @@ void md_destroy(md_system* s) {
     destroy_graph(s->g_mid);
     for (auto& row : s->g_fused)
         for (auto& gr : row) destroy_graph(gr);
+    destroy_graph(s->g_multi);
     if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
     if (prev >= 0 && prev != s->device) cudaSetDevice(prev);
     delete s;

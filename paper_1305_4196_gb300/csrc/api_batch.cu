@@ -38,6 +38,8 @@ struct md_batch {
     int device = 0;
     cudaStream_t stream = nullptr;
     cudaStream_t cap_stream = nullptr;  // capture only records; the legacy stream cannot capture
+    cudaStream_t bucket_streams[NBUCKET] = {};  // one branch of the captured graph per size bucket
+    cudaEvent_t fork_ev = nullptr, join_ev[NBUCKET] = {};
     int nsys = 0;
     std::vector<int64_t> n, a0;
     std::vector<double> box;  // 3 per system
@@ -171,8 +173,19 @@ int run_buckets(md_batch* b, int n_steps, int flags) {
         if (b->gexec) cudaGraphExecDestroy(b->gexec);
         b->gexec = nullptr;
         cudaGraph_t g = nullptr;
+        // the buckets touch disjoint systems: one parallel branch each, so that they share the
+        // GPU instead of running one after another
         BCK(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
-        enqueue_buckets(b, n_steps, flags, b->cap_stream);
+        BCK(cudaEventRecord(b->fork_ev, b->cap_stream));
+        for (int k = 0; k < NBUCKET; ++k) {
+            md_batch::Bucket& B = b->bk[k];
+            if (B.ids.empty()) continue;
+            BCK(cudaStreamWaitEvent(b->bucket_streams[k], b->fork_ev, 0));
+            launch_batch_run(B.d_sys, (int)B.ids.size(), b->st, b->pt, n_steps, flags, b->dt, B.threads, B.nmax,
+                             B.cmax, b->d_pe, b->d_ke, b->pe_atom, b->bucket_streams[k]);
+            BCK(cudaEventRecord(b->join_ev[k], b->bucket_streams[k]));
+            BCK(cudaStreamWaitEvent(b->cap_stream, b->join_ev[k], 0));
+        }
         BCK(cudaStreamEndCapture(b->cap_stream, &g));
         cudaError_t e = cudaGraphInstantiate(&b->gexec, g, 0);
         cudaGraphDestroy(g);
@@ -278,6 +291,11 @@ int md_batch_create(int32_t n_systems, const int64_t* n_atoms, const double* box
     cudaGetDevice(&b->device);
     b->stream = static_cast<cudaStream_t>(p->stream);
     if (cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) != cudaSuccess) return bail(MD_ERR_CUDA);
+    if (cudaEventCreateWithFlags(&b->fork_ev, cudaEventDisableTiming) != cudaSuccess) return bail(MD_ERR_CUDA);
+    for (int k = 0; k < NBUCKET; ++k)
+        if (cudaStreamCreateWithFlags(&b->bucket_streams[k], cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&b->join_ev[k], cudaEventDisableTiming) != cudaSuccess)
+            return bail(MD_ERR_CUDA);
     b->nsys = n_systems;
     b->r_cut = r_cut;
     b->skin = skin;
@@ -324,6 +342,10 @@ int md_batch_create(int32_t n_systems, const int64_t* n_atoms, const double* box
             b->big_ids.push_back(k);
         }
     }
+    // largest systems first within a bucket: CTAs start in index order, so the longest ones
+    // are not left for the end of the launch
+    for (auto& B : b->bk)
+        std::stable_sort(B.ids.begin(), B.ids.end(), [&](int x, int y) { return b->n[x] > b->n[y]; });
     // FP64 decision band: the widest any system needs, for either cell divisor
     double band = 0.0;
     for (int k = 0; k < n_systems; ++k)
@@ -651,6 +673,11 @@ void md_batch_destroy(md_batch* b) {
     for (md_system* m : b->big) md_destroy(m);
     for (cudaStream_t s : b->big_streams) cudaStreamDestroy(s);
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    for (int k = 0; k < NBUCKET; ++k) {
+        if (b->bucket_streams[k]) cudaStreamDestroy(b->bucket_streams[k]);
+        if (b->join_ev[k]) cudaEventDestroy(b->join_ev[k]);
+    }
+    if (b->fork_ev) cudaEventDestroy(b->fork_ev);
     for (void* p : b->allocs) cudaFree(p);
     delete b;
 }
