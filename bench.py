@@ -27,6 +27,8 @@ import time
 import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
+# hardware work queues for the ensemble's many streams (read when the CUDA context starts)
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 sys.path.insert(0, ROOT)
 
 METRIC = "atom-timesteps/s"

@@ -15,6 +15,9 @@
  * concatenated in system order (system k's atoms after those of systems 0..k-1),
  * N x 3 row-major, host or device as the device_ptrs flag says; the library
  * copies in and out.  Every call returns MD_OK or a negative MD_ERR_* code.
+ * The larger systems overlap on the GPU only as far as CUDA's hardware work queues
+ * allow: set CUDA_DEVICE_MAX_CONNECTIONS=32 before the process creates its CUDA
+ * context (the default, 8, serialises most of the 100+ streams of a large ensemble).
  * No counterpart in the paper beyond the replica remark above.
  */
 #ifndef MDGB_BATCH_H

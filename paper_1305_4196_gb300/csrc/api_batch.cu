@@ -249,7 +249,8 @@ template <typename F>
 int for_big(md_batch* b, F&& f) {
     const int m = (int)b->big.size();
     if (m == 0) return MD_OK;
-    const int nt = std::min(m, 8);
+    // one host thread per core: each waits on its system's steps in turn
+    const int nt = std::min(m, std::max(8, (int)std::thread::hardware_concurrency()));
     std::vector<int> rc(nt, MD_OK);
     std::vector<std::thread> th;
     for (int t = 0; t < nt; ++t)
