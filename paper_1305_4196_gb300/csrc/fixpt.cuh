@@ -109,4 +109,51 @@ __device__ __forceinline__ float4 lds_tile(unsigned base, int u) {
     return v;
 }
 
+// ---------------------------------------------------------------- packed FP32x2 helpers
+// sm_100-family packed single-precision arithmetic: two IEEE FP32 operations per
+// instruction, each rounded exactly as its scalar counterpart.
+typedef unsigned long long f2_t;
+
+__device__ __forceinline__ f2_t f2_pack(float a, float b) {
+    f2_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void f2_unpack(f2_t v, float& a, float& b) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ f2_t f2_add(f2_t a, f2_t b) {
+    f2_t r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2_t f2_sub(f2_t a, f2_t b) {
+    f2_t r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2_t f2_mul(f2_t a, f2_t b) {
+    f2_t r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2_t f2_fma(f2_t a, f2_t b, f2_t c) {
+    f2_t r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+
+// Two pairs' fixed-point terms of one component, packed: the same operations as fix_add.
+__device__ __forceinline__ void fix_add2(FixAcc& acc, f2_t fs2, f2_t d, f2_t magic2, f2_t two21) {
+    const f2_t t1 = f2_fma(fs2, d, magic2);
+    const f2_t nh = f2_sub(magic2, t1);  // -h, exact
+    const f2_t r = f2_fma(fs2, d, nh);
+    const f2_t t2 = f2_fma(r, two21, magic2);
+    float t1a, t1b, t2a, t2b;
+    f2_unpack(t1, t1a, t1b);
+    f2_unpack(t2, t2a, t2b);
+    acc.hi += __float_as_uint(t1a) + __float_as_uint(t1b);
+    acc.lo += __float_as_uint(t2a) + __float_as_uint(t2b);
+}
+
 }  // namespace mdgb

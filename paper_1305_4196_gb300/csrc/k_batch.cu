@@ -9,61 +9,23 @@
 // between CTAs at all.  Per step the CTA
 //   * re-bins its atoms into cells at least r_cut / R wide (counting sort in shared
 //     memory; atoms of a cell kept in index order),
-//   * evaluates the cutoff LJ force on every atom over the (2R+1)^3 surrounding cells
-//     (FP32 pair arithmetic on cell-relative coordinates, every pair force component
-//     added as rint(f * 2^32) through the same exact two-part integer split as the
-//     main path, so forces do not depend on summation order),
+//   * evaluates the cutoff LJ force on every atom over the (2R+1)^3 surrounding cells:
+//     two candidates per step in packed FP32x2 arithmetic on cell-relative coordinates
+//     (structure-of-arrays copies in shared memory, so one 64-bit load brings a pair),
+//     with no branches, every pair force component added as rint(f * 2^32) through
+//     the main path's exact two-part integer split (forces do not depend on order);
+//     an atom with a pair in the FP64 cutoff band or a force beyond the split's range
+//     is finished after the loop by an exact scalar pass,
 //   * and integrates velocity Verlet in FP64.
 // There is no neighbour list: the cells are rebuilt every step, which for systems of
 // this size costs less than a list build would.
+#include "fixpt.cuh"
 #include "mdgb_batch_internal.cuh"
 #include "tile.cuh"
 
 namespace mdgb {
 
 namespace {
-
-constexpr float BMAGIC = 12582912.0f;  // 1.5 * 2^23
-constexpr float BTWO21 = 2097152.0f;   // 2^21
-
-struct Fix2 {
-    unsigned hi, lo;
-};
-
-// add rint(a * 2^21) in units of 2^-32 for a = fs2 * d (|a| < 2^22): exact two-part split
-__device__ __forceinline__ void bfix_add(Fix2& acc, float fs2, float d) {
-    const float t1 = __fmaf_rn(fs2, d, BMAGIC);
-    const float h = __fsub_rn(t1, BMAGIC);
-    const float r = __fmaf_rn(fs2, d, -h);
-    const float t2 = __fmaf_rn(r, BTWO21, BMAGIC);
-    acc.hi += __float_as_uint(t1);
-    acc.lo += __float_as_uint(t2);
-}
-
-// the same sum for |fs2 * d| >= 2^22 (or non-finite): FP64 rounding, same two-part form
-__device__ __noinline__ uint2 bfix_wide(float fs2, float d, uint32_t* err) {
-    double a = (double)fs2 * (double)d * 2097152.0;
-    if (!(fabs(a) < 9.0e15)) {
-        atomicOr(err, ERR_NONFINITE);
-        a = 0.0;
-    }
-    const long long q = __double2ll_rn(a);
-    const long long qh = q >> 21;
-    return make_uint2(__float_as_uint(BMAGIC) + (unsigned)(int)qh,
-                      __float_as_uint(BMAGIC) + (unsigned)(int)(q - qh * 2097152LL));
-}
-
-__device__ __forceinline__ long long bfix_final(const Fix2& a, int nterms) {
-    const int hi = (int)(a.hi - (unsigned)nterms * __float_as_uint(BMAGIC));
-    const int lo = (int)(a.lo - (unsigned)nterms * __float_as_uint(BMAGIC));
-    return (long long)hi * 2097152LL + (long long)lo;
-}
-
-__device__ __forceinline__ float brcp(float x) {
-    float r;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-    return r;
-}
 
 // block-wide exclusive scan of cnt[0..m) into start[0..m], start[m] = total
 __device__ void block_scan(const int* __restrict__ cnt, int* __restrict__ start, int m, int* warp_tot) {
@@ -100,12 +62,15 @@ __device__ void block_scan(const int* __restrict__ cnt, int* __restrict__ start,
 }
 
 struct Smem {
-    float4* xr;        // n: FP32 coordinates relative to the cell centre, by slot (species in w)
-    uint16_t* perm;    // n: slot -> local atom
-    uint16_t* cell;    // n: local atom -> cell, then local atom -> slot
-    int* cstart;       // ncell + 1
-    int* ccount;       // ncell
-    int* warp_tot;     // 32
+    float *px, *py, *pz;  // n + 2: FP32 coordinates relative to the cell centre, by slot (slot n: far away)
+    uint16_t* perm;       // n: slot -> local atom
+    uint16_t* cell;       // n: local atom -> cell, then local atom -> slot
+    uint16_t* scell;      // n + 2: slot -> cell
+    uint16_t* queue;      // n: slots left to the exact pass
+    int* nqueued;
+    int* cstart;          // ncell + 1
+    int* ccount;          // ncell
+    int* warp_tot;        // 32
 };
 
 // Wrap every atom into the box (one box length at most, counted in the image
@@ -163,98 +128,169 @@ __device__ void batch_bin(const BatchSys& y, BatchState st, Smem& sm) {
             int rank = 0;
             for (int f = 0; f < cnt; ++f) rank += (int)sm.perm[s0 + f] < mine;
             const int64_t g = y.a0 + mine;
-            float4 p;
-            p.x = __double2float_rn(st.x[g] - ox);
-            p.y = __double2float_rn(st.y[g] - oy);
-            p.z = __double2float_rn(st.z[g] - oz);
-            p.w = __int_as_float(st.species[g]);
-            sm.xr[s0 + rank] = p;
+            sm.px[s0 + rank] = __double2float_rn(st.x[g] - ox);
+            sm.py[s0 + rank] = __double2float_rn(st.y[g] - oy);
+            sm.pz[s0 + rank] = __double2float_rn(st.z[g] - oz);
+            sm.scell[s0 + rank] = (uint16_t)id;
             sm.cell[mine] = (uint16_t)(s0 + rank);
         }
+    }
+    if (threadIdx.x == 0) {  // slot n: read as the second of a pair at the last cell's end
+        sm.px[n] = sm.py[n] = sm.pz[n] = 1.0e4f;
+        sm.scell[n] = 0;
     }
     __syncthreads();
     for (int a = threadIdx.x; a < n; a += blockDim.x) sm.perm[sm.cell[a]] = (uint16_t)a;
     __syncthreads();
 }
 
-// Force on every atom (fixed point into st.fq); with energy, also its half pair
-// energies (FP32 per atom, neighbours in slot order: deterministic).
+// Cell coordinates of slot p's cell.
+__device__ __forceinline__ void slot_cell(const BatchSys& y, const Smem& sm, int p, int& cx, int& cy, int& cz) {
+    const int id = sm.scell[p];
+    cx = id % y.nc[0];
+    cy = (id / y.nc[0]) % y.nc[1];
+    cz = id / (y.nc[0] * y.nc[1]);
+}
+
+__device__ __forceinline__ int wrap_cell(int c, int nc) { return c < 0 ? c + nc : (c >= nc ? c - nc : c); }
+
+// Exact force on the atom of slot p, one candidate at a time: a pair whose FP32 r^2 lies in
+// the band around r_cut^2 is decided in FP64 by the definition, a large term is rounded in
+// FP64 (fix_wide_terms); every other term is the one the packed loop would add.
+template <bool ENERGY>
+__device__ __noinline__ void batch_force_exact(const BatchSys& y, const BatchState& st, const PairTable& pt,
+                                               float fs2_max, const Smem& sm, float* __restrict__ pe_out, int p) {
+    const int R = y.R;
+    const float sig2 = pt.sig2_f[0], c48 = pt.c48_f[0], c24 = pt.c24_f[0], c4 = pt.c4_f[0];
+    const int a = sm.perm[p];
+    const int64_t g = y.a0 + a;
+    int cx, cy, cz;
+    slot_cell(y, sm, p, cx, cy, cz);
+    const float xi = sm.px[p], yi = sm.py[p], zi = sm.pz[p];
+    FixAcc ax{0u, 0u}, ay{0u, 0u}, az{0u, 0u};
+    int nterms = 0;
+    float pe = 0.f;
+    for (int dz = -R; dz <= R; ++dz)
+        for (int dy = -R; dy <= R; ++dy)
+            for (int dx = -R; dx <= R; ++dx) {
+                const int id = wrap_cell(cx + dx, y.nc[0]) +
+                               y.nc[0] * (wrap_cell(cy + dy, y.nc[1]) + y.nc[1] * wrap_cell(cz + dz, y.nc[2]));
+                const float sx = (float)dx * y.wf[0], sy = (float)dy * y.wf[1], sz = (float)dz * y.wf[2];
+                const int q1 = sm.cstart[id + 1];
+                for (int q = sm.cstart[id]; q < q1; ++q) {
+                    if (q == p) continue;
+                    const float ex = xi - (sm.px[q] + sx), ey = yi - (sm.py[q] + sy), ez = zi - (sm.pz[q] + sz);
+                    const float r2 = fmaf(ez, ez, fmaf(ey, ey, ex * ex));
+                    if (!(r2 < pt.rc2hi_f[0])) continue;
+                    if (!(r2 < pt.rc2lo_f[0]) &&
+                        !fp64_pair_test(st.x, st.y, st.z, y.L[0], y.L[1], y.L[2], g, y.a0 + sm.perm[q], pt.rc2_d[0]))
+                        continue;
+                    const float inv = rcp_approx(r2);
+                    const float s2 = sig2 * inv;
+                    const float s6 = s2 * s2 * s2;
+                    const float fs2 = __fmul_rn(__fmul_rn(__fmaf_rn(c48, s6, -c24), s6), inv);  // (|f|/r) * 2^11
+                    if (fabsf(fs2) < fs2_max) {
+                        fix_add(ax, fs2, ex);
+                        fix_add(ay, fs2, ey);
+                        fix_add(az, fs2, ez);
+                    } else {
+                        fix_add_wide(ax, fs2, ex, st.err);
+                        fix_add_wide(ay, fs2, ey, st.err);
+                        fix_add_wide(az, fs2, ez, st.err);
+                    }
+                    ++nterms;
+                    if (ENERGY) pe += c4 * s6 * (s6 - 1.0f);
+                }
+            }
+    st.fq[g] = fix_final(ax, nterms);
+    st.fq[st.ntot + g] = fix_final(ay, nterms);
+    st.fq[2 * st.ntot + g] = fix_final(az, nterms);
+    if (ENERGY) pe_out[a] = 0.5f * pe;
+}
+
+// Force on every atom (fixed point into st.fq); with energy, also its half pair energies
+// (FP32 per atom, neighbours in slot order: deterministic).  Two candidates per step:
+// the pair (q, q+1) with q even, masked to the cell's range and away from the atom itself.
 template <bool ENERGY>
 __device__ void batch_forces(const BatchSys& y, BatchState st, const PairTable& pt, float fs2_max, Smem& sm,
                              float* __restrict__ pe_out) {
     const int n = y.n, R = y.R;
-    const float sig2 = pt.sig2_f[0], c48 = pt.c48_f[0], c24 = pt.c24_f[0], c4 = pt.c4_f[0];
-    const float rc2_lo = pt.rc2lo_f[0], rc2_hi = pt.rc2hi_f[0];
+    const f2_t magic2 = f2_pack(MAGIC, MAGIC), two21 = f2_pack(TWO21, TWO21);
+    const f2_t sig2 = f2_pack(pt.sig2_f[0], pt.sig2_f[0]), c48 = f2_pack(pt.c48_f[0], pt.c48_f[0]);
+    const f2_t nc24 = f2_pack(-pt.c24_f[0], -pt.c24_f[0]);
+    const float rc2_lo = pt.rc2lo_f[0], rc2_hi = pt.rc2hi_f[0], c4 = pt.c4_f[0];
+    const unsigned spx = (unsigned)__cvta_generic_to_shared(sm.px);
+    const unsigned spy = (unsigned)__cvta_generic_to_shared(sm.py);
+    const unsigned spz = (unsigned)__cvta_generic_to_shared(sm.pz);
+    if (threadIdx.x == 0) *sm.nqueued = 0;
+    __syncthreads();
     for (int p = threadIdx.x; p < n; p += blockDim.x) {
-        const int a = sm.perm[p];
-        const float4 pi = sm.xr[p];
-        // cell of slot p: find it from the cell of atom a (binary search would also do)
-        const int64_t g = y.a0 + a;
-        int cc[3];
-        {
-            const double* X[3] = {st.x, st.y, st.z};
-#pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                int v = (int)(X[d][g] * y.inv_w[d]);
-                cc[d] = v < 0 ? 0 : (v >= y.nc[d] ? y.nc[d] - 1 : v);
-            }
-        }
-        Fix2 ax{0u, 0u}, ay{0u, 0u}, az{0u, 0u};
+        int cx, cy, cz;
+        slot_cell(y, sm, p, cx, cy, cz);
+        const float xi = sm.px[p], yi = sm.py[p], zi = sm.pz[p];
+        const f2_t pix = f2_pack(xi, xi), piy = f2_pack(yi, yi), piz = f2_pack(zi, zi);
+        FixAcc ax{0u, 0u}, ay{0u, 0u}, az{0u, 0u};
         int nterms = 0;
         float pe = 0.f;
-        for (int dz = -R; dz <= R; ++dz) {
-            int z = cc[2] + dz;
-            z += z < 0 ? y.nc[2] : (z >= y.nc[2] ? -y.nc[2] : 0);
-            for (int dy = -R; dy <= R; ++dy) {
-                int yy = cc[1] + dy;
-                yy += yy < 0 ? y.nc[1] : (yy >= y.nc[1] ? -y.nc[1] : 0);
+        bool bad = false;
+        for (int dz = -R; dz <= R; ++dz)
+            for (int dy = -R; dy <= R; ++dy)
                 for (int dx = -R; dx <= R; ++dx) {
-                    int x = cc[0] + dx;
-                    x += x < 0 ? y.nc[0] : (x >= y.nc[0] ? -y.nc[0] : 0);
-                    const int id = x + y.nc[0] * (yy + y.nc[1] * z);
-                    const float sx = (float)dx * y.wf[0], sy = (float)dy * y.wf[1], sz = (float)dz * y.wf[2];
-                    const bool self_cell = (dx | dy | dz) == 0;
-                    const int q1 = sm.cstart[id + 1];
-                    for (int q = sm.cstart[id]; q < q1; ++q) {
-                        if (self_cell && q == p) continue;
-                        const float4 pj = sm.xr[q];
-                        const float ex = pi.x - (pj.x + sx), ey = pi.y - (pj.y + sy), ez = pi.z - (pj.z + sz);
-                        const float r2 = fmaf(ez, ez, fmaf(ey, ey, ex * ex));
-                        if (!(r2 < rc2_hi)) continue;
-                        if (!(r2 < rc2_lo) &&  // rare: decide the cutoff in FP64, as the definition
-                            !fp64_pair_test(st.x, st.y, st.z, y.L[0], y.L[1], y.L[2], g, y.a0 + sm.perm[q],
-                                            pt.rc2_d[0]))
-                            continue;
-                        const float inv = brcp(r2);
-                        const float s2 = sig2 * inv;
-                        const float s6 = s2 * s2 * s2;
-                        const float fs2 = (c48 * s6 - c24) * s6 * inv;  // (|f|/r) * 2^11
-                        if (fabsf(fs2) < fs2_max) {
-                            bfix_add(ax, fs2, ex);
-                            bfix_add(ay, fs2, ey);
-                            bfix_add(az, fs2, ez);
-                        } else {
-                            uint2 t = bfix_wide(fs2, ex, st.err);
-                            ax.hi += t.x;
-                            ax.lo += t.y;
-                            t = bfix_wide(fs2, ey, st.err);
-                            ay.hi += t.x;
-                            ay.lo += t.y;
-                            t = bfix_wide(fs2, ez, st.err);
-                            az.hi += t.x;
-                            az.lo += t.y;
+                    const int id = wrap_cell(cx + dx, y.nc[0]) +
+                                   y.nc[0] * (wrap_cell(cy + dy, y.nc[1]) + y.nc[1] * wrap_cell(cz + dz, y.nc[2]));
+                    const float sxf = (float)dx * y.wf[0], syf = (float)dy * y.wf[1], szf = (float)dz * y.wf[2];
+                    const f2_t sx = f2_pack(sxf, sxf), sy = f2_pack(syf, syf), sz = f2_pack(szf, szf);
+                    const int c0 = sm.cstart[id], c1 = sm.cstart[id + 1];
+                    for (int q = c0 & ~1; q < c1; q += 2) {
+                        f2_t X, Y, Z;
+                        asm volatile("ld.shared.b64 %0, [%1];" : "=l"(X) : "r"(spx + 4u * (unsigned)q));
+                        asm volatile("ld.shared.b64 %0, [%1];" : "=l"(Y) : "r"(spy + 4u * (unsigned)q));
+                        asm volatile("ld.shared.b64 %0, [%1];" : "=l"(Z) : "r"(spz + 4u * (unsigned)q));
+                        const f2_t ex = f2_sub(pix, f2_add(X, sx));
+                        const f2_t ey = f2_sub(piy, f2_add(Y, sy));
+                        const f2_t ez = f2_sub(piz, f2_add(Z, sz));
+                        const f2_t r2 = f2_fma(ez, ez, f2_fma(ey, ey, f2_mul(ex, ex)));
+                        float r2a, r2b;
+                        f2_unpack(r2, r2a, r2b);
+                        const bool ina = (q >= c0) & (q != p) & (r2a < rc2_hi);
+                        const bool inb = (q + 1 < c1) & (q + 1 != p) & (r2b < rc2_hi);
+                        const f2_t inv = f2_pack(rcp_approx(r2a), rcp_approx(r2b));
+                        const f2_t s2 = f2_mul(sig2, inv);
+                        const f2_t s6 = f2_mul(f2_mul(s2, s2), s2);
+                        const f2_t fsv = f2_mul(f2_mul(f2_fma(c48, s6, nc24), s6), inv);
+                        float fa, fb;
+                        f2_unpack(fsv, fa, fb);
+                        fa = ina ? fa : 0.0f;
+                        fb = inb ? fb : 0.0f;
+                        bad |= (ina & !(r2a < rc2_lo)) | (inb & !(r2b < rc2_lo)) | !(fabsf(fa) < fs2_max) |
+                               !(fabsf(fb) < fs2_max);
+                        const f2_t fs2 = f2_pack(fa, fb);
+                        fix_add2(ax, fs2, ex, magic2, two21);
+                        fix_add2(ay, fs2, ey, magic2, two21);
+                        fix_add2(az, fs2, ez, magic2, two21);
+                        nterms += 2;
+                        if (ENERGY) {
+                            float s6a, s6b;
+                            f2_unpack(s6, s6a, s6b);
+                            pe += (ina ? c4 * s6a * (s6a - 1.0f) : 0.0f) + (inb ? c4 * s6b * (s6b - 1.0f) : 0.0f);
                         }
-                        ++nterms;
-                        if (ENERGY) pe += c4 * s6 * (s6 - 1.0f);
                     }
                 }
-            }
+        if (bad) {  // finished by batch_force_exact after the loop
+            sm.queue[atomicAdd(sm.nqueued, 1)] = (uint16_t)p;
+            continue;
         }
-        st.fq[g] = bfix_final(ax, nterms);
-        st.fq[st.ntot + g] = bfix_final(ay, nterms);
-        st.fq[2 * st.ntot + g] = bfix_final(az, nterms);
+        const int a = sm.perm[p];
+        const int64_t g = y.a0 + a;
+        st.fq[g] = fix_final(ax, nterms);
+        st.fq[st.ntot + g] = fix_final(ay, nterms);
+        st.fq[2 * st.ntot + g] = fix_final(az, nterms);
         if (ENERGY) pe_out[a] = 0.5f * pe;
     }
+    __syncthreads();
+    const int nq = *sm.nqueued;
+    for (int k = threadIdx.x; k < nq; k += blockDim.x)
+        batch_force_exact<ENERGY>(y, st, pt, fs2_max, sm, pe_out, sm.queue[k]);
 }
 
 // v += k F (FP64, F in Q31.32); with drift also x += dt v
@@ -311,10 +347,17 @@ __global__ void __launch_bounds__(BATCH_MAX_THREADS) k_batch_run(const BatchSys*
         if (threadIdx.x == 0) atomicOr(st.err, ERR_TILE_OVERFLOW);
         return;
     }
+    __shared__ int nqueued;
     Smem sm;
-    sm.xr = reinterpret_cast<float4*>(smem);
-    sm.perm = reinterpret_cast<uint16_t*>(sm.xr + nmax);
+    const int np2 = nmax + 2;  // even: the three coordinate arrays stay 8-byte aligned
+    sm.px = reinterpret_cast<float*>(smem);
+    sm.py = sm.px + np2;
+    sm.pz = sm.py + np2;
+    sm.perm = reinterpret_cast<uint16_t*>(sm.pz + np2);
     sm.cell = sm.perm + nmax;
+    sm.scell = sm.cell + nmax;
+    sm.queue = sm.scell + np2;
+    sm.nqueued = &nqueued;
     sm.cstart = reinterpret_cast<int*>(smem + batch_smem_ints_offset(nmax));
     sm.ccount = sm.cstart + cmax + 1;
     sm.warp_tot = warp_tot;

@@ -31,8 +31,12 @@ struct BatchState {
     uint32_t* err;
 };
 
+// Shared memory of a system of at most nmax atoms (nmax a multiple of 8): three FP32
+// coordinate arrays and the slot -> cell map of nmax + 2 slots, three u16 arrays of nmax,
+// then the int arrays (cell starts and counts).
 __host__ __device__ inline size_t batch_smem_ints_offset(int nmax) {
-    return ((size_t)nmax * (16 + 2 + 2) + 15) & ~(size_t)15;
+    const size_t np2 = (size_t)nmax + 2;
+    return (np2 * (3 * 4 + 2) + (size_t)nmax * 3 * 2 + 15) & ~(size_t)15;
 }
 size_t batch_smem_bytes(int nmax, int cmax);
 void launch_batch_run(const BatchSys* sys, int nsys, const BatchState& st, const PairTable& pt, int n_steps,
