@@ -19,37 +19,12 @@
 // Full lists hold every neighbour of every atom.  Half lists (Newton's third
 // law, Sec. II.D.3) hold each pair once: a neighbour in the same cell only if
 // it comes later in cell order, plus all neighbours of the 13 "forward" cells.
+#include "fixpt.cuh"
 #include "tile.cuh"
 
 namespace mdgb {
 
 constexpr int NL_WARPS = 8;
-
-typedef unsigned long long f2_t;
-
-__device__ __forceinline__ f2_t f2_pack(float a, float b) {
-    f2_t r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
-    return r;
-}
-__device__ __forceinline__ void f2_unpack(f2_t v, float& a, float& b) {
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
-}
-__device__ __forceinline__ f2_t f2_sub(f2_t a, f2_t b) {
-    f2_t r;
-    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-    return r;
-}
-__device__ __forceinline__ f2_t f2_mul(f2_t a, f2_t b) {
-    f2_t r;
-    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-    return r;
-}
-__device__ __forceinline__ f2_t f2_fma(f2_t a, f2_t b, f2_t c) {
-    f2_t r;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
-    return r;
-}
 
 // Two packed FP32 pairs from 16 bytes of shared memory (one 128-bit load).
 __device__ __forceinline__ void lds_f2x2(unsigned addr, f2_t& lo, f2_t& hi) {
