@@ -137,3 +137,23 @@ def test_cutoff_decided_by_the_definition():
         Fref, _, _ = O.lj_forces(s.pos, s.box, P)
         assert np.abs(Fref).max() > 0.03
         assert np.abs(F - Fref).max() <= 2e-5 * np.abs(Fref).max()
+
+
+def test_full_ensemble_sampled_systems():
+    """The benchmark's ensemble itself: 512 systems, 3.6 million atoms, autotuned, 10 steps.
+    Forces of sampled systems on both paths (one CTA per system and md_system), at the
+    state the GPU reached, match the oracle's."""
+    systems = W.batch_ensemble(512, seed=4)
+    b = BA.from_systems(systems)
+    b.autotune(os.path.join(tempfile.mkdtemp(), "tune.json"))
+    b.step(10)
+    pos, _, _ = b.get_state()
+    F = b.forces()
+    path, _, _ = b.layout()
+    offs = np.concatenate([[0], np.cumsum([s.n for s in systems])])
+    picks = [k for k in range(512) if path[k] == 0][::60] + [k for k in range(512) if path[k] == 1][::40]
+    assert len(picks) >= 8
+    for k in picks:
+        sl = slice(offs[k], offs[k + 1])
+        Fref, _, _ = O.lj_forces(pos[sl], systems[k].box, P)
+        assert force_error(F[sl], Fref) <= 2e-5, k

@@ -136,3 +136,18 @@ def test_switch_back_to_pair_potential_and_argument_errors():
     s.set_tbsma(CU.A, CU.xi, CU.p, CU.q, CU.r0, CU.rc)
     with pytest.raises(M.MDError):
         s.forces_backward(np.zeros_like(pos))  # derivatives are for the pair potential
+
+
+def test_full_size_bulk_copper():
+    """The benchmark's many-body workload, the paper's bulk copper size: 1,000,188 atoms
+    (63^3 fcc cells) at room-temperature displacements, all forces and the energy against
+    the oracle, after 20 steps in the benchmark's launch configuration."""
+    pos, vel, box = crystal(n_cells=63, seed=11)
+    s = make(pos, vel, box, dt=0.0982)
+    s.step(20)
+    p, _, _ = s.get_state()
+    F = s.forces()
+    Fref, E_ref, _ = O.tbsma_forces(p, box, CU)
+    assert force_error(F, Fref) <= 2e-5
+    pe, _, _ = s.energy_virial()
+    assert abs(pe - E_ref) <= 1e-6 * abs(E_ref)
