@@ -148,15 +148,17 @@ int md_forces(md_system *s, double *f_out, int device_ptrs);
 /*
  * Integrate n_steps velocity-Verlet steps: v += dt F/(2m); x += dt v;
  * rebuild lists if the policy says so; F = F(x); v += dt F/(2m).
- * Steps run as CUDA-graph launches (one graph per step, the rebuild decision
- * taken on the device in a conditional node); the host reads the device status
- * once per chunk of up to 200 steps.  If a rebuild inside a chunk outgrows the
+ * Steps run as CUDA-graph launches (the rebuild decision taken on the device in a
+ * conditional node per step; one step per graph while md_set_timing is on, else
+ * graphs of 8 steps where possible); the host reads the device status once per
+ * chunk of up to 200 steps.  If a rebuild inside a chunk outgrows the
  * list or tile capacity, the chunk is redone from a snapshot of its starting
  * state after the capacities have been regrown (md_info.n_redos counts these).
  * On the mixed-precision full-list path the force kernel of each step also
  * performs the velocity-Verlet updates around it (closing kick, and unless it
  * is the last step of the call, the next opening kick and drift): the same
- * operations as separate kernels, with the FP32 coordinates double-buffered.
+ * operations as separate kernels, with the positions (FP32 and FP64)
+ * double-buffered.  After md_set_tbsma the integration runs as separate kernels.
  * With the environment variable MDGB_NO_GRAPHS=1 set when the system is
  * created, the same kernels are launched from the host instead and the rebuild
  * flag is read after every step (slower; for profilers that do not follow
