@@ -116,7 +116,8 @@ int md_create(int64_t n, const double box[3], double r_cut, double skin,
  * Load positions, velocities (N x 3, original order) and species ids (N,
  * values in [0, n_species); NULL: all 0).  Positions may lie anywhere; they
  * are mapped into [0, L) at the next neighbour build.  Invalidates forces and
- * lists.  Errors: MD_ERR_ARG (bad species id), MD_ERR_CUDA.
+ * lists.  Errors: MD_ERR_ARG (bad species id), MD_ERR_NONFINITE (a position
+ * or velocity is NaN or infinite; the state is not loaded), MD_ERR_CUDA.
  */
 int md_set_state(md_system *s, const double *pos, const double *vel,
                  const int32_t *species, int device_ptrs);
@@ -267,6 +268,20 @@ int md_get_info(md_system *s, md_info *out);
  * and md_info.build_ms (the counters restart when timing is switched on).
  */
 int md_set_timing(md_system *s, int enable);
+
+/*
+ * Race detector for the colour schedule of the half-list kernel (Sec. II.A: no
+ * particle may be updated by two tasks of one wave; Sec. II.B).  On the GPU,
+ * with the current binning, every 2x2x2-cell block of a phase tags each atom of
+ * its 4x4x4-cell tile (the atoms its CTA writes) with its block id, by
+ * compare-and-swap on a per-atom tag; an atom already tagged by another block
+ * of the same phase is a conflict.  n_phases = 8 checks the 8 colour classes the
+ * kernels use (conflicts must be 0); n_phases = 1 puts every block into one
+ * phase, where overlapping tiles must show up.  *conflicts: the total over the
+ * phases.  Debug use only (not on any timed path).  Errors: MD_ERR_ARG (n_phases
+ * not 1 or 8), MD_ERR_STATE, MD_ERR_CUDA.
+ */
+int md_colour_conflicts(md_system *s, int32_t n_phases, int64_t *conflicts);
 
 /*
  * Kinetic energy 1/2 sum m v^2 of n atoms, for callers that cannot allocate

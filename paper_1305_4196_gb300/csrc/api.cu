@@ -1061,6 +1061,7 @@ int md_set_state(md_system* s, const double* pos, const double* vel, const int32
     s->lists_valid = false;
     s->forces_valid = false;
     if (s->h_flags[0] & 0x80000000u) return fail(s, MD_ERR_ARG, "species id out of range");
+    if (s->h_flags[0] & 0x40000000u) return fail(s, MD_ERR_NONFINITE, "non-finite position or velocity");
     s->has_state = true;
     return MD_OK;
 }
@@ -1177,6 +1178,34 @@ int md_set_params(md_system* s, const double* eps, const double* sigma, const do
     s->potential = 0;
     s->forces_valid = false;
     s->graphs_valid = false;
+    return MD_OK;
+}
+
+int md_colour_conflicts(md_system* s, int32_t n_phases, int64_t* conflicts) {
+    if (!s || !conflicts || (n_phases != 1 && n_phases != 8)) return MD_ERR_ARG;
+    if (!s->has_state) return fail(s, MD_ERR_STATE, "no state");
+    DeviceGuard dg(s->device);
+    *conflicts = 0;
+    if (s->n == 0) return MD_OK;
+    int rc = ensure_lists(s);  // a current binning
+    if (rc) return rc;
+    int32_t* tags = nullptr;
+    unsigned long long* cnt = nullptr;
+    CK(cudaMallocAsync(&tags, sizeof(int32_t) * (size_t)s->n, s->stream));
+    CK(cudaMallocAsync(&cnt, sizeof(unsigned long long), s->stream));
+    CK(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), s->stream));
+    const int per = s->g.nblock / n_phases;
+    for (int c = 0; c < n_phases; ++c) {
+        CK(cudaMemsetAsync(tags, 0xff, sizeof(int32_t) * (size_t)s->n, s->stream));  // -1: unclaimed
+        launch_colour_tags(s->st[0], s->g, c * per, per, tags, cnt, s->stream);
+        CKL();
+    }
+    unsigned long long h = 0;
+    CK(cudaMemcpyAsync(&h, cnt, sizeof(h), cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaFreeAsync(tags, s->stream));
+    CK(cudaFreeAsync(cnt, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    *conflicts = (int64_t)h;
     return MD_OK;
 }
 

@@ -214,12 +214,20 @@ __global__ void k_set_state(DevState s, const double* __restrict__ pos, const do
                             const int32_t* __restrict__ species, int nsp) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= s.n) return;
-    s.x[i] = pos[3 * i];
-    s.y[i] = pos[3 * i + 1];
-    s.z[i] = pos[3 * i + 2];
-    s.vx[i] = vel ? vel[3 * i] : 0.0;
-    s.vy[i] = vel ? vel[3 * i + 1] : 0.0;
-    s.vz[i] = vel ? vel[3 * i + 2] : 0.0;
+    double q[6] = {pos[3 * i], pos[3 * i + 1], pos[3 * i + 2], vel ? vel[3 * i] : 0.0, vel ? vel[3 * i + 1] : 0.0,
+                   vel ? vel[3 * i + 2] : 0.0};
+#pragma unroll
+    for (int k = 0; k < 6; ++k)
+        if (!isfinite(q[k])) {  // refused by md_set_state; kept finite meanwhile
+            atomicOr(s.err, 0x40000000u);
+            q[k] = 0.0;
+        }
+    s.x[i] = q[0];
+    s.y[i] = q[1];
+    s.z[i] = q[2];
+    s.vx[i] = q[3];
+    s.vy[i] = q[4];
+    s.vz[i] = q[5];
     s.ix[i] = 0;
     s.iy[i] = 0;
     s.iz[i] = 0;

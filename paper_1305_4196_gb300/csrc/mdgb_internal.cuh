@@ -226,6 +226,9 @@ enum { FUSE_KICK = 1, FUSE_KICK_KICK_DRIFT = 2 };  // modes of launch_forces_mix
 void launch_tbsma(const DevState& s, const Geometry& g, const TBTable& tb, const TileOffsets& to, int tile_cap,
                   float* emb, int with_energy, cudaStream_t st);
 size_t tbsma_smem_bytes(int tile_cap);
+// Colour-schedule race detector: blocks [block0, block0 + nblocks) tag their tile atoms.
+void launch_colour_tags(const DevState& s, const Geometry& g, int block0, int nblocks, int32_t* tags,
+                        unsigned long long* conflicts, cudaStream_t st);
 void init_tbsma_kernels();
 void launch_forces_fp64(const DevState& s, const Geometry& g, const PairTable& pt, int tile_cap, int half,
                         int with_energy, cudaStream_t st);

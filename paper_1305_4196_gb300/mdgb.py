@@ -40,7 +40,7 @@ MD_REBUILD_EVERY_K = 1
 EXPORTED = ["md_create", "md_set_state", "md_bin_cells", "md_build_neighbors", "md_forces", "md_step",
             "md_energy_virial", "md_get_state", "md_get_neighbors", "md_get_cells", "md_get_info",
             "md_set_timing", "md_last_error", "md_destroy", "md_kinetic_energy_noalloc", "md_set_params",
-            "md_forces_backward", "md_energy_param_grad", "md_set_tbsma"]
+            "md_forces_backward", "md_energy_param_grad", "md_set_tbsma", "md_colour_conflicts"]
 
 
 class md_params(C.Structure):
@@ -92,6 +92,7 @@ def _load():
     lib.md_forces_backward.argtypes = [P, P, C.c_int, P, P, P]
     lib.md_energy_param_grad.argtypes = [P, P, P]
     lib.md_set_tbsma.argtypes = [P] + [C.c_double] * 6
+    lib.md_colour_conflicts.argtypes = [P, C.c_int32, C.POINTER(C.c_int64)]
     lib.md_last_error.argtypes = [P, C.c_char_p, C.c_int64]
     lib.md_destroy.argtypes = [P]
     lib.md_destroy.restype = None
@@ -322,6 +323,12 @@ class System:
 
     def set_params(self, eps, sigma, rcut=None):
         md_set_params(self.handle, eps, sigma, rcut)
+
+    def colour_conflicts(self, n_phases=8):
+        """Atoms claimed by two blocks of one phase (md_colour_conflicts): 0 for the 8 colours."""
+        out = C.c_int64()
+        _check(self.handle, _lib.md_colour_conflicts(self.handle, int(n_phases), C.byref(out)))
+        return int(out.value)
 
     def set_tbsma(self, A, xi, p, q, r0, r_cut):
         """Cleri-Rosato tight-binding second-moment many-body potential (md_set_tbsma)."""

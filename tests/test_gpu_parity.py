@@ -469,3 +469,53 @@ def test_full_size_fused_steps_sampled():
     mag = np.sqrt((Fs ** 2).sum(1))
     frms = np.sqrt((F ** 2).sum(1).mean())
     assert (np.sqrt(((F[idx] - Fs) ** 2).sum(1)) / np.maximum(mag, frms)).max() <= TOL["mixed"]
+
+
+# ---------------------------------------------------------------- race detection, faults, checkpoints
+@pytest.mark.parametrize("n_cells", [10, 20])
+def test_colour_schedule_race_detector(n_cells):
+    """On the GPU, with the kernels' own block and tile mapping: no atom is claimed by two
+    blocks of one colour phase (the non-overlap rule of Sec. II.A for each of the 8 waves),
+    while one phase holding every block shows the overlaps the colours avoid."""
+    sysm = liquid(n_cells)
+    s = make(sysm, "mixed", "half")
+    s.forces()
+    assert s.colour_conflicts(8) == 0
+    assert s.colour_conflicts(1) > 0
+    with pytest.raises(M.MDError):
+        s.colour_conflicts(3)
+
+
+def test_nonfinite_state_is_refused():
+    sysm = liquid(8)
+    s = make(sysm)
+    bad = sysm.pos.copy()
+    bad[17, 1] = np.nan
+    with pytest.raises(M.MDError) as ei:
+        s.set_state(bad, sysm.vel, sysm.species)
+    assert ei.value.code == M.MD_ERR_NONFINITE
+    vel = sysm.vel.copy()
+    vel[3, 0] = np.inf
+    with pytest.raises(M.MDError):
+        s.set_state(sysm.pos, vel, sysm.species)
+    s.set_state(sysm.pos, sysm.vel, sysm.species)  # a valid state loads again
+    assert force_error(s.forces(), O.lj_forces(sysm.pos, sysm.box, O.LJParams.single())[0]) <= TOL["mixed"]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_checkpoint_resume_is_bitwise(precision):
+    """Save the state after 50 steps (md_get_state), restore it into a new system
+    (md_set_state) and run 50 more: bit-identical to the run that continued, when that run
+    rebuilds its lists at the save point as the restored one does."""
+    sysm = liquid(10)
+    a = make(sysm, precision)
+    a.step(50)
+    pos, vel, img = a.get_state()
+    a.build_neighbors()
+    a.step(50)
+    b = make(W.System(pos, vel, sysm.species, sysm.box), precision)
+    b.step(50)
+    pa, va, ia = a.get_state()
+    pb, vb, ib = b.get_state()
+    assert np.array_equal(pa, pb) and np.array_equal(va, vb)
+    assert np.array_equal(ia, ib + img)
