@@ -29,6 +29,7 @@ struct md_system {
     double rcut_default = 0;  // r_cut argument of md_create (pairs without a table entry)
     int precision = MD_MIXED, list_kind = MD_LIST_FULL, rebuild = MD_REBUILD_SKIN_HALF, rebuild_k = 10;
     int list_cap = 0, tile_cap = 0;
+    int tile_floor = 0;  // lower bound on tile_cap after a redo (the tiles a chunk of steps grew into)
     DevState st[3]{};  // [0] the state, [1] scratch for the reorder gather, [2] snapshot for redo
     int cur = 0;       // always 0: the state lives in st[0]
     // binning scratch
@@ -333,6 +334,7 @@ int do_build(md_system* s, int p = 0) {
             // (25 % headroom: later rebuilds inside graph-launched steps reuse this capacity)
             s->tile_cap = std::max(max_tile, std::min(round_up(max_tile + max_tile / 4 + 64, 32),
                                                       round_up((int)s->n + 1, 32)));
+            s->tile_cap = std::max(s->tile_cap, s->tile_floor);
             return MD_OK;
         }
     }
@@ -851,7 +853,14 @@ int restore_snapshot(md_system* s) {
     const int need_list = std::max((int)s->h_flags[2], saved_list);
     const int need_tile = std::max((int)s->h_flags[3], saved_tile);
     if (need_list > s->list_cap && (rc = alloc_lists(s, std::min(list_cap_for(need_list), 65535)))) return rc;
-    if (need_tile > s->tile_cap) s->tile_cap = round_up(need_tile + need_tile / 4 + 64, 32);
+    if (need_tile > s->tile_cap) {
+        // the rebuild in the chunk needed larger tiles than the restored state has: keep
+        // the grown capacity through the rebuild below (which otherwise fits it to the
+        // restored state), or the redone chunk would overflow again
+        s->tile_cap = std::min(round_up(need_tile + need_tile / 4 + 64, 32), round_up((int)s->n + 1, 32));
+        s->tile_cap = std::max(s->tile_cap, need_tile);
+        s->tile_floor = std::max(s->tile_floor, s->tile_cap);
+    }
     s->lists_valid = false;
     s->forces_valid = false;
     if ((rc = do_build(s))) return rc;

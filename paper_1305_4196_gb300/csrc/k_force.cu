@@ -541,6 +541,7 @@ __global__ void __launch_bounds__(F_THREADS) k_force_fp64_full(DevState s, Geome
                 }
             }
         })
+        if (!(isfinite(fx) && isfinite(fy) && isfinite(fz))) atomicOr(s.err, ERR_NONFINITE);
         s.f[gi] = fx;
         s.f[n + gi] = fy;
         s.f[2 * n + gi] = fz;
@@ -617,6 +618,8 @@ __global__ void __launch_bounds__(F_THREADS) k_force_fp64_half(DevState s, Geome
                 }
             }
         })
+        // a non-finite pair force leaves its mark on the i-side sum (a pair at r = 0 gives inf * 0)
+        if (!(isfinite(fx) && isfinite(fy) && isfinite(fz))) atomicOr(s.err, ERR_NONFINITE);
         atomicAdd(&acc[ui], fx);
         atomicAdd(&acc[tile_cap + ui], fy);
         atomicAdd(&acc[2 * tile_cap + ui], fz);

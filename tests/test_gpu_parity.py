@@ -519,3 +519,34 @@ def test_checkpoint_resume_is_bitwise(precision):
     pb, vb, ib = b.get_state()
     assert np.array_equal(pa, pb) and np.array_equal(va, vb)
     assert np.array_equal(ia, ib + img)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("lst", ["full", "half"])
+def test_nonfinite_force_is_reported(precision, lst):
+    """Two atoms on one spot (a pair at r = 0, an infinite force): the force kernels raise
+    the sticky non-finite flag, so md_forces and md_step return MD_ERR_NONFINITE."""
+    sysm = liquid(8)
+    pos = sysm.pos.copy()
+    pos[5] = pos[4]
+    bad = W.System(pos, sysm.vel, sysm.species, sysm.box)
+    s = make(bad, precision, lst)
+    with pytest.raises(M.MDError) as ei:
+        s.forces()
+    assert ei.value.code == M.MD_ERR_NONFINITE
+    s2 = make(bad, precision, lst)
+    with pytest.raises(M.MDError) as ei:
+        s2.step(2)
+    assert ei.value.code == M.MD_ERR_NONFINITE
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_skin_violation_is_reported(precision):
+    """Fixed-interval rebuilds (the paper's every-k protocol) with an interval far too long:
+    once an atom has moved more than skin/2 since the last build, md_step reports
+    MD_ERR_SKIN_VIOLATION instead of running on with incomplete lists."""
+    sysm = W.lj_fcc(10, seed=2)
+    s = make(sysm, precision, "full", rebuild=M.MD_REBUILD_EVERY_K, rebuild_k=100000)
+    with pytest.raises(M.MDError) as ei:
+        s.step(300)
+    assert ei.value.code == M.MD_ERR_SKIN_VIOLATION
