@@ -550,3 +550,24 @@ def test_skin_violation_is_reported(precision):
     with pytest.raises(M.MDError) as ei:
         s.step(300)
     assert ei.value.code == M.MD_ERR_SKIN_VIOLATION
+
+
+def test_redo_after_tile_growth_in_a_long_chunk():
+    """The strongly inhomogeneous workload (fcc slab plus 40 particles in vacuum, 1,192,114
+    atoms, T* = 0.3) in one 500-step call: the cold slab contracts, so a rebuild inside a
+    chunk of graph-launched steps outgrows the captured tile capacity and the chunk is redone
+    from its snapshot with grown capacities.  The redo must converge (the grown capacity is
+    kept through the rebuild of the restored state), and sampled forces at the end match
+    the oracle."""
+    sysm = W.slab_nanoparticles(152.0, rho=0.8442, T=0.3, seed=3)
+    s = make(sysm)
+    s.step(100)
+    s.step(500)
+    assert s.info()["n_redos"] >= 1
+    pos, _, _ = s.get_state()
+    F = s.forces()
+    idx = np.sort(W.splitmix64(13, 0, 256) % np.uint64(sysm.n)).astype(np.int64)
+    Fs, _, _ = O.lj_forces_subset(pos, sysm.box, O.LJParams.single(), idx)
+    mag = np.sqrt((Fs ** 2).sum(1))
+    frms = np.sqrt((F ** 2).sum(1).mean())
+    assert (np.sqrt(((F[idx] - Fs) ** 2).sum(1)) / np.maximum(mag, frms)).max() <= TOL["mixed"]
