@@ -487,7 +487,7 @@ def batch_ensemble_timing(stream, steps=200):
     b.autotune(cache)
     t_tune = time.perf_counter() - t0
     path, threads, R = b.layout()
-    b.step(2)  # warm-up (graph capture)
+    b.step(20)  # warm-up: graph captures of the buckets and of the larger systems' steps
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     b.step(steps)
