@@ -258,7 +258,7 @@ __global__ void __maxnreg__(SINGLE ? MDGB_FULL_MAX_REGS : MDGB_FULL_MAX_REGS_SPE
     __shared__ int nqueued;
     float4* tile = reinterpret_cast<float4*>(smem);
     uint16_t* queued = reinterpret_cast<uint16_t*>(tile + tile_cap);  // own atoms left to finish_atom_warp
-    const int b = blockIdx.x;
+    const int b = spatial_block(g, blockIdx.x);
     load_species_table(pt, stab);
     if (threadIdx.x == 0) nqueued = 0;
     tile_meta(g, s.cell_start, b, m);
@@ -499,7 +499,7 @@ __global__ void __launch_bounds__(F_THREADS) k_force_fp64_full(DevState s, Geome
     double* ty = tx + tile_cap;
     double* tz = ty + tile_cap;
     int* tsp = reinterpret_cast<int*>(tz + tile_cap);
-    const int b = blockIdx.x;
+    const int b = spatial_block(g, blockIdx.x);
     tile_meta(g, s.cell_start, b, m);
     const int T = m.prefix[64];
     if (T + 1 > tile_cap) {

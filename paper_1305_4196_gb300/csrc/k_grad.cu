@@ -60,7 +60,7 @@ __global__ void __launch_bounds__(G_THREADS) k_force_backward(DevState s, Geomet
                                                               int want_energy) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ TileMeta m;
-    const int b = blockIdx.x;
+    const int b = spatial_block(g, blockIdx.x);
     tile_meta(g, s.cell_start, b, m);
     const int T_ = m.prefix[64];
     if (T_ + 1 > tile_cap) {

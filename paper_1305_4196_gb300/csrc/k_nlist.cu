@@ -223,7 +223,7 @@ __global__ void __launch_bounds__(NL_WARPS * 32, 3) k_build_lists(DevState s, Ge
     float* tz = ty + SL;
     uint16_t* buf = reinterpret_cast<uint16_t*>(tz + SL);  // NL_WARPS x NL_RING x 32
 
-    const int b = blockIdx.x;
+    const int b = spatial_block(g, blockIdx.x);
     tile_meta(g, s.cell_start, b, m);
     const int T = m.prefix[64];
     if (threadIdx.x == 0) atomicMax(&s.stats[1], T + 1);

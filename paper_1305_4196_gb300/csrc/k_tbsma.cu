@@ -63,7 +63,7 @@ __device__ __forceinline__ bool tb_inside_exact(const DevState& s, const Geometr
 // Stage the tile; returns false (after flagging) when it does not fit.
 __device__ __forceinline__ bool tb_stage(const DevState& s, const Geometry& g, const TileOffsets& to, int tile_cap,
                                          TileMeta& m, float4* tile) {
-    tile_meta(g, s.cell_start, blockIdx.x, m);
+    tile_meta(g, s.cell_start, spatial_block(g, blockIdx.x), m);
     const int T = m.prefix[64];
     if (T + 1 > tile_cap) {
         if (threadIdx.x == 0) atomicOr(s.err, ERR_TILE_OVERFLOW);

@@ -134,6 +134,16 @@ __host__ __device__ inline void block_coords(const Geometry& g, int b, int& bx, 
     bz = 2 * hz + ((col >> 2) & 1);
 }
 
+// The i-th block in x-fastest spatial order.  Kernels with one CTA per block and no colour
+// constraint take their blocks in this order: CTAs that run at the same time then hold
+// neighbouring blocks, whose tiles share cells, so the staging reads hit L2.  (Block ids
+// themselves are colour-major, for the colour launches of the half-list kernels.)
+__host__ __device__ inline int spatial_block(const Geometry& g, int i) {
+    const int nbx = 2 * g.nbh[0], nby = 2 * g.nbh[1];
+    const int bx = i % nbx, t = i / nbx;
+    return block_id_of(g, bx, t % nby, t / nby);
+}
+
 __host__ __device__ inline int cell_id_of(const Geometry& g, int cx, int cy, int cz) {
     return block_id_of(g, cx >> 1, cy >> 1, cz >> 1) * 8 + ((cx & 1) | ((cy & 1) << 1) | ((cz & 1) << 2));
 }
