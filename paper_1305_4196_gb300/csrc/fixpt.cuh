@@ -109,6 +109,26 @@ __device__ __forceinline__ float4 lds_tile(unsigned base, int u) {
     return v;
 }
 
+// Neighbour lists come in chunks of 8 tile indices (one 16-byte load per chunk,
+// chunk c of atom i at uint4 index c * np + i); the last chunk is padded with the
+// tile's dummy slot T, which holds a point far outside every cutoff.
+#define MDGB_FOR_EACH_NEIGHBOUR(ROW0, NP, NCH, ...)                                         \
+    {                                                                                        \
+        const uint4* lp_ = (ROW0);                                                           \
+        uint4 cur_ = make_uint4(0u, 0u, 0u, 0u);                                             \
+        if ((NCH) > 0) cur_ = __ldcs(lp_);                                                   \
+        for (int c_ = 0; c_ < (NCH); ++c_) {                                                 \
+            uint4 nxt_ = cur_;                                                               \
+            if (c_ + 1 < (NCH)) nxt_ = __ldcs(lp_ + (size_t)(c_ + 1) * (NP));                \
+            const unsigned w_[4] = {cur_.x, cur_.y, cur_.z, cur_.w};                         \
+            _Pragma("unroll") for (int e_ = 0; e_ < 8; ++e_) {                               \
+                const int u = (int)((w_[e_ >> 1] >> ((e_ & 1) * 16)) & 0xffffu);             \
+                __VA_ARGS__                                                                  \
+            }                                                                                \
+            cur_ = nxt_;                                                                     \
+        }                                                                                    \
+    }
+
 // ---------------------------------------------------------------- packed FP32x2 helpers
 // sm_100-family packed single-precision arithmetic: two IEEE FP32 operations per
 // instruction, each rounded exactly as its scalar counterpart.

@@ -23,7 +23,7 @@
 // result is bit-reproducible for any list order, thread mapping or list kind,
 // and f_ji = -f_ij bit for bit makes the total force exactly zero.
 //
-// FP64: the same structure with FP64 tile coordinates and FP64 sums.
+// FP64: the same structure with FP64 tile coordinates and FP64 sums (k_force_fp64.cu).
 #include "fixpt.cuh"
 #include "tile.cuh"
 
@@ -52,26 +52,6 @@ __device__ __forceinline__ float lj_fs_unmasked(const PairTable& pt, int t, floa
     s6_out = s6;
     return (c48 * s6 - c24) * s6 * inv;  // constants carry the 2^11 scale
 }
-
-// Neighbour lists come in chunks of 8 tile indices (one 16-byte load per chunk,
-// chunk c of atom i at uint4 index c * np + i); the last chunk is padded with the
-// tile's dummy slot T, which holds a point far outside every cutoff.
-#define MDGB_FOR_EACH_NEIGHBOUR(ROW0, NP, NCH, ...)                                         \
-    {                                                                                        \
-        const uint4* lp_ = (ROW0);                                                           \
-        uint4 cur_ = make_uint4(0u, 0u, 0u, 0u);                                             \
-        if ((NCH) > 0) cur_ = __ldcs(lp_);                                                   \
-        for (int c_ = 0; c_ < (NCH); ++c_) {                                                 \
-            uint4 nxt_ = cur_;                                                               \
-            if (c_ + 1 < (NCH)) nxt_ = __ldcs(lp_ + (size_t)(c_ + 1) * (NP));                \
-            const unsigned w_[4] = {cur_.x, cur_.y, cur_.z, cur_.w};                         \
-            _Pragma("unroll") for (int e_ = 0; e_ < 8; ++e_) {                               \
-                const int u = (int)((w_[e_ >> 1] >> ((e_ & 1) * 16)) & 0xffffu);             \
-                __VA_ARGS__                                                                  \
-            }                                                                                \
-            cur_ = nxt_;                                                                     \
-        }                                                                                    \
-    }
 
 __device__ __forceinline__ void stage_dummy_f32(float4* tile, int T) {
     if (threadIdx.x == 0) tile[T] = make_float4(1.0e4f, 1.0e4f, 1.0e4f, __int_as_float(0));
@@ -490,160 +470,6 @@ __global__ void __launch_bounds__(F_THREADS) k_force_mixed_half(DevState s, Geom
     }
 }
 
-// ---------------------------------------------------------------- FP64
-template <bool EV>
-__global__ void __launch_bounds__(F_THREADS) k_force_fp64_full(DevState s, Geometry g, PairTable pt, int tile_cap) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ TileMeta m;
-    double* tx = reinterpret_cast<double*>(smem);
-    double* ty = tx + tile_cap;
-    double* tz = ty + tile_cap;
-    int* tsp = reinterpret_cast<int*>(tz + tile_cap);
-    const int b = spatial_block(g, blockIdx.x);
-    tile_meta(g, s.cell_start, b, m);
-    const int T = m.prefix[64];
-    if (T + 1 > tile_cap) {
-        if (threadIdx.x == 0) atomicOr(s.err, ERR_TILE_OVERFLOW);
-        return;
-    }
-    tile_stage_f64(s, g, m, b, tx, ty, tz, tsp);
-    __syncthreads();
-    const int blk0 = m.start[0];
-    const int nown = m.prefix[8];
-    const int64_t n = s.n;
-    const int np = s.np;
-    for (int ui = threadIdx.x; ui < nown; ui += blockDim.x) {
-        const int gi = blk0 + ui;
-        const double xi = tx[ui], yi = ty[ui], zi = tz[ui];
-        const int si = tsp[ui];
-        const int nch = (s.nl_cnt[gi] + 7) >> 3;
-        double fx = 0, fy = 0, fz = 0, pe = 0, w0 = 0, w1 = 0, w2 = 0, w3 = 0, w4 = 0, w5 = 0;
-        MDGB_FOR_EACH_NEIGHBOUR(reinterpret_cast<const uint4*>(s.nl) + gi, np, nch, {
-            const double dx = xi - tx[u], dy = yi - ty[u], dz = zi - tz[u];
-            const double r2 = dx * dx + dy * dy + dz * dz;
-            const int t = si * pt.nsp + tsp[u];
-            if (r2 < pt.rc2_d[t]) {
-                const double sr2 = pt.sig2_d[t] / r2;
-                const double s6 = sr2 * sr2 * sr2;
-                const double e = pt.eps_d[t];
-                const double fr = 24.0 * e * (2.0 * s6 * s6 - s6) / r2;
-                fx += fr * dx;
-                fy += fr * dy;
-                fz += fr * dz;
-                if (EV) {
-                    pe += 4.0 * e * (s6 * s6 - s6);
-                    w0 += dx * (fr * dx);
-                    w1 += dy * (fr * dy);
-                    w2 += dz * (fr * dz);
-                    w3 += dx * (fr * dy);
-                    w4 += dx * (fr * dz);
-                    w5 += dy * (fr * dz);
-                }
-            }
-        })
-        if (!(isfinite(fx) && isfinite(fy) && isfinite(fz))) atomicOr(s.err, ERR_NONFINITE);
-        s.f[gi] = fx;
-        s.f[n + gi] = fy;
-        s.f[2 * n + gi] = fz;
-        if (EV) {
-            s.pe_atom_d[gi] = 0.5 * pe;
-            s.vir_atom_d[gi] = 0.5 * w0;
-            s.vir_atom_d[n + gi] = 0.5 * w1;
-            s.vir_atom_d[2 * n + gi] = 0.5 * w2;
-            s.vir_atom_d[3 * n + gi] = 0.5 * w3;
-            s.vir_atom_d[4 * n + gi] = 0.5 * w4;
-            s.vir_atom_d[5 * n + gi] = 0.5 * w5;
-        }
-    }
-}
-
-// FP64 half list, one colour: reactions through FP64 shared-memory accumulators.
-template <bool EV>
-__global__ void __launch_bounds__(F_THREADS) k_force_fp64_half(DevState s, Geometry g, PairTable pt, int tile_cap,
-                                                               int block0) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ TileMeta m;
-    double* tx = reinterpret_cast<double*>(smem);
-    double* ty = tx + tile_cap;
-    double* tz = ty + tile_cap;
-    double* acc = tz + tile_cap;  // 3 x tile_cap
-    int* tsp = reinterpret_cast<int*>(acc + 3 * tile_cap);
-    const int b = block0 + blockIdx.x;
-    tile_meta(g, s.cell_start, b, m);
-    const int T = m.prefix[64];
-    if (T + 1 > tile_cap) {
-        if (threadIdx.x == 0) atomicOr(s.err, ERR_TILE_OVERFLOW);
-        return;
-    }
-    tile_stage_f64(s, g, m, b, tx, ty, tz, tsp);
-    for (int u = threadIdx.x; u <= T; u += blockDim.x) {
-        acc[u] = 0;
-        acc[tile_cap + u] = 0;
-        acc[2 * tile_cap + u] = 0;
-    }
-    __syncthreads();
-    const int blk0 = m.start[0];
-    const int nown = m.prefix[8];
-    const int64_t n = s.n;
-    const int np = s.np;
-    for (int ui = threadIdx.x; ui < nown; ui += blockDim.x) {
-        const int gi = blk0 + ui;
-        const double xi = tx[ui], yi = ty[ui], zi = tz[ui];
-        const int si = tsp[ui];
-        const int nch = (s.nl_cnt[gi] + 7) >> 3;
-        double fx = 0, fy = 0, fz = 0, pe = 0, w0 = 0, w1 = 0, w2 = 0, w3 = 0, w4 = 0, w5 = 0;
-        MDGB_FOR_EACH_NEIGHBOUR(reinterpret_cast<const uint4*>(s.nl) + gi, np, nch, {
-            const double dx = xi - tx[u], dy = yi - ty[u], dz = zi - tz[u];
-            const double r2 = dx * dx + dy * dy + dz * dz;
-            const int t = si * pt.nsp + tsp[u];
-            if (r2 < pt.rc2_d[t]) {
-                const double sr2 = pt.sig2_d[t] / r2;
-                const double s6 = sr2 * sr2 * sr2;
-                const double e = pt.eps_d[t];
-                const double fr = 24.0 * e * (2.0 * s6 * s6 - s6) / r2;
-                fx += fr * dx;
-                fy += fr * dy;
-                fz += fr * dz;
-                atomicAdd(&acc[u], -fr * dx);
-                atomicAdd(&acc[tile_cap + u], -fr * dy);
-                atomicAdd(&acc[2 * tile_cap + u], -fr * dz);
-                if (EV) {
-                    pe += 4.0 * e * (s6 * s6 - s6);
-                    w0 += dx * (fr * dx);
-                    w1 += dy * (fr * dy);
-                    w2 += dz * (fr * dz);
-                    w3 += dx * (fr * dy);
-                    w4 += dx * (fr * dz);
-                    w5 += dy * (fr * dz);
-                }
-            }
-        })
-        // a non-finite pair force leaves its mark on the i-side sum (a pair at r = 0 gives inf * 0)
-        if (!(isfinite(fx) && isfinite(fy) && isfinite(fz))) atomicOr(s.err, ERR_NONFINITE);
-        atomicAdd(&acc[ui], fx);
-        atomicAdd(&acc[tile_cap + ui], fy);
-        atomicAdd(&acc[2 * tile_cap + ui], fz);
-        if (EV) {
-            s.pe_atom_d[gi] = pe;
-            s.vir_atom_d[gi] = w0;
-            s.vir_atom_d[n + gi] = w1;
-            s.vir_atom_d[2 * n + gi] = w2;
-            s.vir_atom_d[3 * n + gi] = w3;
-            s.vir_atom_d[4 * n + gi] = w4;
-            s.vir_atom_d[5 * n + gi] = w5;
-        }
-    }
-    __syncthreads();
-    for (int u = threadIdx.x; u < T; u += blockDim.x) {
-        const int slot = tile_slot_of(m, u);
-        const int gj = m.start[slot] + (u - m.prefix[slot]);
-        s.f[gj] += acc[u];
-        s.f[n + gj] += acc[tile_cap + u];
-        s.f[2 * n + gj] += acc[2 * tile_cap + u];
-    }
-}
-
-// ---------------------------------------------------------------- launchers
 size_t force_smem_bytes(int mixed, int half, int with_energy, int tile_cap) {
     (void)with_energy;
     if (mixed) {
@@ -682,10 +508,7 @@ void init_force_kernels() {
     allow_max_smem(k_force_mixed_half<true, true>);
     allow_max_smem(k_force_mixed_half<false, false>);
     allow_max_smem(k_force_mixed_half<false, true>);
-    allow_max_smem(k_force_fp64_full<false>);
-    allow_max_smem(k_force_fp64_full<true>);
-    allow_max_smem(k_force_fp64_half<false>);
-    allow_max_smem(k_force_fp64_half<true>);
+    init_force_fp64_kernels();
 }
 
 // |fs2 * d| < 2^22 (the exact range of the two-part split) is guaranteed when |fs2| < 2^22 / r_cut
@@ -759,29 +582,6 @@ void launch_forces_mixed_fused(const DevState& s, const Geometry& g, const PairT
             launch_full_mode<true, FM_KKD>(s, g, pt, to, tile_cap, fs2_max, out, dt, lim2_f, smem, st);
         else
             launch_full_mode<false, FM_KKD>(s, g, pt, to, tile_cap, fs2_max, out, dt, lim2_f, smem, st);
-    }
-}
-
-void launch_forces_fp64(const DevState& s, const Geometry& g, const PairTable& pt, int tile_cap, int half,
-                        int with_energy, cudaStream_t st) {
-    if (s.n == 0) return;
-    const size_t smem = force_smem_bytes(0, half, with_energy, tile_cap);
-    if (!half) {
-        if (with_energy) {
-            k_force_fp64_full<true><<<g.nblock, F_THREADS, smem, st>>>(s, g, pt, tile_cap);
-        } else {
-            k_force_fp64_full<false><<<g.nblock, F_THREADS, smem, st>>>(s, g, pt, tile_cap);
-        }
-        return;
-    }
-    cudaMemsetAsync(s.f, 0, sizeof(double) * 3 * (size_t)s.n, st);
-    const int per = g.nblock / 8;
-    for (int col = 0; col < 8; ++col) {
-        if (with_energy) {
-            k_force_fp64_half<true><<<per, F_THREADS, smem, st>>>(s, g, pt, tile_cap, col * per);
-        } else {
-            k_force_fp64_half<false><<<per, F_THREADS, smem, st>>>(s, g, pt, tile_cap, col * per);
-        }
     }
 }
 

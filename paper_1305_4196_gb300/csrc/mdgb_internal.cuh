@@ -255,6 +255,7 @@ void launch_pairs_out(const DevState& s, const Geometry& g, int half, unsigned l
                       int32_t* pairs, long long cap, cudaStream_t st);
 
 void init_force_kernels();
+void init_force_fp64_kernels();
 void init_grad_kernels();
 size_t backward_smem_bytes(int fp64, int tile_cap);
 size_t backward_scratch_doubles(int64_t n, int nsp, int nparts);
