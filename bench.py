@@ -56,6 +56,10 @@ def parse():
     p.add_argument("--e2e-steps", type=int, default=3)
     p.add_argument("--many-body", action="store_true",
                    help="only time the TB-SMA copper system (the many_body extra) and print it")
+    p.add_argument("--only", choices=["ensemble", "force-matching"],
+                   help="only time that extra (the batch_ensemble or force_matching entry) and print it")
+    p.add_argument("--ensemble-steps", type=int, default=200, help="timed steps of the ensemble extra")
+    p.add_argument("--no-autotune", action="store_true", help="ensemble extra: keep the default launch shapes")
     return p.parse_args()
 
 
@@ -471,7 +475,7 @@ def comparisons(args, sysm, M, stream, value, list_len_hom, hom=None):
     return {"compare": out}
 
 
-def batch_ensemble_timing(stream, steps=200):
+def batch_ensemble_timing(stream, steps=200, autotune=True):
     """512 independent LJ systems, atom counts log-uniform in 256..32,768, densities
     U(0.7, 0.95), temperatures U(0.5, 1.5), 200 steps, mixed precision: systems of at most
     8,192 atoms one CTA each in one launch per size bucket (shapes autotuned first), the
@@ -482,10 +486,12 @@ def batch_ensemble_timing(stream, steps=200):
     from paper_1305_4196_gb300 import workloads as W
     systems = W.batch_ensemble(512, seed=4)
     b = BA.from_systems(systems, stream=stream.cuda_stream)
-    cache = os.path.join(tempfile.mkdtemp(), "batch_tune.json")
-    t0 = time.perf_counter()
-    b.autotune(cache)
-    t_tune = time.perf_counter() - t0
+    t_tune = 0.0
+    if autotune:
+        cache = os.path.join(tempfile.mkdtemp(), "batch_tune.json")
+        t0 = time.perf_counter()
+        b.autotune(cache)
+        t_tune = time.perf_counter() - t0
     path, threads, R = b.layout()
     b.step(20)  # warm-up: graph captures of the buckets and of the larger systems' steps
     torch.cuda.synchronize()
@@ -601,6 +607,18 @@ def main():
         from paper_1305_4196_gb300 import mdgb as M
         stream = torch.cuda.Stream()
         print(json.dumps({"many_body": many_body_timing(M, stream, steps=args.inner)}))
+    elif args.only:
+        import torch
+        from paper_1305_4196_gb300 import build as B
+        B.build()
+        from paper_1305_4196_gb300 import mdgb as M
+        stream = torch.cuda.Stream()
+        if args.only == "ensemble":
+            res = {"batch_ensemble": batch_ensemble_timing(stream, steps=args.ensemble_steps,
+                                                           autotune=not args.no_autotune)}
+        else:
+            res = {"force_matching": force_matching_timing(M, stream)}
+        print(json.dumps(res))
     elif args.impl == "reference":
         run_reference(args)
     else:
