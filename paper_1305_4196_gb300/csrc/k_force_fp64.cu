@@ -15,9 +15,12 @@
 #include "fixpt.cuh"
 #include "tile.cuh"
 
+#include <algorithm>
+
 namespace mdgb {
 
 constexpr int F_THREADS = 256;
+static int g_sm_count = 0;  // SMs of the device, read at initialisation (never during a stream capture)
 
 // 1/x to within about an ulp: the hardware's approximate reciprocal, refined by three
 // Newton-Raphson steps y <- y + y (1 - x y), each of which doubles the correct bits.  For
@@ -35,14 +38,17 @@ __device__ __forceinline__ double rcp_nr(double x) {
 
 // ---------------------------------------------------------------- full list
 template <bool EV>
-__global__ void __launch_bounds__(F_THREADS) k_force_fp64_full(DevState s, Geometry g, PairTable pt, int tile_cap) {
+__global__ void __launch_bounds__(F_THREADS) k_force_fp64_full(DevState s, Geometry g, PairTable pt, int tile_cap,
+                                                               int split) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ TileMeta m;
     double* tx = reinterpret_cast<double*>(smem);
     double* ty = tx + tile_cap;
     double* tz = ty + tile_cap;
     int* tsp = reinterpret_cast<int*>(tz + tile_cap);
-    const int b = spatial_block(g, blockIdx.x);
+    // split CTAs share one block (small systems): each stages the tile and takes every
+    // split-th group of F_THREADS own atoms
+    const int b = spatial_block(g, blockIdx.x / split), part = blockIdx.x % split;
     tile_meta(g, s.cell_start, b, m);
     const int T = m.prefix[64];
     if (T + 1 > tile_cap) {
@@ -55,7 +61,7 @@ __global__ void __launch_bounds__(F_THREADS) k_force_fp64_full(DevState s, Geome
     const int nown = m.prefix[8];
     const int64_t n = s.n;
     const int np = s.np;
-    for (int ui = threadIdx.x; ui < nown; ui += blockDim.x) {
+    for (int ui = part * blockDim.x + threadIdx.x; ui < nown; ui += split * blockDim.x) {
         const int gi = blk0 + ui;
         const double xi = tx[ui], yi = ty[ui], zi = tz[ui];
         const int si = tsp[ui];
@@ -194,10 +200,16 @@ void launch_forces_fp64(const DevState& s, const Geometry& g, const PairTable& p
     if (s.n == 0) return;
     const size_t smem = force_smem_bytes(0, half, with_energy, tile_cap);
     if (!half) {
+        // CTAs per block: about one own atom per thread while the grid is below two CTAs per SM
+        const int sms = g_sm_count > 0 ? g_sm_count : 152;
+        const int64_t per_block = (s.n + g.nblock - 1) / g.nblock;
+        int split = (int)std::min<int64_t>((per_block + F_THREADS - 1) / F_THREADS, (2 * sms + g.nblock - 1) / g.nblock);
+        split = std::max(1, std::min(split, 8));
+        const unsigned grid = (unsigned)g.nblock * (unsigned)split;
         if (with_energy) {
-            k_force_fp64_full<true><<<g.nblock, F_THREADS, smem, st>>>(s, g, pt, tile_cap);
+            k_force_fp64_full<true><<<grid, F_THREADS, smem, st>>>(s, g, pt, tile_cap, split);
         } else {
-            k_force_fp64_full<false><<<g.nblock, F_THREADS, smem, st>>>(s, g, pt, tile_cap);
+            k_force_fp64_full<false><<<grid, F_THREADS, smem, st>>>(s, g, pt, tile_cap, split);
         }
         return;
     }
@@ -223,6 +235,8 @@ static void allow_max_smem(K kernel) {
 }
 
 void init_force_fp64_kernels() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&g_sm_count, cudaDevAttrMultiProcessorCount, dev);
     allow_max_smem(k_force_fp64_full<false>);
     allow_max_smem(k_force_fp64_full<true>);
     allow_max_smem(k_force_fp64_half<false>);

@@ -22,9 +22,12 @@
 // block-frame coordinates) on mixed-precision ones.
 #include "tile.cuh"
 
+#include <algorithm>
+
 namespace mdgb {
 
 constexpr int G_THREADS = 128;
+static int g_sm_count = 0;  // SMs of the device, read at initialisation
 constexpr int G_QUANT = 4;  // per species pair: dL/deps, dL/dsig, dE/deps, dE/dsig
 
 template <typename T>
@@ -57,10 +60,12 @@ template <typename T>
 __global__ void __launch_bounds__(G_THREADS) k_force_backward(DevState s, Geometry g, PairTable pt, TileOffsets to,
                                                               int tile_cap, const double* __restrict__ G,
                                                               double* __restrict__ gx_out, double* __restrict__ prm,
-                                                              int want_energy) {
+                                                              int want_energy, int split) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ TileMeta m;
-    const int b = spatial_block(g, blockIdx.x);
+    // split CTAs share one block: each stages the whole tile and takes every split-th group
+    // of G_THREADS own atoms, so that a small system still spreads over the SMs
+    const int b = spatial_block(g, blockIdx.x / split), part = blockIdx.x % split;
     tile_meta(g, s.cell_start, b, m);
     const int T_ = m.prefix[64];
     if (T_ + 1 > tile_cap) {
@@ -104,7 +109,7 @@ __global__ void __launch_bounds__(G_THREADS) k_force_backward(DevState s, Geomet
     const int ncol = nsp * nsp * G_QUANT;
     const int blk0 = m.start[0];
     const int64_t n = s.n;
-    for (int ui = threadIdx.x; ui < nown; ui += blockDim.x) {
+    for (int ui = part * blockDim.x + threadIdx.x; ui < nown; ui += split * blockDim.x) {
         const int64_t gi = blk0 + ui;
         const T xi = t.x[ui], yi = t.y[ui], zi = t.z[ui];
         const T Gx = G ? (T)G[gi] : T(0), Gy = G ? (T)G[n + gi] : T(0), Gz = G ? (T)G[2 * n + gi] : T(0);
@@ -249,12 +254,19 @@ void launch_force_backward(const DevState& s, const Geometry& g, const PairTable
     const unsigned nb = (unsigned)((n + bs - 1) / bs);
     if (G) k_grad_in<<<nb, bs, 0, st>>>(s, G, Gc);
     const size_t smem = backward_smem_bytes(fp64, tile_cap);
+    // CTAs per block: enough for about one own atom per thread, while the grid is below two
+    // CTAs per SM (small systems, e.g. force-matching snapshots of a few 10^4 atoms)
+    const int sms = g_sm_count > 0 ? g_sm_count : 152;
+    const int64_t per_block = (n + g.nblock - 1) / g.nblock;
+    int split = (int)std::min<int64_t>((per_block + G_THREADS - 1) / G_THREADS, (2 * sms + g.nblock - 1) / g.nblock);
+    split = std::max(1, std::min(split, 8));
+    const unsigned grid = (unsigned)g.nblock * (unsigned)split;
     if (fp64)
-        k_force_backward<double><<<g.nblock, G_THREADS, smem, st>>>(s, g, pt, to, tile_cap, G ? Gc : nullptr,
-                                                                   gx_orig ? gxc : nullptr, prm, want_energy);
+        k_force_backward<double><<<grid, G_THREADS, smem, st>>>(s, g, pt, to, tile_cap, G ? Gc : nullptr,
+                                                               gx_orig ? gxc : nullptr, prm, want_energy, split);
     else
-        k_force_backward<float><<<g.nblock, G_THREADS, smem, st>>>(s, g, pt, to, tile_cap, G ? Gc : nullptr,
-                                                                  gx_orig ? gxc : nullptr, prm, want_energy);
+        k_force_backward<float><<<grid, G_THREADS, smem, st>>>(s, g, pt, to, tile_cap, G ? Gc : nullptr,
+                                                              gx_orig ? gxc : nullptr, prm, want_energy, split);
     if (gx_orig) k_grad_out<<<nb, bs, 0, st>>>(s, gxc, gx_orig);
     const int64_t chunk = (n + nparts - 1) / nparts;
     k_colsum_partials<<<nparts, CS_THREADS, 0, st>>>(prm, n, ncol, chunk > 0 ? chunk : 1, part);
@@ -272,6 +284,8 @@ static void allow_max_smem(K kernel) {
 }
 
 void init_grad_kernels() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&g_sm_count, cudaDevAttrMultiProcessorCount, dev);
     allow_max_smem(k_force_backward<double>);
     allow_max_smem(k_force_backward<float>);
 }
