@@ -571,3 +571,22 @@ def test_redo_after_tile_growth_in_a_long_chunk():
     mag = np.sqrt((Fs ** 2).sum(1))
     frms = np.sqrt((F ** 2).sum(1).mean())
     assert (np.sqrt(((F[idx] - Fs) ** 2).sum(1)) / np.maximum(mag, frms)).max() <= TOL["mixed"]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_time_reversibility(precision):
+    """Velocity Verlet is time-reversible: 50 steps forward, velocities negated, 50 steps back
+    return the atoms to their start up to the rounding of the FP64 updates (the forces are a
+    deterministic function of the positions on both paths, and rebuilds do not change them)."""
+    sysm = liquid(10)
+    s = make(sysm, precision)
+    x0, s_vel0, i0 = s.get_state()
+    s.step(50)
+    pos, vel, img = s.get_state()
+    s.set_state(pos, -vel, sysm.species)
+    s.step(50)
+    x1, v1, i1 = s.get_state()
+    # set_state starts the image counters again from zero
+    d = np.abs((x1 + (i1 + img) * sysm.box) - (x0 + i0 * sysm.box)).max()
+    assert d < 1e-8, d
+    assert np.abs(v1 + s_vel0).max() < 1e-8
