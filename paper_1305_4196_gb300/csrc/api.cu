@@ -53,6 +53,8 @@ struct md_system {
         cudaGraph_t graph = nullptr;
         cudaGraphExec_t exec = nullptr;
         cudaGraphNode_t ev_a = nullptr, ev_b = nullptr;
+        // multi-step graphs under md_set_timing: the event nodes around each step's force kernel
+        std::vector<cudaGraphNode_t> ev_multi_a, ev_multi_b;
     };
     cudaStream_t cap_stream = nullptr;
     StepGraph g_first, g_mid;
@@ -606,8 +608,23 @@ int capture_fused_multi(md_system* s, md_system::StepGraph& out) {
         CK(cudaGraphAddNode(&cnode, cg, deps, nullptr, ndeps, &cp));
         cudaGraph_t body = cp.conditional.phGraph_out[0];
         CK(cudaStreamUpdateCaptureDependencies(cs, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies));
+        if (s->timing) {
+            // event nodes around the force kernel; each launch points them at fresh events
+            auto ev = take_events(s);
+            s->ev_free.push_back(ev);
+            CK(cudaEventRecordWithFlags(ev.first, cs, cudaEventRecordExternal));
+            CK(cudaStreamGetCaptureInfo(cs, &status, nullptr, &cg, &deps, nullptr, &ndeps));
+            out.ev_multi_a.push_back(ndeps ? deps[0] : nullptr);
+        }
         launch_forces_mixed_fused(a, s->g, s->pt, s->to, s->tile_cap, FUSE_KICK_KICK_DRIFT, step_out(s, 1 - p), s->dt,
                                   s->lim2, cs);
+        if (s->timing) {
+            auto ev = take_events(s);
+            s->ev_free.push_back(ev);
+            CK(cudaEventRecordWithFlags(ev.second, cs, cudaEventRecordExternal));
+            CK(cudaStreamGetCaptureInfo(cs, &status, nullptr, &cg, &deps, nullptr, &ndeps));
+            out.ev_multi_b.push_back(ndeps ? deps[0] : nullptr);
+        }
         CK(cudaStreamGetCaptureInfo(cs, &status, nullptr, &cg, &deps, nullptr, &ndeps));
         tail.assign(deps, deps + ndeps);
         CK(cudaStreamEndCapture(cs, &g));
@@ -632,7 +649,7 @@ int ensure_graphs(md_system* s) {
         for (int k = 0; k < 2; ++k)
             for (int p = 0; p < 2; ++p)
                 if ((rc = capture_fused(s, k == 1, p, s->g_fused[k][p]))) return rc;
-        if (!s->timing && (rc = capture_fused_multi(s, s->g_multi))) return rc;
+        if ((rc = capture_fused_multi(s, s->g_multi))) return rc;
     } else {
         if ((rc = capture_step(s, INT_KICK_DRIFT, s->g_first))) return rc;
         if ((rc = capture_step(s, INT_KICK_KICK_DRIFT, s->g_mid))) return rc;
@@ -740,7 +757,17 @@ int run_chunk_fused(md_system* s, int len, bool first, bool last) {
     int p = 0;
     const int n_kkd = last ? len - 1 : len;  // steps that end with the next opening kick and drift
     for (int k = 0; k < len; ++k) {
-        if (!s->timing && s->g_multi.exec && p == 0 && k + MULTI_STEPS <= n_kkd) {
+        if (s->g_multi.exec && p == 0 && k + MULTI_STEPS <= n_kkd) {
+            if (s->timing) {
+                const auto& gm = s->g_multi;
+                for (size_t j = 0; j < gm.ev_multi_a.size() && j < gm.ev_multi_b.size(); ++j) {
+                    if (!gm.ev_multi_a[j] || !gm.ev_multi_b[j]) continue;
+                    auto ev = take_events(s);
+                    CK(cudaGraphExecEventRecordNodeSetEvent(gm.exec, gm.ev_multi_a[j], ev.first));
+                    CK(cudaGraphExecEventRecordNodeSetEvent(gm.exec, gm.ev_multi_b[j], ev.second));
+                    s->ev_force.push_back(ev);
+                }
+            }
             CK(cudaGraphLaunch(s->g_multi.exec, s->stream));  // MULTI_STEPS steps; back in buffer 0
             s->launches += 2 * MULTI_STEPS;
             s->force_evals += MULTI_STEPS;
