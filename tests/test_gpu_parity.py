@@ -593,3 +593,43 @@ def test_time_reversibility(precision):
     tol = 1e-8 if precision == "fp64" else 1e-5
     assert d < tol, d
     assert np.abs(v1 + s_vel0).max() < (1e-8 if precision == "fp64" else 1e-3)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_randomised_small_systems(seed):
+    """Seeded random shapes: a gas of 2..800 atoms in a box with sides drawn from 11.3..17
+    sigma (neighbour set bit for bit against the oracle, both list kinds), and a jittered fcc
+    crystal of 1,500..4,000 atoms at a density drawn from 0.7..0.95 with random vacancies,
+    whose ragged cells the forces must handle (both precisions and list kinds).  Boxes this
+    small have 4 cells per side, so every tile holds the whole system; 4,000 atoms keep the
+    FP64 half-list tile (52 B per atom) within shared memory."""
+    rng = np.random.default_rng(1000 + seed)
+    box = rng.uniform(11.3, 17.0, 3)
+    n = int(rng.integers(2, 800))
+    pos = W.random_gas(n, box, seed=200 + seed)
+    for lst in (M.MD_LIST_FULL, M.MD_LIST_HALF_COLOUR8):
+        s = M.System(n, box, list_kind=lst)
+        s.set_state(pos, np.zeros_like(pos))
+        assert np.array_equal(s.neighbors(), O.neighbor_pairs(pos, box, RC + SKIN))
+        s.close()
+    sysm = W.fcc_vacancies(int(rng.integers(1500, 4000)), float(rng.uniform(0.7, 0.95)), 1.0, seed=300 + seed)
+    Fref = O.lj_forces(sysm.pos, sysm.box, O.LJParams.single())[0]
+    for precision in ("fp64", "mixed"):
+        for lst in ("full", "half"):
+            s = make(sysm, precision, lst)
+            assert force_error(s.forces(), Fref) <= TOL[precision], (precision, lst)
+            s.close()
+
+
+def test_whole_system_tile_limit_is_reported():
+    """With 4 cells per side every tile is the whole system.  A system whose tile does not
+    fit the kernel's shared memory (here the FP64 half-list kernel, 52 B per atom, at 6,000
+    atoms) is refused with MD_ERR_CELL_OVERFLOW, while the full-list kernels take it."""
+    sysm = W.fcc_vacancies(6000, 0.8, 1.0, seed=5)
+    s = make(sysm, "fp64", "half")
+    with pytest.raises(M.MDError) as ei:
+        s.forces()
+    assert ei.value.code == M.MD_ERR_CELL_OVERFLOW
+    Fref = O.lj_forces(sysm.pos, sysm.box, O.LJParams.single())[0]
+    for precision in ("fp64", "mixed"):
+        assert force_error(make(sysm, precision, "full").forces(), Fref) <= TOL[precision]
