@@ -38,6 +38,8 @@ WORKLOADS = {
     "lj_liquid_1048576": dict(n_cells=64, rho=0.8442, T=0.72, seed=2),
     # strongly inhomogeneous: fcc slab (30 % of a 151.2 sigma cube) plus 40 fcc nanoparticles in vacuum
     "slab_nanoparticles_1192114": dict(L=152.0, rho=0.8442, T=0.3, seed=3),
+    # the same structure in the literal 300 sigma cube (supplementary row)
+    "slab_nanoparticles_7239270": dict(L=300.0, rho=0.8442, T=0.3, seed=3),
 }
 
 
@@ -439,6 +441,8 @@ def comparisons(args, sysm, M, stream, value, list_len_hom, hom=None):
                                 "build_ns_per_atom": build_ms_inh * 1e6 / inh.n,
                                 "homogeneous": hom}
         s.close()
+    if args.workload.startswith("lj_liquid") and args.precision == "mixed" and args.list == "full":
+        out["inhomogeneous_literal"] = literal_inhomogeneous_timing(M, stream, value)
     out["force_matching"] = force_matching_timing(M, stream)
     out["batch_ensemble"] = batch_ensemble_timing(stream)
     out["many_body"] = many_body_timing(M, stream)
@@ -546,6 +550,34 @@ def many_body_timing(M, stream, steps=200):
            "mean_list_length": i1["list_entries"] / len(pos)}
     s.close()
     return res
+
+
+def literal_inhomogeneous_timing(M, stream, value_hom, steps=500):
+    """The strongly inhomogeneous structure in the literal 300 sigma cube: the fcc slab fills
+    30 % of the height and 40 particles sit in the vacuum, 7,239,270 atoms, T* = 0.3, 500 steps
+    from the prepared state (supplementary to the 1,192,114-atom row, whose smaller cube has
+    more surface per atom)."""
+    import torch
+    w = make_workload("slab_nanoparticles_7239270")
+    s = M.System(w.n, w.box, precision=M.MD_MIXED, stream=stream.cuda_stream)
+    s.set_state(w.pos, w.vel, w.species)
+    s.forces()
+    torch.cuda.synchronize()
+    i0 = s.info()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps // 100):
+        s.step(100)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    i1 = s.info()
+    s.close()
+    ns = ms * 1e6 / (w.n * steps)
+    return {"workload": "slab_nanoparticles_7239270", "atoms": w.n, "box_sigma": float(w.box[0]),
+            "timesteps": steps, "value": w.n * steps / (ms * 1e-3), "unit": METRIC, "ns_per_atom_timestep": ns,
+            "rebuilds_per_timestep": (i1["n_builds"] - i0["n_builds"]) / steps,
+            "per_atom_cost_vs_homogeneous": ns / (1e9 / value_hom)}
 
 
 def force_matching_timing(M, stream, n_snap=8):
