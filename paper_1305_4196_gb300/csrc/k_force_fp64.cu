@@ -22,14 +22,15 @@ namespace mdgb {
 constexpr int F_THREADS = 256;
 static int g_sm_count = 0;  // SMs of the device, read at initialisation (never during a stream capture)
 
-// 1/x to within about an ulp: the hardware's approximate reciprocal, refined by three
-// Newton-Raphson steps y <- y + y (1 - x y), each of which doubles the correct bits.  For
-// x = 0 the result is not finite, and the force kernels flag the non-finite force.
+// 1/x to within about an ulp: the hardware's approximate reciprocal, refined by two
+// Newton-Raphson steps y <- y + y (1 - x y), each of which doubles the correct bits (a
+// seed good to 2^-14 or better reaches full precision).  For x = 0 the result is not
+// finite, and the force kernels flag the non-finite force.
 __device__ __forceinline__ double rcp_nr(double x) {
     double y;
     asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
+    for (int k = 0; k < 2; ++k) {
         const double e = fma(-x, y, 1.0);
         y = fma(y, e, y);
     }
