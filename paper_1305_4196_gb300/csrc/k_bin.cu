@@ -27,17 +27,25 @@ __global__ void k_bin_assign(DevState s, Geometry g, int32_t* __restrict__ atom_
     for (int d = 0; d < 3; ++d) {
         double x = X[d][i];
         const double L = g.L[d];
-        if (x >= L) {
-            x = __dsub_rn(x, L);
-            I[d][i] += 1;
-            X[d][i] = x;
-        } else if (x < 0.0) {
-            x = __dadd_rn(x, L);
-            I[d][i] -= 1;
-            X[d][i] = x;
-        }
-        if (!(x >= 0.0 && x <= L)) bad |= isfinite(x) ? ERR_ESCAPE : ERR_NONFINITE;
+        // The FP64 pipe is the scarce one on this GPU: most atoms need only the cell,
+        // x * nc / L truncated (two FP64 operations).  The exact comparisons of the wrap run
+        // for the atoms that may need it: negative or non-finite x, and the last cell column
+        // (x * nc / L >= nc - 1 holds for every x >= L).
         int cc = (int)(x * g.inv_w[d]);
+        const long long bits = __double_as_longlong(x);
+        if (bits < 0 || cc >= g.nc[d] - 1 || ((bits >> 52) & 0x7ff) == 0x7ff) {
+            if (x >= L) {
+                x = __dsub_rn(x, L);
+                I[d][i] += 1;
+                X[d][i] = x;
+            } else if (x < 0.0) {
+                x = __dadd_rn(x, L);
+                I[d][i] -= 1;
+                X[d][i] = x;
+            }
+            if (!(x >= 0.0 && x <= L)) bad |= isfinite(x) ? ERR_ESCAPE : ERR_NONFINITE;
+            cc = (int)(x * g.inv_w[d]);
+        }
         cc = cc < 0 ? 0 : (cc >= g.nc[d] ? g.nc[d] - 1 : cc);
         c[d] = cc;
     }
