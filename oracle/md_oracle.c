@@ -25,7 +25,13 @@
  *     equations of motion", Sec. II.A) with a neighbour rebuild whenever some
  *     particle moved more than skin/2 since the last build (or every k steps,
  *     the paper's own protocol, Sec. III);
- *   - serial execution, as the paper's single-thread scheduler (Sec. II.C).
+ *   - serial execution, as the paper's single-thread scheduler (Sec. II.C);
+ *     one extra form, orc_lj_forces_full_omp / orc_run_nve_omp, sums each
+ *     atom's full neighbour set on every host core (one writer per atom, the
+ *     rule of Sec. II.A) for the timed CPU baseline, pinned against the serial
+ *     definition by the CPU tests;
+ *   - the same velocity-Verlet loop around the many-body TB-SMA forces
+ *     (orc_run_nve_tbsma, Sec. III's potential).
  *
  * Readings where the paper is silent (potential, integrator, rebuild rule,
  * strict '<' at both cutoffs, minimum image by rint) are the ones listed in
@@ -36,6 +42,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 /* ---------------------------------------------------------------- helpers */
 
@@ -547,7 +556,8 @@ double orc_kinetic(int64_t n, const double *v, const int32_t *species, const dou
 }
 
 /*
- * Velocity-Verlet run of nsteps with neighbour rebuilds.
+ * Velocity-Verlet run of nsteps with neighbour rebuilds, for any force field
+ * (force(ctx, n, x, box, f, pe) overwrites f and the potential energy *pe).
  *
  * Per step: v += (dt/2m) F;  x += dt v;  rebuild test;  F = F(x);
  * v += (dt/2m) F.  The rebuild test (policy 0) fires when some particle's
@@ -556,25 +566,29 @@ double orc_kinetic(int64_t n, const double *v, const int32_t *species, const dou
  * box length at most, counted in the image array) and records them as the
  * new reference positions.  Forces are the plain definition at every step.
  *
- * x, v, image (N x 3) are updated in place.  Optional per-step outputs
- * (length nsteps): pe_hist, ke_hist.  Returns the number of rebuilds.
+ * x, v, image (N x 3) are updated in place.  f_io (nullable, N x 3): with
+ * f_given != 0 it holds the forces at the starting x and the run uses them
+ * instead of evaluating them once more; on return it holds the forces at the
+ * final x.  Optional per-step outputs (length nsteps): pe_hist, ke_hist.
+ * Returns the number of rebuilds.
  */
-int64_t orc_run_nve(int64_t n, double *x, double *v, int32_t *image, const double *box,
-                    const int32_t *species, int32_t nsp, const double *eps, const double *sig,
-                    const double *rc, const double *mass, double dt, double skin,
-                    int32_t policy, int32_t every_k, int64_t nsteps,
-                    double *pe_hist, double *ke_hist)
+typedef void (*force_eval_fn)(void *ctx, int64_t n, const double *x, const double *box, double *f, double *pe);
+
+static int64_t vv_run(int64_t n, double *x, double *v, int32_t *image, const double *box,
+                      const int32_t *species, int32_t nsp, const double *mass, double dt, double skin,
+                      int32_t policy, int32_t every_k, int64_t nsteps, force_eval_fn force, void *fctx,
+                      double *f_io, int32_t f_given, double *pe_hist, double *ke_hist)
 {
-    double *f = (double *)malloc(sizeof(double) * 3 * (size_t)n);
-    double *xref = (double *)malloc(sizeof(double) * 3 * (size_t)n);
+    double *f = f_io ? f_io : (double *)malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
+    double *xref = (double *)malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
     double *hdtm = (double *)malloc(sizeof(double) * (size_t)nsp);
     for (int32_t s = 0; s < nsp; ++s) hdtm[s] = (0.5 * dt) / mass[s];
     memcpy(xref, x, sizeof(double) * 3 * (size_t)n);
     const double half_skin = 0.5 * skin;
     const double lim2 = half_skin * half_skin;
-    double pe = 0.0, vir[6];
+    double pe = 0.0;
     int64_t rebuilds = 0;
-    orc_lj_forces(n, x, box, species, nsp, eps, sig, rc, 0, f, NULL, &pe, vir);
+    if (!(f_io && f_given)) force(fctx, n, x, box, f, &pe);
     for (int64_t step = 0; step < nsteps; ++step) {
         for (int64_t i = 0; i < n; ++i) {
             double h = hdtm[species ? species[i] : 0];
@@ -609,7 +623,7 @@ int64_t orc_run_nve(int64_t n, double *x, double *v, int32_t *image, const doubl
             memcpy(xref, x, sizeof(double) * 3 * (size_t)n);
             rebuilds++;
         }
-        orc_lj_forces(n, x, box, species, nsp, eps, sig, rc, 0, f, NULL, &pe, vir);
+        force(fctx, n, x, box, f, &pe);
         for (int64_t i = 0; i < n; ++i) {
             double h = hdtm[species ? species[i] : 0];
             for (int k = 0; k < 3; ++k) v[3 * i + k] = v[3 * i + k] + h * f[3 * i + k];
@@ -617,8 +631,182 @@ int64_t orc_run_nve(int64_t n, double *x, double *v, int32_t *image, const doubl
         if (pe_hist) pe_hist[step] = pe;
         if (ke_hist) ke_hist[step] = orc_kinetic(n, v, species, mass);
     }
-    free(f);
+    if (!f_io) free(f);
     free(xref);
     free(hdtm);
     return rebuilds;
+}
+
+/* The Lennard-Jones model of orc_lj_forces as a force field of vv_run. */
+typedef struct {
+    const int32_t *species;
+    int32_t nsp;
+    const double *eps, *sig, *rc;
+} lj_model;
+
+static void lj_eval(void *ctx, int64_t n, const double *x, const double *box, double *f, double *pe)
+{
+    const lj_model *m = (const lj_model *)ctx;
+    double vir[6];
+    orc_lj_forces(n, x, box, m->species, m->nsp, m->eps, m->sig, m->rc, 0, f, NULL, pe, vir);
+}
+
+/* Velocity Verlet with the Lennard-Jones forces of orc_lj_forces (see vv_run). */
+int64_t orc_run_nve(int64_t n, double *x, double *v, int32_t *image, const double *box,
+                    const int32_t *species, int32_t nsp, const double *eps, const double *sig,
+                    const double *rc, const double *mass, double dt, double skin,
+                    int32_t policy, int32_t every_k, int64_t nsteps, double *f_io, int32_t f_given,
+                    double *pe_hist, double *ke_hist)
+{
+    lj_model m = {species, nsp, eps, sig, rc};
+    return vv_run(n, x, v, image, box, species, nsp, mass, dt, skin, policy, every_k, nsteps, lj_eval, &m,
+                  f_io, f_given, pe_hist, ke_hist);
+}
+
+/* The many-body model of orc_tbsma_forces as a force field of vv_run. */
+typedef struct {
+    const double *prm;
+    double rc;
+} tb_model;
+
+static void tb_eval(void *ctx, int64_t n, const double *x, const double *box, double *f, double *pe)
+{
+    const tb_model *m = (const tb_model *)ctx;
+    orc_tbsma_forces(n, x, box, m->prm, m->rc, 0, f, NULL, NULL, pe, NULL);
+}
+
+/* Velocity Verlet with the TB-SMA forces of orc_tbsma_forces, one species of mass `mass`. */
+int64_t orc_run_nve_tbsma(int64_t n, double *x, double *v, int32_t *image, const double *box,
+                          const double *prm, double rc, double mass, double dt, double skin,
+                          int32_t policy, int32_t every_k, int64_t nsteps, double *pe_hist, double *ke_hist)
+{
+    tb_model m = {prm, rc};
+    return vv_run(n, x, v, image, box, NULL, 1, &mass, dt, skin, policy, every_k, nsteps, tb_eval, &m,
+                  NULL, 0, pe_hist, ke_hist);
+}
+
+/* ------------------------------------------------------- all host cores */
+
+/*
+ * Lennard-Jones forces by full neighbour sums on every host core: the force on
+ * atom i is the sum over all j != i closer than their cutoff of the pair
+ * force f_ij, each atom summed by one thread that writes only that atom (the
+ * full-list form of the paper's cell tasks, Sec. II.A: no particle is written
+ * by two threads, so no locks or reductions are needed).  Each pair is thus
+ * evaluated twice, once from each side; the result equals orc_lj_forces up to
+ * the order of the additions.  Linked cells of width >= the largest cutoff
+ * when every dimension holds at least 3, else all pairs.  *pe is the total
+ * potential energy (half of each pair per atom, summed in atom order).
+ * Returns the number of threads used.
+ */
+int32_t orc_lj_forces_full_omp(int64_t n, const double *x, const double *box, const int32_t *species,
+                               int32_t nsp, const double *eps, const double *sig, const double *rc,
+                               double *f, double *pe)
+{
+    const double r = max_cut(nsp, rc);
+    int nc[3];
+    for (int k = 0; k < 3; ++k) {
+        nc[k] = (int)floor(box[k] / r);
+        if (nc[k] < 1) nc[k] = 1;
+    }
+    const int cells = nc[0] >= 3 && nc[1] >= 3 && nc[2] >= 3;
+    const int64_t ncell = cells ? (int64_t)nc[0] * nc[1] * nc[2] : 1;
+    int64_t *head = (int64_t *)malloc(sizeof(int64_t) * ncell);
+    int64_t *next = (int64_t *)malloc(sizeof(int64_t) * (n > 0 ? n : 1));
+    int32_t *cell = (int32_t *)malloc(sizeof(int32_t) * 3 * (n > 0 ? n : 1));
+    double *pe_atom = (double *)malloc(sizeof(double) * (n > 0 ? n : 1));
+    for (int64_t c = 0; c < ncell; ++c) head[c] = -1;
+    for (int64_t i = n - 1; i >= 0; --i) {
+        int cc[3] = {0, 0, 0};
+        if (cells)
+            for (int k = 0; k < 3; ++k) {
+                double w = box[k] / nc[k];
+                double xk = x[3 * i + k] - box[k] * floor(x[3 * i + k] / box[k]);
+                int c = (int)floor(xk / w);
+                if (c < 0) c = 0;
+                if (c >= nc[k]) c = nc[k] - 1;
+                cc[k] = c;
+            }
+        for (int k = 0; k < 3; ++k) cell[3 * i + k] = cc[k];
+        int64_t c = ((int64_t)cc[2] * nc[1] + cc[1]) * nc[0] + cc[0];
+        if (!cells) c = 0;
+        next[i] = head[c];
+        head[c] = i;
+    }
+    int32_t threads = 1;
+#pragma omp parallel
+    {
+#ifdef _OPENMP
+#pragma omp single
+        threads = (int32_t)omp_get_num_threads();
+#endif
+#pragma omp for schedule(dynamic, 256)
+        for (int64_t i = 0; i < n; ++i) {
+            double fi[3] = {0.0, 0.0, 0.0}, ui = 0.0, d[3];
+            const int32_t si = species ? species[i] : 0;
+            const int span = cells ? 1 : 0;
+            for (int oz = -span; oz <= span; ++oz)
+                for (int oy = -span; oy <= span; ++oy)
+                    for (int ox = -span; ox <= span; ++ox) {
+                        int64_t c = 0;
+                        if (cells) {
+                            int cx = (cell[3 * i + 0] + ox + nc[0]) % nc[0];
+                            int cy = (cell[3 * i + 1] + oy + nc[1]) % nc[1];
+                            int cz = (cell[3 * i + 2] + oz + nc[2]) % nc[2];
+                            c = ((int64_t)cz * nc[1] + cy) * nc[0] + cx;
+                        }
+                        for (int64_t j = head[c]; j >= 0; j = next[j]) {
+                            if (j == i) continue;
+                            double r2 = pair_disp(x, i, j, box, d);
+                            int32_t t = si * nsp + (species ? species[j] : 0);
+                            if (!(r2 < rc[t] * rc[t])) continue;
+                            double sr2 = (sig[t] * sig[t]) / r2;
+                            double s6 = sr2 * sr2 * sr2;
+                            double fr = 24.0 * eps[t] * (2.0 * s6 * s6 - s6) / r2;
+                            for (int k = 0; k < 3; ++k) fi[k] += fr * d[k];
+                            ui += 0.5 * (4.0 * eps[t] * (s6 * s6 - s6));
+                        }
+                    }
+            for (int k = 0; k < 3; ++k) f[3 * i + k] = fi[k];
+            pe_atom[i] = ui;
+        }
+    }
+    if (pe) {
+        csum acc = {0.0, 0.0};
+        for (int64_t i = 0; i < n; ++i) csum_add(&acc, pe_atom[i]);
+        *pe = csum_get(&acc);
+    }
+    free(head);
+    free(next);
+    free(cell);
+    free(pe_atom);
+    return threads;
+}
+
+static void lj_eval_omp(void *ctx, int64_t n, const double *x, const double *box, double *f, double *pe)
+{
+    const lj_model *m = (const lj_model *)ctx;
+    orc_lj_forces_full_omp(n, x, box, m->species, m->nsp, m->eps, m->sig, m->rc, f, pe);
+}
+
+/* Velocity Verlet with the all-cores full-sum forces of orc_lj_forces_full_omp (see vv_run). */
+int64_t orc_run_nve_omp(int64_t n, double *x, double *v, int32_t *image, const double *box,
+                        const int32_t *species, int32_t nsp, const double *eps, const double *sig,
+                        const double *rc, const double *mass, double dt, double skin,
+                        int32_t policy, int32_t every_k, int64_t nsteps, double *f_io, int32_t f_given,
+                        double *pe_hist, double *ke_hist)
+{
+    lj_model m = {species, nsp, eps, sig, rc};
+    return vv_run(n, x, v, image, box, species, nsp, mass, dt, skin, policy, every_k, nsteps, lj_eval_omp, &m,
+                  f_io, f_given, pe_hist, ke_hist);
+}
+
+/* Threads an OpenMP region of this library uses (1 when built without OpenMP). */
+int32_t orc_threads(void)
+{
+#ifdef _OPENMP
+    return (int32_t)omp_get_max_threads();
+#else
+    return 1;
+#endif
 }

@@ -34,9 +34,11 @@ def build(force: bool = False) -> str:
             and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
         return _LIB_PATH
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
-           _SRC, "-o", tmp, "-lm"]
-    subprocess.run(cmd, check=True)
+    base = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared"]
+    # OpenMP for the all-cores baseline form; without it the same code runs on one thread
+    r = subprocess.run(base + ["-fopenmp", _SRC, "-o", tmp, "-lm"], capture_output=True, text=True)
+    if r.returncode != 0:
+        subprocess.run(base + [_SRC, "-o", tmp, "-lm"], check=True)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -71,10 +73,24 @@ def _configure(lib):
     lib.orc_tbsma_forces.restype = None
     lib.orc_tbsma_forces.argtypes = [C.c_int64, _dp, _dp, _dp, C.c_double, C.c_int, _dp, C.c_void_p, C.c_void_p,
                                      C.c_void_p, C.c_void_p]
-    lib.orc_run_nve.restype = C.c_int64
-    lib.orc_run_nve.argtypes = [C.c_int64, _dp, _dp, _ip, _dp, C.c_void_p, C.c_int32, _dp, _dp, _dp,
-                                _dp, C.c_double, C.c_double, C.c_int32, C.c_int32, C.c_int64,
-                                C.c_void_p, C.c_void_p]
+    for name in ("orc_run_nve", "orc_run_nve_omp"):
+        fn = getattr(lib, name, None)
+        if fn is None:
+            continue
+        fn.restype = C.c_int64
+        fn.argtypes = [C.c_int64, _dp, _dp, _ip, _dp, C.c_void_p, C.c_int32, _dp, _dp, _dp,
+                       _dp, C.c_double, C.c_double, C.c_int32, C.c_int32, C.c_int64,
+                       C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]
+    if hasattr(lib, "orc_run_nve_tbsma"):
+        lib.orc_run_nve_tbsma.restype = C.c_int64
+        lib.orc_run_nve_tbsma.argtypes = [C.c_int64, _dp, _dp, _ip, _dp, _dp, C.c_double, C.c_double, C.c_double,
+                                          C.c_double, C.c_int32, C.c_int32, C.c_int64, C.c_void_p, C.c_void_p]
+    if hasattr(lib, "orc_lj_forces_full_omp"):
+        lib.orc_lj_forces_full_omp.restype = C.c_int32
+        lib.orc_lj_forces_full_omp.argtypes = [C.c_int64, _dp, _dp, C.c_void_p, C.c_int32, _dp, _dp, _dp, _dp,
+                                               C.c_void_p]
+        lib.orc_threads.restype = C.c_int32
+        lib.orc_threads.argtypes = []
     return lib
 
 
@@ -282,8 +298,12 @@ def kinetic(vel, params: LJParams, species=None) -> float:
 
 
 def run_nve(pos, vel, box, params: LJParams, dt, skin, nsteps, species=None, image=None,
-            policy=0, every_k=10, history=False):
-    """Velocity-Verlet run; returns dict(pos, vel, image, rebuilds[, pe, ke])."""
+            policy=0, every_k=10, history=False, forces=None, all_cores=False):
+    """Velocity-Verlet run; returns dict(pos, vel, image, rebuilds, forces[, pe, ke]).
+
+    forces: the forces at pos (from an earlier run's result), used instead of evaluating
+    them again, so that a run of k steps evaluates the forces exactly k times.
+    all_cores: the full-sum forces of orc_lj_forces_full_omp on every host core."""
     lib = _load()
     x = _c(pos, np.float64).copy()
     v = _c(vel, np.float64).copy()
@@ -293,12 +313,57 @@ def run_nve(pos, vel, box, params: LJParams, dt, skin, nsteps, species=None, ima
     sp = _sp(species)
     pe_h = np.zeros(nsteps) if history else None
     ke_h = np.zeros(nsteps) if history else None
-    nreb = lib.orc_run_nve(n, x.ravel(), v.ravel(), img.ravel(), box, sp[1] if sp else None, params.nsp,
-                           params.eps.ravel(), params.sig.ravel(), params.rc.ravel(), params.mass,
-                           float(dt), float(skin), int(policy), int(every_k), int(nsteps),
-                           pe_h.ctypes.data if history else None, ke_h.ctypes.data if history else None)
+    f = np.zeros((n, 3)) if forces is None else _c(forces, np.float64).copy()
+    fn = lib.orc_run_nve_omp if all_cores else lib.orc_run_nve
+    nreb = fn(n, x.ravel(), v.ravel(), img.ravel(), box, sp[1] if sp else None, params.nsp,
+              params.eps.ravel(), params.sig.ravel(), params.rc.ravel(), params.mass,
+              float(dt), float(skin), int(policy), int(every_k), int(nsteps),
+              f.ctypes.data, 0 if forces is None else 1,
+              pe_h.ctypes.data if history else None, ke_h.ctypes.data if history else None)
+    out = dict(pos=x, vel=v, image=img, rebuilds=int(nreb), forces=f)
+    if history:
+        out["pe"] = pe_h
+        out["ke"] = ke_h
+    return out
+
+
+def run_nve_tbsma(pos, vel, box, params: "TBSMAParams", mass, dt, skin, nsteps, image=None,
+                  policy=0, every_k=10, history=False):
+    """Velocity-Verlet run with the many-body TB-SMA forces (one species of the given mass);
+    returns dict(pos, vel, image, rebuilds[, pe, ke])."""
+    lib = _load()
+    x = _c(pos, np.float64).copy()
+    v = _c(vel, np.float64).copy()
+    n = x.shape[0]
+    img = np.zeros((n, 3), dtype=np.int32) if image is None else _c(image, np.int32).copy()
+    box = _c(box, np.float64)
+    pe_h = np.zeros(nsteps) if history else None
+    ke_h = np.zeros(nsteps) if history else None
+    nreb = lib.orc_run_nve_tbsma(n, x.ravel(), v.ravel(), img.ravel(), box, params.array(), float(params.rc),
+                                 float(mass), float(dt), float(skin), int(policy), int(every_k), int(nsteps),
+                                 pe_h.ctypes.data if history else None, ke_h.ctypes.data if history else None)
     out = dict(pos=x, vel=v, image=img, rebuilds=int(nreb))
     if history:
         out["pe"] = pe_h
         out["ke"] = ke_h
     return out
+
+
+def lj_forces_all_cores(pos, box, params: LJParams, species=None):
+    """Forces and potential energy by full neighbour sums on every host core
+    (orc_lj_forces_full_omp); returns (forces, pe, threads used)."""
+    lib = _load()
+    pos = _c(pos, np.float64)
+    n = pos.shape[0]
+    box = _c(box, np.float64)
+    f = np.zeros((n, 3))
+    pe = np.zeros(1)
+    sp = _sp(species)
+    th = lib.orc_lj_forces_full_omp(n, pos.ravel(), box, sp[1] if sp else None, params.nsp, params.eps.ravel(),
+                                    params.sig.ravel(), params.rc.ravel(), f.ravel(), pe.ctypes.data)
+    return f, float(pe[0]), int(th)
+
+
+def threads() -> int:
+    """Host threads the all-cores form uses."""
+    return int(_load().orc_threads())

@@ -166,3 +166,36 @@ def test_backward_cutoff_decided_by_the_definition():
     gx_ref, ge_ref, gs_ref = O.lj_force_grad(pos, box, P, G, sp)
     assert np.abs(gx - gx_ref).max() <= 2e-5 * np.abs(gx_ref).max()
     assert abs(ge[0, 0] - ge_ref[0, 0]) <= 2e-5 * abs(ge_ref[0, 0])
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_backward_at_the_force_matching_size(precision):
+    """The force-matching workload at its stated size, in the launch configuration the
+    benchmark times: 32,000 Kob-Andersen atoms (20^3 fcc cells at rho* = 1.2, L = 29.88),
+    lists sized for cutoffs 10 % above 2.5 sigma_ab (8 cells per side, so 64 blocks whose
+    4x4x4-cell tiles are smaller than the box), parameters perturbed by 10 %; dL/dx,
+    dL/deps and dL/dsigma for a random upstream gradient, and dE/deps, dE/dsigma, element
+    by element against the oracle's analytic gradient at the same bars as above."""
+    s, sp = ka_snapshot(n_cells=20, seed=101)
+    eps1 = KA_EPS * np.array([[1.1, 0.9], [0.9, 1.1]])
+    sig1 = KA_SIG * np.array([[0.9, 1.1], [1.1, 0.9]])
+    sysm = M.System(s.n, s.box, r_cut=2.5 * 1.1, skin=0.3, eps=KA_EPS, sigma=KA_SIG, mass=[1.0, 1.0],
+                    precision=PREC[precision], rcut=2.5 * KA_SIG * 1.1)
+    sysm.set_state(np.ascontiguousarray(s.pos), np.zeros_like(s.pos), sp)
+    sysm.set_params(eps1, sig1, 2.5 * sig1)
+    assert sysm.info()["ncell"] == [8, 8, 8]
+    P = O.LJParams(eps1, sig1, 2.5 * sig1, [1.0, 1.0])
+    G = np.random.default_rng(7).normal(size=(s.n, 3))
+    gx, ge, gs = sysm.forces_backward(G)
+    gx_ref, ge_ref, gs_ref = O.lj_force_grad(s.pos, s.box, P, G, sp)
+    assert vec_error(gx, gx_ref) <= TOL[precision]
+    for t, tref in [(ge, ge_ref), (gs, gs_ref)]:
+        assert np.abs(t - tref).max() <= TOL[precision] * np.abs(tref).max()
+    de, ds = sysm.energy_param_grad()
+    de_ref, ds_ref = O.lj_energy_param_grad(s.pos, s.box, P, sp)
+    tol = 1e-11 if precision == "fp64" else 1e-5
+    assert np.abs(de - de_ref).max() <= tol * np.abs(de_ref).max()
+    assert np.abs(ds - ds_ref).max() <= tol * np.abs(ds_ref).max()
+    F = sysm.forces()
+    Fref = O.lj_forces(s.pos, s.box, P, sp)[0]
+    assert vec_error(F, Fref) <= (1e-12 if precision == "fp64" else 2e-5)

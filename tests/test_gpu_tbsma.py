@@ -5,8 +5,8 @@ Inputs: fcc copper at its lattice constant 3.615 A with Gaussian displacements o
 kT = 0.02585 eV (eV, Angstrom, amu; the time unit is 10.18 fs); isolated pairs at
 r_cut (1 -/+ 1e-7).  Bars as for the pair potential in mixed precision: forces per atom
 within 2e-5 of max(|F_i|, F_rms), energy and virial within 1e-6 relative, bit-identical
-forces for any input order; a 20-step trajectory within 1e-6 A of velocity Verlet on the
-oracle's forces.
+forces for any input order; a 20-step trajectory within 1e-6 A of the oracle's many-body
+velocity-Verlet run.
 """
 import numpy as np
 import pytest
@@ -91,15 +91,10 @@ def test_trajectory_follows_oracle_velocity_verlet():
     s = make(pos, vel, box, dt=dt)
     s.step(steps)
     p_gpu, v_gpu, img = s.get_state()
-    x, v = pos.copy(), vel.copy()
-    F = O.tbsma_forces(x, box, CU)[0]
-    for _ in range(steps):
-        v = v + (0.5 * dt / MASS) * F
-        x = x + dt * v
-        F = O.tbsma_forces(x, box, CU)[0]  # minimum image: unwrapped positions are fine
-        v = v + (0.5 * dt / MASS) * F
+    ref = O.run_nve_tbsma(pos, vel, box, CU, MASS, dt, SKIN, steps)
+    x = ref["pos"] + ref["image"] * box
     assert np.abs(p_gpu + img * box - x).max() <= 1e-6
-    assert np.abs(v_gpu - v).max() <= 1e-6 * np.abs(v).max()
+    assert np.abs(v_gpu - ref["vel"]).max() <= 1e-6 * np.abs(ref["vel"]).max()
 
 
 def test_energy_drift_small_over_1000_steps():

@@ -338,14 +338,67 @@ def test_velocity_verlet_time_reversible():
 
 
 def test_nve_energy_bounded_config1():
-    """4,000-atom fcc start at T*=0.72: |E(t)-E(0)|/N stays small over 100 steps."""
+    """4,000-atom fcc start at T*=0.72, 100 steps.  The potential is cut without a shift,
+    so every pair crossing r_cut changes E by u(r_cut) = 4 (2.5^-12 - 2.5^-6): the energy
+    of the shifted potential, E - u(r_cut) * (pairs inside r_cut), is what velocity Verlet
+    conserves to O(dt^2).  Measured here: |dE|/N reaches 5.9e-3 (the melting lattice gains
+    about 1,400 interacting pairs), while the shifted energy moves by at most 1.8e-4 per
+    atom at the checked steps.  Bars: 8e-3 and 5e-4 per atom (margins 1.35x and 2.7x)."""
     s = W.lj_fcc(10, seed=1)
     P = O.LJParams.single()
     e0 = O.lj_forces(s.pos, s.box, P)[1] + O.kinetic(s.vel, P)
+    n0 = len(O.neighbor_pairs(s.pos, s.box, 2.5))
+    u_rc = 4.0 * (2.5 ** -12 - 2.5 ** -6)
     r = O.run_nve(s.pos, s.vel, s.box, P, 0.005, 0.3, 100, history=True)
     drift = np.abs(r["pe"] + r["ke"] - e0).max() / s.n
-    assert drift < 0.02
+    assert drift < 8e-3
     assert r["rebuilds"] >= 1
+    x, v, img, f = s.pos, s.vel, None, None
+    for steps in (25, 25, 50):  # the same trajectory, checked at steps 25, 50 and 100
+        q = O.run_nve(x, v, s.box, P, 0.005, 0.3, steps, image=img, forces=f, history=True)
+        x, v, img, f = q["pos"], q["vel"], q["image"], q["forces"]
+        dn = len(O.neighbor_pairs(x, s.box, 2.5)) - n0
+        shifted = (q["pe"][-1] + q["ke"][-1] - e0 - u_rc * dn) / s.n
+        assert abs(shifted) < 5e-4, (steps, shifted)
+
+
+def test_all_cores_form_equals_serial_definition():
+    """The all-cores full-sum forces (each atom summed from both sides of its pairs) equal
+    the serial Newton-3 definition up to rounding order: one and two species, linked cells
+    and the all-pairs path of a small box; a 20-step run takes the same trajectory."""
+    for n_cells, species in ((6, False), (6, True), (2, False)):
+        s = W.lj_fcc(n_cells, seed=3 + n_cells, jitter=0.05)
+        if species:
+            sp = W.species_shuffle(s.n, 0.2, 7)
+            P = O.LJParams([[1.0, 1.5], [1.5, 0.5]], [[1.0, 0.8], [0.8, 0.88]],
+                           [[2.5, 2.0], [2.0, 2.2]], [1.0, 1.0])
+        else:
+            sp, P = None, O.LJParams.single(rc=2.5 if n_cells > 2 else 1.6)
+        F, pe, _ = O.lj_forces(s.pos, s.box, P, sp)
+        Fa, pea, th = O.lj_forces_all_cores(s.pos, s.box, P, sp)
+        frms = np.sqrt((F ** 2).sum(1).mean())
+        assert th >= 1
+        assert np.abs(Fa - F).max() <= 1e-13 * frms
+        assert abs(pea - pe) <= 1e-13 * abs(pe)
+    s = W.lj_fcc(6, seed=11)
+    P = O.LJParams.single()
+    a = O.run_nve(s.pos, s.vel, s.box, P, 0.005, 0.3, 20)
+    b = O.run_nve(s.pos, s.vel, s.box, P, 0.005, 0.3, 20, all_cores=True)
+    assert np.abs(a["pos"] + a["image"] * s.box - b["pos"] - b["image"] * s.box).max() < 1e-11
+    assert a["rebuilds"] == b["rebuilds"]
+
+
+def test_run_continues_from_given_forces():
+    """A run of 10 + 10 steps that hands the forces over evaluates each force once per
+    step and follows the 20-step run (to the rounding of a re-wrapped position)."""
+    s = W.lj_fcc(5, seed=12)
+    P = O.LJParams.single()
+    whole = O.run_nve(s.pos, s.vel, s.box, P, 0.005, 0.3, 20)
+    a = O.run_nve(s.pos, s.vel, s.box, P, 0.005, 0.3, 10)
+    b = O.run_nve(a["pos"], a["vel"], s.box, P, 0.005, 0.3, 10, image=a["image"], forces=a["forces"])
+    assert np.abs(b["pos"] + b["image"] * s.box - whole["pos"] - whole["image"] * s.box).max() < 1e-12
+    assert np.abs(b["forces"] - whole["forces"]).max() < 1e-9
+    assert np.abs(b["forces"] - O.lj_forces(b["pos"], s.box, P)[0]).max() == 0.0
 
 
 def test_skin_half_rebuild_rule_and_wrap():
@@ -571,3 +624,40 @@ def test_tbsma_invariances_and_brute_force():
     far = np.vstack([pos, [1.5 * box]])
     F4, _, _, rho4, ea4 = O.tbsma_forces(far, big, CU, per_atom=True)
     assert rho4[-1] == 0.0 and ea4[-1] == 0.0 and np.all(F4[-1] == 0.0)
+
+
+def _cu_cluster():
+    """13 copper atoms: one fcc site and its 12 nearest neighbours, far from any image, so
+    no pair ever reaches r_cut (the largest distance is 2 r0 = 5.11 A)."""
+    pos, box = W.fcc_lattice(2, 2, 2, 3.615)
+    c = pos[np.argmin(((pos - box / 2) ** 2).sum(1))]
+    d = W.wrap(pos - c + box / 2, box) - box / 2
+    cl = d[np.sqrt((d ** 2).sum(1)) < 2.7] + 50.0
+    assert len(cl) == 13
+    vel = W.thermal_velocities(np.full(13, 63.546), 0.05, 31, stream=1)
+    return cl, vel, np.array([100.0, 100.0, 100.0])
+
+
+def test_tbsma_velocity_verlet_is_second_order():
+    """The many-body run conserves energy to O(dt^2): halving dt cuts the largest energy
+    error over 8 time units (81 fs) by about 4 (measured 4.01)."""
+    cl, vel, box = _cu_cluster()
+    errs = []
+    for dt in (0.2, 0.1):
+        r = O.run_nve_tbsma(cl, vel, box, CU, 63.546, dt, 1.0, int(round(8.0 / dt)), history=True)
+        e0 = O.tbsma_forces(cl, box, CU)[1] + 0.5 * 63.546 * (vel ** 2).sum()
+        errs.append(np.abs(r["pe"] + r["ke"] - e0).max())
+    assert 3.3 < errs[0] / errs[1] < 4.8, errs
+    assert errs[1] < 1e-3 * 0.05 * 13  # far below the kinetic energy scale
+
+
+def test_tbsma_velocity_verlet_time_reversible():
+    """30 steps forward, velocities negated, 30 back: the thermal periodic crystal returns
+    to its start (measured 4e-15 A), through a rebuild and its wrap."""
+    pos, box = _cu_crystal(n_cells=4, jitter=0.08, seed=3)
+    vel = W.thermal_velocities(np.full(len(pos), 63.546), 0.02585, 3, stream=1)
+    a = O.run_nve_tbsma(pos, vel, box, CU, 63.546, 0.1, 0.4, 30)
+    b = O.run_nve_tbsma(a["pos"], -a["vel"], box, CU, 63.546, 0.1, 0.4, 30, image=a["image"])
+    assert a["rebuilds"] >= 1
+    assert np.abs(b["pos"] + b["image"] * box - pos).max() < 1e-9
+    assert np.abs(b["vel"] + vel).max() < 1e-9 * np.abs(vel).max()
