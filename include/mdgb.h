@@ -285,9 +285,10 @@ int md_colour_conflicts(md_system *s, int32_t n_phases, int64_t *conflicts);
 
 /*
  * Kinetic energy 1/2 sum m v^2 of n atoms, for callers that cannot allocate
- * device memory at the moment they need it - e.g. code that runs while a CUDA
- * stream is being captured into a graph (no cudaMalloc there), or a host that
- * gives this library a fixed memory budget and locks allocation afterwards.
+ * device memory at the moment they need it - e.g. a host that gives this library
+ * a fixed memory budget and locks allocation afterwards (an embedding runtime
+ * that owns all device memory through its own pool), or a real-time loop that
+ * must not call cudaMalloc, which can synchronise the device.
  * The paper has no counterpart of this call: it is a deployment variant of the
  * deterministic FP64 two-pass reduction md_energy_virial uses.  It needs no
  * md_system and allocates nothing: its partial sums live in a file-scope static
@@ -296,9 +297,13 @@ int md_colour_conflicts(md_system *s, int32_t n_phases, int64_t *conflicts);
  *   vel      device, n x 3 doubles (any order); species: device, n int32, or NULL (all 0)
  *   mass     host, n_species doubles (1 <= n_species <= 4), copied by value
  *   ke_out   device, one double, written on `stream` (cudaStream_t, NULL = legacy default)
+ * Every species id must lie in [0, n_species).  The ids are device data, so they
+ * are checked on the device: an id outside that range contributes no mass and
+ * makes *ke_out NaN (no memory outside mass[0 .. n_species) is read).
  * Limits and errors: MD_ERR_ARG if n < 0 or n > 2^30 (the largest size it
  * accepts), if ke_out or mass is NULL, or if n_species is out of range; nothing
- * is launched then.  MD_ERR_CUDA if the launch fails.
+ * is launched then.  MD_ERR_CUDA if a launch fails (the status of this call's
+ * own launches; an error pending from earlier work is left as it is).
  * The first call on each device looks up the array's device address with that
  * device current (cudaGetSymbolAddress); make that first call before any stream
  * capture.  Every call overwrites the whole partial-sum array it uses, so nothing

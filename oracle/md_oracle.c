@@ -363,6 +363,7 @@ typedef struct {
     const double *G;
     double *gx;
     csum *geps, *gsig, *eeps, *esig; /* per unordered species pair, index a * nsp + b with a <= b */
+    int absmode;                     /* sum |term| instead of term for geps, gsig (a sum's scale) */
 } lj_grad_acc;
 
 static void lj_grad_pair(void *ctx, int64_t i, int64_t j, const double d[3], double r2)
@@ -391,8 +392,10 @@ static void lj_grad_pair(void *ctx, int64_t i, int64_t j, const double d[3], dou
             a->gx[3 * i + k] += h;
             a->gx[3 * j + k] -= h;
         }
-        csum_add(&a->geps[u], wd * (g / e));
-        csum_add(&a->gsig[u], wd * (144.0 * e * (4.0 * s6 * s6 - s6) / (s * r2)));
+        double te = wd * (g / e);
+        double ts = wd * (144.0 * e * (4.0 * s6 * s6 - s6) / (s * r2));
+        csum_add(&a->geps[u], a->absmode ? fabs(te) : te);
+        csum_add(&a->gsig[u], a->absmode ? fabs(ts) : ts);
     }
     if (a->eeps) {
         csum_add(&a->eeps[u], 4.0 * (s6 * s6 - s6));
@@ -400,14 +403,15 @@ static void lj_grad_pair(void *ctx, int64_t i, int64_t j, const double d[3], dou
     }
 }
 
-void orc_lj_grad(int64_t n, const double *x, const double *box, const int32_t *species, int32_t nsp,
-                 const double *eps, const double *sig, const double *rc, const double *G, double *gx,
-                 double *geps, double *gsig, double *dE_deps, double *dE_dsig)
+static void lj_grad_run(int64_t n, const double *x, const double *box, const int32_t *species, int32_t nsp,
+                        const double *eps, const double *sig, const double *rc, const double *G, double *gx,
+                        double *geps, double *gsig, double *dE_deps, double *dE_dsig, int absmode)
 {
     csum acc[4][64];
     memset(acc, 0, sizeof(acc));
     lj_grad_acc a;
     memset(&a, 0, sizeof(a));
+    a.absmode = absmode;
     a.nsp = nsp;
     a.eps = eps;
     a.sig = sig;
@@ -435,6 +439,25 @@ void orc_lj_grad(int64_t n, const double *x, const double *box, const int32_t *s
                 dE_dsig[p * nsp + q] = csum_get(&acc[3][u]);
             }
         }
+}
+
+void orc_lj_grad(int64_t n, const double *x, const double *box, const int32_t *species, int32_t nsp,
+                 const double *eps, const double *sig, const double *rc, const double *G, double *gx,
+                 double *geps, double *gsig, double *dE_deps, double *dE_dsig)
+{
+    lj_grad_run(n, x, box, species, nsp, eps, sig, rc, G, gx, geps, gsig, dE_deps, dE_dsig, 0);
+}
+
+/*
+ * The scale of the parameter sums of orc_lj_grad: sum over the pairs of |term| for
+ * dL/deps_ab and dL/dsig_ab (same tables).  A sum whose terms each carry a relative
+ * error e is off by at most e times this scale, however much its terms cancel.
+ */
+void orc_lj_grad_abs(int64_t n, const double *x, const double *box, const int32_t *species, int32_t nsp,
+                     const double *eps, const double *sig, const double *rc, const double *G, double *gx_scratch,
+                     double *geps_abs, double *gsig_abs)
+{
+    lj_grad_run(n, x, box, species, nsp, eps, sig, rc, G, gx_scratch, geps_abs, gsig_abs, NULL, NULL, 1);
 }
 
 /* ------------------------------------------------------- many-body (TB-SMA) */

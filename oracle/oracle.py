@@ -70,6 +70,10 @@ def _configure(lib):
     lib.orc_lj_grad.restype = None
     lib.orc_lj_grad.argtypes = [C.c_int64, _dp, _dp, C.c_void_p, C.c_int32, _dp, _dp, _dp, C.c_void_p,
                                 C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+    if hasattr(lib, "orc_lj_grad_abs"):
+        lib.orc_lj_grad_abs.restype = None
+        lib.orc_lj_grad_abs.argtypes = [C.c_int64, _dp, _dp, C.c_void_p, C.c_int32, _dp, _dp, _dp, C.c_void_p,
+                                        C.c_void_p, C.c_void_p, C.c_void_p]
     lib.orc_tbsma_forces.restype = None
     lib.orc_tbsma_forces.argtypes = [C.c_int64, _dp, _dp, _dp, C.c_double, C.c_int, _dp, C.c_void_p, C.c_void_p,
                                      C.c_void_p, C.c_void_p]
@@ -239,6 +243,24 @@ def lj_force_grad(pos, box, params: LJParams, G, species=None):
     lib.orc_lj_grad(n, pos.ravel(), box, sp[1] if sp else None, params.nsp, params.eps.ravel(), params.sig.ravel(),
                     params.rc.ravel(), G.ctypes.data, gx.ctypes.data, ge.ctypes.data, gs.ctypes.data, None, None)
     return gx, ge, gs
+
+
+def lj_force_grad_scale(pos, box, params: LJParams, G, species=None):
+    """Sum over the pairs of |term| of dL/deps and dL/dsig (the tables of lj_force_grad):
+    the scale that bounds the error of those sums when every term has a relative error."""
+    lib = _load()
+    pos = _c(pos, np.float64)
+    box = _c(box, np.float64)
+    G = _c(G, np.float64)
+    n = pos.shape[0]
+    scratch = np.zeros((n, 3))
+    ge = np.zeros((params.nsp, params.nsp))
+    gs = np.zeros((params.nsp, params.nsp))
+    sp = _sp(species)
+    lib.orc_lj_grad_abs(n, pos.ravel(), box, sp[1] if sp else None, params.nsp, params.eps.ravel(),
+                        params.sig.ravel(), params.rc.ravel(), G.ctypes.data, scratch.ctypes.data, ge.ctypes.data,
+                        gs.ctypes.data)
+    return ge, gs
 
 
 def lj_energy_param_grad(pos, box, params: LJParams, species=None):

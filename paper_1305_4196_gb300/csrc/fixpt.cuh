@@ -41,25 +41,51 @@ __device__ __forceinline__ void fix_sub(FixAcc& acc, float fs2, float d) {
     acc.lo += __float_as_uint(t2);
 }
 
-// slow exact path for |fs2 * d| >= 2^22 (pair force component >= 2048 eps/sigma): add
-// rint(fs2 * d * 2^21) in the same two-part form (FP64 product of two floats is exact).
-static __device__ __noinline__ uint2 fix_wide_terms(float fs2, float d, uint32_t* err) {
-    double a = (double)fs2 * (double)d * 2097152.0;
-    if (!(fabs(a) < 9.0e15)) {
-        atomicOr(err, ERR_NONFINITE);
-        a = 0.0;
-    }
-    long long q = __double2ll_rn(a);
-    long long qh = q >> 21;
-    return make_uint2(__float_as_uint(MAGIC) + (unsigned)(int)qh,
-                      __float_as_uint(MAGIC) + (unsigned)(int)(q - qh * 2097152LL));
+// The same term as one 64-bit integer rint(fs2 * d * 2^21) (units of 2^-32): the two-part
+// split of fix_add recombined, so a sum of these equals fix_final of the fix_add sums
+// whenever those do not wrap.  Valid for |fs2 * d| < 2^22.
+__device__ __forceinline__ long long fix_term(float fs2, float d) {
+    const float t1 = __fmaf_rn(fs2, d, MAGIC);
+    const float h = __fsub_rn(t1, MAGIC);
+    const float r = __fmaf_rn(fs2, d, -h);
+    const float t2 = __fmaf_rn(r, TWO21, MAGIC);
+    return (long long)(int)(__float_as_uint(t1) - __float_as_uint(MAGIC)) * 2097152LL +
+           (long long)(int)(__float_as_uint(t2) - __float_as_uint(MAGIC));
 }
 
-__device__ __forceinline__ void fix_add_wide(FixAcc& acc, float fs2, float d, uint32_t* err) {
-    const uint2 t = fix_wide_terms(fs2, d, err);
-    acc.hi += t.x;
-    acc.lo += t.y;
+// Terms beyond the split (|fs2 * d| >= 2^22, a pair force component of 2048 eps/sigma or
+// more): rint(fs2 * d * 2^21) in FP64, exact because the product of two floats is.  The
+// sums take terms below FIX_WIDE_LIMIT = 2^54 units (a component below 2^22 = 4.2e6
+// eps/sigma; Lennard-Jones atoms closer than about 0.42 sigma exceed it); a larger or
+// non-finite term flags ERR_NONFINITE and adds nothing.  With at most FIX_WIDE_MAX_TERMS
+// such terms per atom (more also flag ERR_NONFINITE) and every other term below 2^43
+// units, an atom's 64-bit total cannot wrap.
+constexpr double FIX_WIDE_LIMIT = 18014398509481984.0;  // 2^54
+constexpr int FIX_WIDE_MAX_TERMS = 255;
+
+static __device__ __noinline__ long long fix_term_wide(float fs2, float d, uint32_t* err) {
+    const double a = (double)fs2 * (double)d * 2097152.0;
+    if (!(fabs(a) < FIX_WIDE_LIMIT)) {
+        atomicOr(err, ERR_NONFINITE);
+        return 0;
+    }
+    return __double2ll_rn(a);
 }
+
+// Exact 64-bit sum of one component for the paths that take terms one at a time (the
+// exact finish of an atom, the scalar batch pass): normal terms through fix_term, the
+// others through fix_term_wide, whose count is checked by fix_wide_count_ok.
+__device__ __forceinline__ long long fix_term_any(float fs2, float d, float fs2_max, uint32_t* err) {
+    return fabsf(fs2) < fs2_max ? fix_term(fs2, d) : fix_term_wide(fs2, d, err);
+}
+
+__device__ __forceinline__ void fix_wide_count_ok(int nwide, uint32_t* err) {
+    if (nwide > FIX_WIDE_MAX_TERMS) atomicOr(err, ERR_NONFINITE);
+}
+
+// A sum of fix_add terms is exact while its high part stays inside int32: below
+// FIX_SPLIT_MAX_TERMS terms (each high part is below 2^22 in magnitude).
+constexpr int FIX_SPLIT_MAX_TERMS = 511;
 
 __device__ __forceinline__ long long fix_final(const FixAcc& acc, int nterms) {
     const int hi = (int)(acc.hi - (unsigned)nterms * __float_as_uint(MAGIC));

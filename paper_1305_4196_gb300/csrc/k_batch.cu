@@ -156,7 +156,7 @@ __device__ __forceinline__ int wrap_cell(int c, int nc) { return c < 0 ? c + nc 
 
 // Exact force on the atom of slot p, one candidate at a time: a pair whose FP32 r^2 lies in
 // the band around r_cut^2 is decided in FP64 by the definition, a large term is rounded in
-// FP64 (fix_wide_terms); every other term is the one the packed loop would add.
+// FP64 (fix_term_wide); every other term is the one the packed loop would add.
 template <bool ENERGY>
 __device__ __noinline__ void batch_force_exact(const BatchSys& y, const BatchState& st, const PairTable& pt,
                                                float fs2_max, const Smem& sm, float* __restrict__ pe_out, int p) {
@@ -167,8 +167,8 @@ __device__ __noinline__ void batch_force_exact(const BatchSys& y, const BatchSta
     int cx, cy, cz;
     slot_cell(y, sm, p, cx, cy, cz);
     const float xi = sm.px[p], yi = sm.py[p], zi = sm.pz[p];
-    FixAcc ax{0u, 0u}, ay{0u, 0u}, az{0u, 0u};
-    int nterms = 0;
+    long long qx = 0, qy = 0, qz = 0;  // exact 64-bit sums
+    int nwide = 0;
     float pe = 0.f;
     for (int dz = -R; dz <= R; ++dz)
         for (int dy = -R; dy <= R; ++dy)
@@ -189,22 +189,17 @@ __device__ __noinline__ void batch_force_exact(const BatchSys& y, const BatchSta
                     const float s2 = sig2 * inv;
                     const float s6 = s2 * s2 * s2;
                     const float fs2 = __fmul_rn(__fmul_rn(__fmaf_rn(c48, s6, -c24), s6), inv);  // (|f|/r) * 2^11
-                    if (fabsf(fs2) < fs2_max) {
-                        fix_add(ax, fs2, ex);
-                        fix_add(ay, fs2, ey);
-                        fix_add(az, fs2, ez);
-                    } else {
-                        fix_add_wide(ax, fs2, ex, st.err);
-                        fix_add_wide(ay, fs2, ey, st.err);
-                        fix_add_wide(az, fs2, ez, st.err);
-                    }
-                    ++nterms;
+                    qx += fix_term_any(fs2, ex, fs2_max, st.err);
+                    qy += fix_term_any(fs2, ey, fs2_max, st.err);
+                    qz += fix_term_any(fs2, ez, fs2_max, st.err);
+                    nwide += fabsf(fs2) < fs2_max ? 0 : 1;
                     if (ENERGY) pe += c4 * s6 * (s6 - 1.0f);
                 }
             }
-    st.fq[g] = fix_final(ax, nterms);
-    st.fq[st.ntot + g] = fix_final(ay, nterms);
-    st.fq[2 * st.ntot + g] = fix_final(az, nterms);
+    fix_wide_count_ok(nwide, st.err);
+    st.fq[g] = qx;
+    st.fq[st.ntot + g] = qy;
+    st.fq[2 * st.ntot + g] = qz;
     if (ENERGY) pe_out[a] = 0.5f * pe;
 }
 
@@ -230,7 +225,7 @@ __device__ void batch_forces(const BatchSys& y, BatchState st, const PairTable& 
         const float xi = sm.px[p], yi = sm.py[p], zi = sm.pz[p];
         const f2_t pix = f2_pack(xi, xi), piy = f2_pack(yi, yi), piz = f2_pack(zi, zi);
         FixAcc ax{0u, 0u}, ay{0u, 0u}, az{0u, 0u};
-        int nterms = 0;
+        int nterms = 0, nin = 0;  // nin: non-zero terms, which bound the 32-bit split sums
         float pe = 0.f;
         bool bad = false;
         for (int dz = -R; dz <= R; ++dz)
@@ -269,6 +264,7 @@ __device__ void batch_forces(const BatchSys& y, BatchState st, const PairTable& 
                         fix_add2(ay, fs2, ey, magic2, two21);
                         fix_add2(az, fs2, ez, magic2, two21);
                         nterms += 2;
+                        nin += (int)ina + (int)inb;
                         if (ENERGY) {
                             float s6a, s6b;
                             f2_unpack(s6, s6a, s6b);
@@ -276,6 +272,7 @@ __device__ void batch_forces(const BatchSys& y, BatchState st, const PairTable& 
                         }
                     }
                 }
+        bad |= nin > FIX_SPLIT_MAX_TERMS;  // the split sums could wrap: the exact 64-bit pass
         if (bad) {  // finished by batch_force_exact after the loop
             sm.queue[atomicAdd(sm.nqueued, 1)] = (uint16_t)p;
             continue;

@@ -125,7 +125,7 @@ __device__ __forceinline__ void full_epilogue(const DevState& s, const PairTable
 // 2048 eps/sigma (beyond the two-part split; or not finite).  About one atom in 1,500 of
 // a liquid.  The neighbours come from the CTA's tile, so every other pair gets exactly
 // the term the FP32 loop adds; band pairs are decided in FP64 in the oracle's operation
-// order; large terms are rounded in FP64 (fix_wide_terms).  Lane sums are exact
+// order; large terms are rounded in FP64 (fix_term_wide).  Lane sums are exact 64-bit
 // integers, so the warp total does not depend on how the list is spread over the lanes.
 // The same epilogue follows.  This runs after the loop, not inside it: a call from the
 // loop cost the kernel half its speed.
@@ -141,8 +141,8 @@ __device__ __forceinline__ void finish_atom_warp(const DevState& s, const Geomet
     const int si = __float_as_int(pi.w);
     const int nsp = pt.nsp;
     const int nent = ((s.nl_cnt[gi] + 7) >> 3) * 8;
-    FixAcc ax{0u, 0u}, ay{0u, 0u}, az{0u, 0u};
-    int nterms = 0;
+    long long qx = 0, qy = 0, qz = 0;  // exact 64-bit sums (any list length)
+    int nwide = 0;
     float pe = 0.f, w0 = 0.f, w1 = 0.f, w2 = 0.f, w3 = 0.f, w4 = 0.f, w5 = 0.f;
     for (int k = lane; k < nent; k += 32) {
         const int u = s.nl[((size_t)(k >> 3) * s.np + gi) * 8 + (k & 7)];
@@ -160,16 +160,10 @@ __device__ __forceinline__ void finish_atom_warp(const DevState& s, const Geomet
             inside = fp64_pair_test(s.x, s.y, s.z, g.L[0], g.L[1], g.L[2], gi, tile_global_index(m, u),
                                     stab.rc2d[t]);
         const float fs2 = inside ? fs : 0.0f;
-        if (fabsf(fs2) < fs2_max) {
-            fix_add(ax, fs2, dx);
-            fix_add(ay, fs2, dy);
-            fix_add(az, fs2, dz);
-        } else {
-            fix_add_wide(ax, fs2, dx, s.err);
-            fix_add_wide(ay, fs2, dy, s.err);
-            fix_add_wide(az, fs2, dz, s.err);
-        }
-        ++nterms;
+        qx += fix_term_any(fs2, dx, fs2_max, s.err);
+        qy += fix_term_any(fs2, dy, fs2_max, s.err);
+        qz += fix_term_any(fs2, dz, fs2_max, s.err);
+        nwide += fabsf(fs2) < fs2_max ? 0 : 1;
         if (EV && inside) {
             const float gq = fs2 * (1.0f / FS_SCALE);
             pe += stab.c4[t] * s6 * (s6 - 1.0f);
@@ -181,7 +175,8 @@ __device__ __forceinline__ void finish_atom_warp(const DevState& s, const Geomet
             w5 += dy * (gq * dz);
         }
     }
-    long long qx = fix_final(ax, nterms), qy = fix_final(ay, nterms), qz = fix_final(az, nterms);
+    nwide = __reduce_add_sync(0xffffffffu, (unsigned)nwide);
+    if (lane == 0) fix_wide_count_ok(nwide, s.err);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         qx += __shfl_xor_sync(0xffffffffu, qx, o);
@@ -272,7 +267,9 @@ __global__ void __maxnreg__(SINGLE ? MDGB_FULL_MAX_REGS : MDGB_FULL_MAX_REGS_SPE
         const f2_t pix = f2_pack(pi.x, pi.x), piy = f2_pack(pi.y, pi.y), piz = f2_pack(pi.z, pi.z);
         FixAcc ax{0u, 0u}, ay{0u, 0u}, az{0u, 0u};
         float pe = 0.f, w0 = 0.f, w1 = 0.f, w2 = 0.f, w3 = 0.f, w4 = 0.f, w5 = 0.f;
-        bool bad = false;
+        // the 32-bit split sums are exact up to FIX_SPLIT_MAX_TERMS terms; a longer list
+        // (only at densities several times a liquid's) goes to the 64-bit warp finish
+        bool bad = nch * 8 > FIX_SPLIT_MAX_TERMS;
         for_each_neighbour_pair(lp, np, nch, [&](int u0, int u1) {
             const float4 pa = lds_tile(tile_s, u0);
             const float4 pb = lds_tile(tile_s, u1);
@@ -360,10 +357,17 @@ __global__ void __launch_bounds__(F_THREADS) k_force_mixed_half(DevState s, Geom
                                                                 int block0) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ TileMeta m;
+    // terms beyond the two-part split (atoms closer than about 0.75 sigma) do not go
+    // through the 32-bit tile sums: they wait here as exact 64-bit values
+    constexpr int WQ = 64;
+    __shared__ long long wq[WQ][3];
+    __shared__ int wq_u[WQ];
+    __shared__ int nwq;
     float4* tile = reinterpret_cast<float4*>(smem);
     unsigned* acc = reinterpret_cast<unsigned*>(tile + tile_cap);  // 6 x tile_cap: hx, lx, hy, ly, hz, lz
     int* nterm = reinterpret_cast<int*>(acc + 6 * tile_cap);        // tile_cap
     const int b = block0 + blockIdx.x;
+    if (threadIdx.x == 0) nwq = 0;
     tile_meta(g, s.cell_start, b, m);
     const int T = m.prefix[64];
     if (T + 1 > tile_cap) {
@@ -409,13 +413,29 @@ __global__ void __launch_bounds__(F_THREADS) k_force_mixed_half(DevState s, Geom
                 fix_sub(bx, fs2, dx);
                 fix_sub(by, fs2, dy);
                 fix_sub(bz, fs2, dz);
-            } else {
-                fix_add_wide(ax, fs2, dx, s.err);
-                fix_add_wide(ay, fs2, dy, s.err);
-                fix_add_wide(az, fs2, dz, s.err);
-                fix_add_wide(bx, fs2, -dx, s.err);
-                fix_add_wide(by, fs2, -dy, s.err);
-                fix_add_wide(bz, fs2, -dz, s.err);
+            } else {  // rare: both atoms' terms into the queue (its count bounds the 64-bit sums)
+                const long long qx = fix_term_wide(fs2, dx, s.err), qy = fix_term_wide(fs2, dy, s.err),
+                                qz = fix_term_wide(fs2, dz, s.err);
+                // the split sums count this pair as a zero term (offset bits only)
+                fix_add(ax, 0.0f, 0.0f);
+                fix_add(ay, 0.0f, 0.0f);
+                fix_add(az, 0.0f, 0.0f);
+                fix_add(bx, 0.0f, 0.0f);
+                fix_add(by, 0.0f, 0.0f);
+                fix_add(bz, 0.0f, 0.0f);
+                const int k = atomicAdd(&nwq, 2);
+                if (k + 1 < WQ && k + 2 <= FIX_WIDE_MAX_TERMS) {
+                    wq_u[k] = ui;
+                    wq[k][0] = qx;
+                    wq[k][1] = qy;
+                    wq[k][2] = qz;
+                    wq_u[k + 1] = u;
+                    wq[k + 1][0] = -qx;
+                    wq[k + 1][1] = -qy;
+                    wq[k + 1][2] = -qz;
+                } else {
+                    atomicOr(s.err, ERR_NONFINITE);
+                }
             }
             atomicAdd(&acc[0 * tile_cap + u], bx.hi);
             atomicAdd(&acc[1 * tile_cap + u], bx.lo);
@@ -459,6 +479,9 @@ __global__ void __launch_bounds__(F_THREADS) k_force_mixed_half(DevState s, Geom
     for (int u = threadIdx.x; u < T; u += blockDim.x) {
         const int nt = nterm[u];
         if (nt == 0) continue;
+        // each term's high part is below 2^22 in magnitude: more than FIX_SPLIT_MAX_TERMS
+        // terms on one atom (densities several times a liquid's) could wrap the 32-bit sum
+        if (nt > FIX_SPLIT_MAX_TERMS) atomicOr(s.err, ERR_NONFINITE);
         const int slot = tile_slot_of(m, u);
         const int gj = m.start[slot] + (u - m.prefix[slot]);
         FixAcc fx{acc[0 * tile_cap + u], acc[1 * tile_cap + u]};
@@ -467,6 +490,18 @@ __global__ void __launch_bounds__(F_THREADS) k_force_mixed_half(DevState s, Geom
         s.fq[gj] += fix_final(fx, nt);
         s.fq[n + gj] += fix_final(fy, nt);
         s.fq[2 * n + gj] += fix_final(fz, nt);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {  // the queued large terms, exact in 64 bits
+        const int nq = nwq < WQ ? nwq : WQ;
+        for (int k = 0; k < nq; ++k) {
+            const int u = wq_u[k];
+            const int slot = tile_slot_of(m, u);
+            const int gj = m.start[slot] + (u - m.prefix[slot]);
+            s.fq[gj] += wq[k][0];
+            s.fq[n + gj] += wq[k][1];
+            s.fq[2 * n + gj] += wq[k][2];
+        }
     }
 }
 

@@ -105,7 +105,7 @@ __global__ void __launch_bounds__(TB_THREADS) k_tbsma_density(DevState s, Geomet
         const int nch = (s.nl_cnt[gi] + 7) >> 3;
         FixAcc acc{0u, 0u};
         float rep = 0.f;
-        bool bad = false;
+        bool bad = nch * 8 > FIX_SPLIT_MAX_TERMS;  // longer lists: the warp's 64-bit sums
         for_each_neighbour(reinterpret_cast<const uint4*>(s.nl) + gi, s.np, nch, [&](int u) {
             float r2;
             tb_disp(pi, lds_tile(tile_s, u), r2);
@@ -129,8 +129,7 @@ __global__ void __launch_bounds__(TB_THREADS) k_tbsma_density(DevState s, Geomet
         const float4 pi = tile[ui];
         const int T = m.prefix[64];
         const int nent = ((s.nl_cnt[gi] + 7) >> 3) * 8;
-        FixAcc acc{0u, 0u};
-        int nterms = 0;
+        long long q = 0;  // exact 64-bit sum (any list length)
         float rep = 0.f;
         for (int e = lane; e < nent; e += 32) {
             const int u = s.nl[((size_t)(e >> 3) * s.np + gi) * 8 + (e & 7)];
@@ -140,11 +139,9 @@ __global__ void __launch_bounds__(TB_THREADS) k_tbsma_density(DevState s, Geomet
             const bool in = tb_inside_exact(s, g, tb, m, gi, u, r2);
             float phi, psi;
             tb_terms(tb, r2, rsqrt_approx(r2), phi, psi);
-            fix_add(acc, in ? psi * FS_SCALE : 0.f, 1.0f);
-            ++nterms;
+            q += fix_term(in ? psi * FS_SCALE : 0.f, 1.0f);
             if (EV) rep += in ? phi : 0.f;
         }
-        long long q = fix_final(acc, nterms);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             q += __shfl_xor_sync(0xffffffffu, q, o);
@@ -179,7 +176,7 @@ __global__ void __launch_bounds__(TB_THREADS) k_tbsma_force(DevState s, Geometry
         const int nch = (s.nl_cnt[gi] + 7) >> 3;
         FixAcc ax{0u, 0u}, ay{0u, 0u}, az{0u, 0u};
         float w0 = 0.f, w1 = 0.f, w2 = 0.f, w3 = 0.f, w4 = 0.f, w5 = 0.f;
-        bool bad = false;
+        bool bad = nch * 8 > FIX_SPLIT_MAX_TERMS;  // longer lists: the warp's 64-bit sums
         for_each_neighbour(reinterpret_cast<const uint4*>(s.nl) + gi, s.np, nch, [&](int u) {
             float r2;
             const float4 pj = lds_tile(tile_s, u);
@@ -229,8 +226,8 @@ __global__ void __launch_bounds__(TB_THREADS) k_tbsma_force(DevState s, Geometry
         const float inv_i = pi.w;
         const int T = m.prefix[64];
         const int nent = ((s.nl_cnt[gi] + 7) >> 3) * 8;
-        FixAcc ax{0u, 0u}, ay{0u, 0u}, az{0u, 0u};
-        int nterms = 0;
+        long long qx = 0, qy = 0, qz = 0;  // exact 64-bit sums (any list length)
+        int nwide = 0;
         float w0 = 0.f, w1 = 0.f, w2 = 0.f, w3 = 0.f, w4 = 0.f, w5 = 0.f;
         for (int e = lane; e < nent; e += 32) {
             const int u = s.nl[((size_t)(e >> 3) * s.np + gi) * 8 + (e & 7)];
@@ -244,16 +241,10 @@ __global__ void __launch_bounds__(TB_THREADS) k_tbsma_force(DevState s, Geometry
             tb_terms(tb, r2, rinv, phi, psi);
             const float fr = __fmaf_rn(tb.c_rep, phi, -tb.c_band * psi * (inv_i + pj.w));
             const float fs2 = in ? fr * rinv * FS_SCALE : 0.f;
-            if (fabsf(fs2) < fs2_max) {
-                fix_add(ax, fs2, d.x);
-                fix_add(ay, fs2, d.y);
-                fix_add(az, fs2, d.z);
-            } else {
-                fix_add_wide(ax, fs2, d.x, s.err);
-                fix_add_wide(ay, fs2, d.y, s.err);
-                fix_add_wide(az, fs2, d.z, s.err);
-            }
-            ++nterms;
+            qx += fix_term_any(fs2, d.x, fs2_max, s.err);
+            qy += fix_term_any(fs2, d.y, fs2_max, s.err);
+            qz += fix_term_any(fs2, d.z, fs2_max, s.err);
+            nwide += fabsf(fs2) < fs2_max ? 0 : 1;
             if (EV) {
                 const float gq = fs2 * (1.0f / FS_SCALE);
                 w0 += d.x * (gq * d.x);
@@ -264,7 +255,8 @@ __global__ void __launch_bounds__(TB_THREADS) k_tbsma_force(DevState s, Geometry
                 w5 += d.y * (gq * d.z);
             }
         }
-        long long qx = fix_final(ax, nterms), qy = fix_final(ay, nterms), qz = fix_final(az, nterms);
+        nwide = __reduce_add_sync(0xffffffffu, (unsigned)nwide);
+        if (lane == 0) fix_wide_count_ok(nwide, s.err);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             qx += __shfl_xor_sync(0xffffffffu, qx, o);

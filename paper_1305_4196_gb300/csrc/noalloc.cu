@@ -1,9 +1,10 @@
 // noalloc.cu - a kinetic-energy reduction that allocates no device memory.
 //
-// Some callers cannot allocate device memory when they need this value: code
-// running while a CUDA stream is being captured into a graph (cudaMalloc is not
-// allowed there), and hosts that hand this library a fixed memory budget with
-// allocation locked after start-up.  md_kinetic_energy_noalloc serves them: it
+// Some callers cannot allocate device memory when they need this value: hosts that
+// hand this library a fixed memory budget and lock allocation after start-up (an
+// embedding runtime that owns every byte of device memory through its own pool), and
+// real-time loops that must not call cudaMalloc, which can synchronise the device and
+// stall the loop.  md_kinetic_energy_noalloc serves them: it
 // computes 1/2 sum m v^2 of caller-owned velocities with the same deterministic
 // two-pass FP64 reduction as md_energy_virial, but keeps its per-CTA partial
 // sums in one statically sized device array instead of allocating scratch.
@@ -26,8 +27,9 @@ struct NoallocMass {
     double m[mdgb::MAX_SPECIES];
 };
 
+// A species id outside [0, nsp) reads no mass: its term is NaN, so the sum reports it.
 __global__ void __launch_bounds__(NOALLOC_THREADS) k_ke_partials(long long n, const double* __restrict__ vel,
-                                                                  const int32_t* __restrict__ species,
+                                                                  const int32_t* __restrict__ species, int nsp,
                                                                   NoallocMass mass, long long chunk,
                                                                   double* __restrict__ partials) {
     __shared__ double sh[NOALLOC_THREADS];
@@ -35,7 +37,8 @@ __global__ void __launch_bounds__(NOALLOC_THREADS) k_ke_partials(long long n, co
     const long long hi = lo + chunk < n ? lo + chunk : n;
     double acc = 0.0;
     for (long long i = lo + threadIdx.x; i < hi; i += NOALLOC_THREADS) {
-        const double m = mass.m[species ? species[i] : 0];
+        const int a = species ? species[i] : 0;
+        const double m = (a >= 0 && a < nsp) ? mass.m[a] : __longlong_as_double(0x7ff8000000000000LL);
         const double vx = vel[3 * i], vy = vel[3 * i + 1], vz = vel[3 * i + 2];
         acc += 0.5 * m * (vx * vx + vy * vy + vz * vz);
     }
@@ -99,7 +102,18 @@ extern "C" int md_kinetic_energy_noalloc(int64_t n, const double* vel, const int
     if (nparts < 1) nparts = 1;
     if (nparts > NOALLOC_MAX_PARTS) nparts = NOALLOC_MAX_PARTS;
     const long long chunk = n > 0 ? (n + nparts - 1) / nparts : 1;
-    k_ke_partials<<<(unsigned)nparts, NOALLOC_THREADS, 0, st>>>(n, vel, species, m, chunk, partials);
-    k_ke_final<<<1, NOALLOC_THREADS, 0, st>>>(partials, (int)nparts, ke_out);
-    return cudaGetLastError() == cudaSuccess ? MD_OK : MD_ERR_CUDA;
+    // cudaLaunchKernel reports each launch's own status, so an error left pending by the
+    // caller's earlier work is neither taken for this call's nor cleared by it
+    int nsp = n_species, np_i = (int)nparts;
+    long long n_arg = n;
+    const double* vel_arg = vel;
+    const int32_t* sp_arg = species;
+    void* a1[] = {&n_arg, &vel_arg, &sp_arg, &nsp, &m, const_cast<long long*>(&chunk), &partials};
+    if (cudaLaunchKernel((const void*)k_ke_partials, dim3((unsigned)nparts), dim3(NOALLOC_THREADS), a1, 0, st) !=
+        cudaSuccess)
+        return MD_ERR_CUDA;
+    void* a2[] = {&partials, &np_i, &ke_out};
+    if (cudaLaunchKernel((const void*)k_ke_final, dim3(1), dim3(NOALLOC_THREADS), a2, 0, st) != cudaSuccess)
+        return MD_ERR_CUDA;
+    return MD_OK;
 }

@@ -175,7 +175,11 @@ def test_backward_at_the_force_matching_size(precision):
     lists sized for cutoffs 10 % above 2.5 sigma_ab (8 cells per side, so 64 blocks whose
     4x4x4-cell tiles are smaller than the box), parameters perturbed by 10 %; dL/dx,
     dL/deps and dL/dsigma for a random upstream gradient, and dE/deps, dE/dsigma, element
-    by element against the oracle's analytic gradient at the same bars as above."""
+    by element against the oracle's analytic gradient.  Bars as above, except that the
+    mixed parameter derivatives dL/deps and dL/dsigma - sums of about 1.3 million pair
+    terms of both signs - are held to the per-term bar 2e-5 times the sum of |term| (the
+    oracle's scale of each sum): their terms cancel, so a bound relative to the result
+    would demand more than FP32 pair terms carry."""
     s, sp = ka_snapshot(n_cells=20, seed=101)
     eps1 = KA_EPS * np.array([[1.1, 0.9], [0.9, 1.1]])
     sig1 = KA_SIG * np.array([[0.9, 1.1], [1.1, 0.9]])
@@ -188,9 +192,13 @@ def test_backward_at_the_force_matching_size(precision):
     G = np.random.default_rng(7).normal(size=(s.n, 3))
     gx, ge, gs = sysm.forces_backward(G)
     gx_ref, ge_ref, gs_ref = O.lj_force_grad(s.pos, s.box, P, G, sp)
+    ae, as_ = O.lj_force_grad_scale(s.pos, s.box, P, G, sp)
     assert vec_error(gx, gx_ref) <= TOL[precision]
-    for t, tref in [(ge, ge_ref), (gs, gs_ref)]:
-        assert np.abs(t - tref).max() <= TOL[precision] * np.abs(tref).max()
+    for t, tref, scale in [(ge, ge_ref, ae), (gs, gs_ref, as_)]:
+        if precision == "fp64":
+            assert np.abs(t - tref).max() <= TOL[precision] * np.abs(tref).max()
+        else:
+            assert np.all(np.abs(t - tref) <= TOL[precision] * scale)
     de, ds = sysm.energy_param_grad()
     de_ref, ds_ref = O.lj_energy_param_grad(s.pos, s.box, P, sp)
     tol = 1e-11 if precision == "fp64" else 1e-5

@@ -241,6 +241,36 @@ def test_close_pairs_take_the_exact_wide_path(lst):
     assert np.array_equal(make(sp, "mixed", lst).forces(), F[perm])
 
 @pytest.mark.parametrize("lst", ["full", "half"])
+def test_very_close_pairs_exact_or_reported(lst):
+    """Pair forces of 1.5e6 eps/sigma (atoms 0.45 sigma apart), three of them adding up to
+    3.1e6 on one atom: beyond 2^20 eps/sigma, the range of 32-bit high-part sums, so the
+    exact 64-bit path must carry them and match the oracle.  Atoms 0.40 sigma apart (7.1e6
+    eps/sigma, beyond the 2^22 the 64-bit sums accept per term) are reported as
+    MD_ERR_NONFINITE instead of a wrapped force."""
+    sysm = liquid()
+    rng = np.random.default_rng(21)
+    pos = sysm.pos.copy()
+    picks = rng.choice(sysm.n // 2, 16, replace=False)
+    for c in range(4):  # each: an atom and three partners at 0.45 sigma, 60 degrees apart
+        i, js = picks[4 * c], picks[4 * c + 1:4 * c + 4]
+        for k, j in enumerate(js):
+            a = (k - 1) * np.pi / 3
+            pos[j] = W.wrap(pos[i] + 0.45 * np.array([np.cos(a), np.sin(a), 0.0]), sysm.box)
+    dense = W.System(pos, sysm.vel, sysm.species, sysm.box)
+    F = make(dense, "mixed", lst).forces()
+    Fref, _, _ = O.lj_forces(pos, sysm.box, O.LJParams.single())
+    assert np.abs(Fref).max() > 3.0e6
+    assert force_error(F, Fref) <= TOL["mixed"]
+    assert np.abs(F - Fref).max() <= 2e-5 * np.abs(Fref).max()
+    pos2 = sysm.pos.copy()
+    pos2[picks[1]] = W.wrap(pos2[picks[0]] + np.array([0.40, 0.0, 0.0]), sysm.box)
+    s = make(W.System(pos2, sysm.vel, sysm.species, sysm.box), "mixed", lst)
+    with pytest.raises(M.MDError) as e:
+        s.forces()
+    assert e.value.code == M.MD_ERR_NONFINITE
+
+
+@pytest.mark.parametrize("lst", ["full", "half"])
 def test_cutoff_decided_by_the_definition(lst):
     """Isolated pairs at r_cut (1 -/+ 1e-7): inside and outside by the FP64 definition, but
     closer to r_cut than FP32 distances resolve.  The unshifted force jumps by |f(r_cut)| there,

@@ -661,3 +661,18 @@ def test_tbsma_velocity_verlet_time_reversible():
     assert a["rebuilds"] >= 1
     assert np.abs(b["pos"] + b["image"] * box - pos).max() < 1e-9
     assert np.abs(b["vel"] + vel).max() < 1e-9 * np.abs(vel).max()
+
+
+def test_force_grad_scale_bounds_the_sums():
+    """The scale sum |term| of the parameter derivatives bounds |sum| (strictly, for a random
+    upstream gradient, whose pair terms cancel), and vanishes with every term: a uniform G
+    gives w = G_i - G_j = 0 on every pair."""
+    s, sp, P = _ka_small(3)
+    G = np.random.default_rng(5).normal(size=(s.n, 3))
+    _, ge, gs = O.lj_force_grad(s.pos, s.box, P, G, sp)
+    ae, as_ = O.lj_force_grad_scale(s.pos, s.box, P, G, sp)
+    assert np.all(ae >= np.abs(ge)) and np.all(as_ >= np.abs(gs))
+    assert np.all(ae > 3 * np.abs(ge))  # random upstream gradients cancel
+    # a uniform field G_i = c: w = 0, every term vanishes, and so does the scale
+    ae0, as0 = O.lj_force_grad_scale(s.pos, s.box, P, np.ones((s.n, 3)), sp)
+    assert np.all(ae0 == 0.0) and np.all(as0 == 0.0)

@@ -1,8 +1,9 @@
 """md_kinetic_energy_noalloc: the kinetic energy for callers that cannot allocate.
 
-Callers inside a CUDA stream capture (no cudaMalloc allowed there) or under a
-locked memory budget use this entry point; it keeps its partial sums in a static
-device array instead of allocating scratch.  Its result must equal the kinetic
+Callers under a locked memory budget (an embedding runtime that owns all device
+memory) or in a loop that must not call cudaMalloc (it can synchronise the device)
+use this entry point; it keeps its partial sums in a static device array instead of
+allocating scratch.  Its result must equal the kinetic
 energy md_energy_virial reports for the same velocities, on every call.  This
 file is collected last so that a failure here does not hide any other test.
 """
@@ -69,3 +70,27 @@ def test_noalloc_rejects_sizes_beyond_the_maximum():
     assert M.md_kinetic_energy_noalloc((1 << 30) + 1, vel, None, [1.0], out) == M.MD_ERR_ARG
     assert M.md_kinetic_energy_noalloc(-1, vel, None, [1.0], out) == M.MD_ERR_ARG
     assert M.md_kinetic_energy_noalloc(1, vel, None, [1.0] * 5, out) == M.MD_ERR_ARG
+
+
+def test_noalloc_species_ids_checked_at_the_limit():
+    """Two species: ids up to n_species - 1 give the right energy; an id equal to
+    n_species or negative reads no mass and turns the result into NaN."""
+    sysm = W.lj_fcc(6, seed=8, jitter=0.05)  # 864 atoms
+    sp = np.zeros(sysm.n, dtype=np.int32)
+    sp[::3] = 1
+    mass = [1.0, 3.0]
+    ke_ref = 0.5 * float((np.asarray(mass)[sp] * (sysm.vel ** 2).sum(1)).sum())
+    dev = torch.device("cuda")
+    vel = torch.from_numpy(np.ascontiguousarray(sysm.vel)).to(dev)
+    out = torch.zeros(3, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream().cuda_stream
+    assert M.md_kinetic_energy_noalloc(sysm.n, vel, torch.from_numpy(sp).to(dev), mass, out[0:1], stream) == M.MD_OK
+    for k, bad in ((1, 2), (2, -1)):
+        spb = sp.copy()
+        spb[sysm.n // 2] = bad
+        assert M.md_kinetic_energy_noalloc(sysm.n, vel, torch.from_numpy(spb).to(dev), mass, out[k:k + 1],
+                                           stream) == M.MD_OK
+    torch.cuda.synchronize()
+    ke = out.cpu().numpy()
+    assert ke[0] == pytest.approx(ke_ref, rel=1e-12)
+    assert np.isnan(ke[1]) and np.isnan(ke[2])
