@@ -125,15 +125,23 @@ __device__ __forceinline__ void full_epilogue(const DevState& s, const PairTable
 // 2048 eps/sigma (beyond the two-part split; or not finite).  About one atom in 1,500 of
 // a liquid.  The neighbours come from the CTA's tile, so every other pair gets exactly
 // the term the FP32 loop adds; band pairs are decided in FP64 in the oracle's operation
-// order; large terms are rounded in FP64 (fix_term_wide).  Lane sums are exact 64-bit
-// integers, so the warp total does not depend on how the list is spread over the lanes.
-// The same epilogue follows.  This runs after the loop, not inside it: a call from the
-// loop cost the kernel half its speed.
+// order; large terms are rounded in FP64 (fix_term_wide).  Each lane keeps the 32-bit
+// split sums of the FP32 loop, and the terms they cannot take - large terms, and the
+// lane's split sums every FIX_SPLIT_MAX_TERMS terms - go to the warp's exact 64-bit sums
+// in shared memory (WarpWide), so this rare path adds no 64-bit registers to the kernel
+// it is inlined into.  All sums are exact integers, so the warp total does not depend on
+// how the list is spread over the lanes.  The same epilogue follows.  This runs after the
+// loop, not inside it: a call from the loop cost the kernel half its speed.
+struct WarpWide {
+    unsigned long long q[3];
+    int nwide;
+};
+
 template <bool SINGLE, bool EV, int MODE>
 __device__ __forceinline__ void finish_atom_warp(const DevState& s, const Geometry& g, const PairTable& pt,
                                                  const float4* __restrict__ tile, const SpeciesTable& stab,
                                                  const TileMeta& m, int ui, float fs2_max, const StepOut& out,
-                                                 double dt, float lim2_f) {
+                                                 double dt, float lim2_f, WarpWide& ww) {
     const int lane = threadIdx.x & 31;
     const int T = m.prefix[64];
     const int gi = m.start[0] + ui;
@@ -141,8 +149,13 @@ __device__ __forceinline__ void finish_atom_warp(const DevState& s, const Geomet
     const int si = __float_as_int(pi.w);
     const int nsp = pt.nsp;
     const int nent = ((s.nl_cnt[gi] + 7) >> 3) * 8;
-    long long qx = 0, qy = 0, qz = 0;  // exact 64-bit sums (any list length)
-    int nwide = 0;
+    if (lane == 0) {
+        ww.q[0] = ww.q[1] = ww.q[2] = 0ull;
+        ww.nwide = 0;
+    }
+    __syncwarp();
+    FixAcc ax{0u, 0u}, ay{0u, 0u}, az{0u, 0u};
+    int nterms = 0;
     float pe = 0.f, w0 = 0.f, w1 = 0.f, w2 = 0.f, w3 = 0.f, w4 = 0.f, w5 = 0.f;
     for (int k = lane; k < nent; k += 32) {
         const int u = s.nl[((size_t)(k >> 3) * s.np + gi) * 8 + (k & 7)];
@@ -152,18 +165,38 @@ __device__ __forceinline__ void finish_atom_warp(const DevState& s, const Geomet
         const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
         const int t = SINGLE ? 0 : si * nsp + __float_as_int(pj.w);
         const float inv = rcp_approx(r2);
-        const float s2 = stab.sig2[t] * inv;
-        const float s6 = s2 * s2 * s2;
-        const float fs = __fmul_rn(__fmul_rn(__fmaf_rn(stab.c48[t], s6, -stab.c24[t]), s6), inv);
+        float fs, s6;  // the FP32 loop's operations, term for term
+        if (SINGLE) {
+            const float inv2 = __fmul_rn(inv, inv), inv3 = __fmul_rn(inv2, inv);
+            fs = __fmul_rn(__fmaf_rn(pt.lj_a_f, inv3, -pt.lj_b_f), __fmul_rn(inv2, inv2));
+            s6 = __fmul_rn(pt.sig6_f, inv3);
+        } else {
+            const float s2 = __fmul_rn(stab.sig2[t], inv);
+            s6 = __fmul_rn(__fmul_rn(s2, s2), s2);
+            fs = __fmul_rn(__fmul_rn(__fmaf_rn(stab.c48[t], s6, -stab.c24[t]), s6), inv);
+        }
         bool inside = r2 < stab.rc2lo[t];
         if (!inside && r2 < stab.rc2hi[t])
             inside = fp64_pair_test(s.x, s.y, s.z, g.L[0], g.L[1], g.L[2], gi, tile_global_index(m, u),
                                     stab.rc2d[t]);
         const float fs2 = inside ? fs : 0.0f;
-        qx += fix_term_any(fs2, dx, fs2_max, s.err);
-        qy += fix_term_any(fs2, dy, fs2_max, s.err);
-        qz += fix_term_any(fs2, dz, fs2_max, s.err);
-        nwide += fabsf(fs2) < fs2_max ? 0 : 1;
+        if (fabsf(fs2) < fs2_max) {
+            fix_add(ax, fs2, dx);
+            fix_add(ay, fs2, dy);
+            fix_add(az, fs2, dz);
+            if (++nterms == FIX_SPLIT_MAX_TERMS) {  // only for lists of more than 16,000 entries
+                atomicAdd(&ww.q[0], (unsigned long long)fix_final(ax, nterms));
+                atomicAdd(&ww.q[1], (unsigned long long)fix_final(ay, nterms));
+                atomicAdd(&ww.q[2], (unsigned long long)fix_final(az, nterms));
+                ax = ay = az = FixAcc{0u, 0u};
+                nterms = 0;
+            }
+        } else {
+            atomicAdd(&ww.q[0], (unsigned long long)fix_term_wide(fs2, dx, s.err));
+            atomicAdd(&ww.q[1], (unsigned long long)fix_term_wide(fs2, dy, s.err));
+            atomicAdd(&ww.q[2], (unsigned long long)fix_term_wide(fs2, dz, s.err));
+            atomicAdd(&ww.nwide, 1);
+        }
         if (EV && inside) {
             const float gq = fs2 * (1.0f / FS_SCALE);
             pe += stab.c4[t] * s6 * (s6 - 1.0f);
@@ -175,8 +208,14 @@ __device__ __forceinline__ void finish_atom_warp(const DevState& s, const Geomet
             w5 += dy * (gq * dz);
         }
     }
-    nwide = __reduce_add_sync(0xffffffffu, (unsigned)nwide);
-    if (lane == 0) fix_wide_count_ok(nwide, s.err);
+    long long qx = fix_final(ax, nterms), qy = fix_final(ay, nterms), qz = fix_final(az, nterms);
+    __syncwarp();
+    if (lane == 0) {
+        fix_wide_count_ok(ww.nwide, s.err);
+        qx += (long long)ww.q[0];
+        qy += (long long)ww.q[1];
+        qz += (long long)ww.q[2];
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         qx += __shfl_xor_sync(0xffffffffu, qx, o);
@@ -231,6 +270,7 @@ __global__ void __maxnreg__(SINGLE ? MDGB_FULL_MAX_REGS : MDGB_FULL_MAX_REGS_SPE
     __shared__ TileMeta m;
     __shared__ SpeciesTable stab;
     __shared__ int nqueued;
+    __shared__ WarpWide wwide[FULL_THREADS / 32];
     float4* tile = reinterpret_cast<float4*>(smem);
     uint16_t* queued = reinterpret_cast<uint16_t*>(tile + tile_cap);  // own atoms left to finish_atom_warp
     const int b = spatial_block(g, blockIdx.x);
@@ -254,52 +294,65 @@ __global__ void __maxnreg__(SINGLE ? MDGB_FULL_MAX_REGS : MDGB_FULL_MAX_REGS_SPE
     const int nsp = pt.nsp;
     const f2_t magic2 = f2_pack(MAGIC, MAGIC);
     const f2_t two21 = f2_pack(TWO21, TWO21);
-    const f2_t sig2_1 = f2_pack(pt.sig2_f[0], pt.sig2_f[0]);
-    const f2_t c48_1 = f2_pack(pt.c48_f[0], pt.c48_f[0]);
-    const f2_t nc24_1 = f2_pack(-pt.c24_f[0], -pt.c24_f[0]);
-    const float rc2hi_1 = pt.rc2hi_f[0], rc2lo_1 = pt.rc2lo_f[0];  // kernel parameters: constant-bank operands
     for (int ui = threadIdx.x; ui < nown; ui += blockDim.x) {
         const int gi = blk0 + ui;
         const float4 pi = tile[ui];
         const int si = __float_as_int(pi.w);
         const int nch = (s.nl_cnt[gi] + 7) >> 3;
         const uint4* lp = reinterpret_cast<const uint4*>(s.nl) + gi;
-        const f2_t pix = f2_pack(pi.x, pi.x), piy = f2_pack(pi.y, pi.y), piz = f2_pack(pi.z, pi.z);
         FixAcc ax{0u, 0u}, ay{0u, 0u}, az{0u, 0u};
         float pe = 0.f, w0 = 0.f, w1 = 0.f, w2 = 0.f, w3 = 0.f, w4 = 0.f, w5 = 0.f;
         // the 32-bit split sums are exact up to FIX_SPLIT_MAX_TERMS terms; a longer list
-        // (only at densities several times a liquid's) goes to the 64-bit warp finish
+        // (only at densities several times a liquid's) goes to the exact finish
         bool bad = nch * 8 > FIX_SPLIT_MAX_TERMS;
+        // one species: the band and large-force tests as two running minima, checked once
+        float mdist = 3.0e38f, mr2 = 3.0e38f;
         for_each_neighbour_pair(lp, np, nch, [&](int u0, int u1) {
             const float4 pa = lds_tile(tile_s, u0);
             const float4 pb = lds_tile(tile_s, u1);
-            const f2_t dx = f2_sub(pix, f2_pack(pa.x, pb.x));
-            const f2_t dy = f2_sub(piy, f2_pack(pa.y, pb.y));
-            const f2_t dz = f2_sub(piz, f2_pack(pa.z, pb.z));
+            // scalar differences land directly in the register pairs of the packed operands
+            const f2_t dx = f2_pack(__fsub_rn(pi.x, pa.x), __fsub_rn(pi.x, pb.x));
+            const f2_t dy = f2_pack(__fsub_rn(pi.y, pa.y), __fsub_rn(pi.y, pb.y));
+            const f2_t dz = f2_pack(__fsub_rn(pi.z, pa.z), __fsub_rn(pi.z, pb.z));
             const f2_t r2 = f2_fma(dz, dz, f2_fma(dy, dy, f2_mul(dx, dx)));
             float r2a, r2b;
             f2_unpack(r2, r2a, r2b);
-            const int ta = SINGLE ? 0 : si * nsp + __float_as_int(pa.w);
-            const int tb = SINGLE ? 0 : si * nsp + __float_as_int(pb.w);
             const f2_t inv = f2_pack(rcp_approx(r2a), rcp_approx(r2b));
-            // single species: the constants are kernel parameters (constant-bank operands)
-            const f2_t sig2 = SINGLE ? sig2_1 : f2_pack(stab.sig2[ta], stab.sig2[tb]);
-            const f2_t c48 = SINGLE ? c48_1 : f2_pack(stab.c48[ta], stab.c48[tb]);
-            const f2_t nc24 = SINGLE ? nc24_1 : f2_pack(-stab.c24[ta], -stab.c24[tb]);
-            const float hia_c = SINGLE ? rc2hi_1 : stab.rc2hi[ta], hib_c = SINGLE ? rc2hi_1 : stab.rc2hi[tb];
-            const float loa_c = SINGLE ? rc2lo_1 : stab.rc2lo[ta], lob_c = SINGLE ? rc2lo_1 : stab.rc2lo[tb];
-            const f2_t s2 = f2_mul(sig2, inv);
-            const f2_t s6 = f2_mul(f2_mul(s2, s2), s2);
-            const f2_t fsv = f2_mul(f2_mul(f2_fma(c48, s6, nc24), s6), inv);
             float fa, fb;
-            f2_unpack(fsv, fa, fb);
-            // inside for certain below the band, tentatively inside up to its top: a pair in
-            // the band leaves the atom to finish_atom_warp (FP64 cutoff decision)
-            const bool ina = r2a < hia_c, inb = r2b < hib_c;
+            f2_t s6;  // (sigma^2 / r^2)^3, for the energy
+            bool ina, inb;
+            if (SINGLE) {
+                // fs2 = inv^4 (a inv^3 - b): the constants are kernel parameters
+                const f2_t inv2 = f2_mul(inv, inv);
+                const f2_t inv3 = f2_mul(inv2, inv);
+                const f2_t t = f2_fma(f2_pack(pt.lj_a_f, pt.lj_a_f), inv3, f2_pack(-pt.lj_b_f, -pt.lj_b_f));
+                f2_unpack(f2_mul(t, f2_mul(inv2, inv2)), fa, fb);
+                if (EV) s6 = f2_mul(f2_pack(pt.sig6_f, pt.sig6_f), inv3);
+                // inside for certain below the band, tentatively inside up to its top: a pair
+                // in the band leaves the atom to finish_atom_warp (FP64 cutoff decision)
+                ina = r2a < pt.rc2hi_f[0];
+                inb = r2b < pt.rc2hi_f[0];
+                float dca, dcb;
+                f2_unpack(f2_sub(r2, f2_pack(pt.rc2_f[0], pt.rc2_f[0])), dca, dcb);  // exact near r_cut
+                mdist = fminf(mdist, fminf(fabsf(dca), fabsf(dcb)));
+                mr2 = fminf(mr2, fminf(r2a, r2b));
+            } else {
+                const int ta = si * nsp + __float_as_int(pa.w);
+                const int tb = si * nsp + __float_as_int(pb.w);
+                const f2_t s2 = f2_mul(f2_pack(stab.sig2[ta], stab.sig2[tb]), inv);
+                s6 = f2_mul(f2_mul(s2, s2), s2);
+                f2_unpack(f2_mul(f2_mul(f2_fma(f2_pack(stab.c48[ta], stab.c48[tb]), s6,
+                                               f2_pack(-stab.c24[ta], -stab.c24[tb])),
+                                        s6),
+                                 inv),
+                          fa, fb);
+                ina = r2a < stab.rc2hi[ta];
+                inb = r2b < stab.rc2hi[tb];
+                bad |= !(fabsf(fa) < fs2_max) | !(fabsf(fb) < fs2_max) | (ina != (r2a < stab.rc2lo[ta])) |
+                       (inb != (r2b < stab.rc2lo[tb]));
+            }
             fa = ina ? fa : 0.0f;
             fb = inb ? fb : 0.0f;
-            bad |= !(fabsf(fa) < fs2_max) | !(fabsf(fb) < fs2_max) | (ina != (r2a < loa_c)) |
-                   (inb != (r2b < lob_c));
             const f2_t fs2 = f2_pack(fa, fb);
             fix_add2(ax, fs2, dx, magic2, two21);
             fix_add2(ay, fs2, dy, magic2, two21);
@@ -310,6 +363,8 @@ __global__ void __maxnreg__(SINGLE ? MDGB_FULL_MAX_REGS : MDGB_FULL_MAX_REGS_SPE
                 f2_unpack(dx, dxa, dxb);
                 f2_unpack(dy, dya, dyb);
                 f2_unpack(dz, dza, dzb);
+                const int ta = SINGLE ? 0 : si * nsp + __float_as_int(pa.w);
+                const int tb = SINGLE ? 0 : si * nsp + __float_as_int(pb.w);
                 const float c4a = SINGLE ? pt.c4_f[0] : stab.c4[ta], c4b = SINGLE ? pt.c4_f[0] : stab.c4[tb];
                 const float ua = ina ? c4a * s6a * (s6a - 1.0f) : 0.0f;
                 const float ub = inb ? c4b * s6b * (s6b - 1.0f) : 0.0f;
@@ -323,6 +378,10 @@ __global__ void __maxnreg__(SINGLE ? MDGB_FULL_MAX_REGS : MDGB_FULL_MAX_REGS_SPE
                 w5 += dya * (ga * dza) + dyb * (gb * dzb);
             }
         });
+        // a pair in the band (|r^2 - r_cut^2| up to its half width) or close enough for a
+        // term beyond the split sends the atom to the exact finish; NaN distances give no
+        // force on either path
+        if (SINGLE) bad |= (mdist <= pt.band_half_f) | (mr2 < pt.r2_wide_f);
         if (bad) {  // finished after the loop by finish_atom_warp, epilogue included
             queued[atomicAdd(&nqueued, 1)] = (uint16_t)ui;
             continue;
@@ -344,7 +403,8 @@ __global__ void __maxnreg__(SINGLE ? MDGB_FULL_MAX_REGS : MDGB_FULL_MAX_REGS_SPE
     __syncthreads();
     const int nq = nqueued;
     for (int k = threadIdx.x >> 5; k < nq; k += blockDim.x >> 5)
-        finish_atom_warp<SINGLE, EV, MODE>(s, g, pt, tile, stab, m, queued[k], fs2_max, out, dt, lim2_f);
+        finish_atom_warp<SINGLE, EV, MODE>(s, g, pt, tile, stab, m, queued[k], fs2_max, out, dt, lim2_f,
+                                           wwide[threadIdx.x >> 5]);
 }
 
 // ---------------------------------------------------------------- mixed, half list, one colour

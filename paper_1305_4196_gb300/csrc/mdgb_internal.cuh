@@ -53,14 +53,41 @@ struct PairTable {
     double mass[MAX_SPECIES];
     float cut_band;  // mixed path: pairs with FP32 r^2 within r_cut^2 (1 -/+ cut_band) are decided in FP64
     float rc2lo_f[MAX_PAIR], rc2hi_f[MAX_PAIR];  // r_cut^2 (1 -/+ cut_band) in FP32
+    // One species: the band as a half width around rc2_f[0] (covering [rc2lo_f, rc2hi_f]),
+    // and an r^2 below which a pair's FP32 force term may reach the split's limit
+    // (fs2_max); above it |fs2| stays below half that limit.
+    float band_half_f, r2_wide_f;
+    // One species: the pair force as fs2 = inv^4 (lj_a inv^3 - lj_b) with inv = 1/r^2,
+    // lj_a = c48 sigma^12, lj_b = c24 sigma^6 (the 2^11 scale included), and sigma^6.
+    float lj_a_f, lj_b_f, sig6_f;
 };
 
-// The FP32 thresholds of the band (after pt.cut_band and pt.rc2_f are set).
+// The FP32 thresholds of the band (after pt.cut_band, the pair constants and pt.rc2_f are set).
 inline void set_band_thresholds(PairTable& pt) {
     for (int t = 0; t < pt.nsp * pt.nsp; ++t) {
         pt.rc2lo_f[t] = (float)((double)pt.rc2_f[t] * (1.0 - (double)pt.cut_band));
         pt.rc2hi_f[t] = (float)((double)pt.rc2_f[t] * (1.0 + (double)pt.cut_band));
     }
+    const float up = pt.rc2hi_f[0] - pt.rc2_f[0], down = pt.rc2_f[0] - pt.rc2lo_f[0];  // exact (Sterbenz)
+    pt.band_half_f = up > down ? up : down;
+    // fs2(r^2) = 2^11 * 24 eps (2 s6^2 - s6) / r^2, s6 = (sigma^2 / r^2)^3, falls monotonically
+    // up to the potential minimum and stays far below the limit beyond it; find where it is
+    // half the limit (the same limit as the kernels: 2^22 / r_cut,max * 0.999)
+    float rc2max = 0.f;
+    for (int t = 0; t < pt.nsp * pt.nsp; ++t) rc2max = pt.rc2_f[t] > rc2max ? pt.rc2_f[t] : rc2max;
+    const double half_lim = 0.5 * (double)(4194304.0f / sqrtf(rc2max) * 0.999f);
+    const double c48 = pt.c48_f[0], c24 = pt.c24_f[0], sg2 = pt.sig2_f[0];
+    double lo = 1e-12 * sg2, hi = 1.2599210498948732 * sg2;  // 2^(1/3) sigma^2: the minimum
+    for (int it = 0; it < 200; ++it) {
+        const double mid = 0.5 * (lo + hi), s6 = (sg2 / mid) * (sg2 / mid) * (sg2 / mid);
+        const double fs = (c48 * s6 - c24) * s6 / mid;
+        if (fs > half_lim) lo = mid; else hi = mid;
+    }
+    pt.r2_wide_f = (float)hi;
+    const double sg6 = sg2 * sg2 * sg2;
+    pt.lj_a_f = (float)(c48 * sg6 * sg6);
+    pt.lj_b_f = (float)(c24 * sg6);
+    pt.sig6_f = (float)sg6;
 }
 
 // Tight-binding second-moment potential (Cleri and Rosato 1993; the potential of the
