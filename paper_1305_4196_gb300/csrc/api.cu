@@ -77,6 +77,8 @@ struct md_system {
     long long* d_ctrl = nullptr;  // [0] step counter, [1] builds done inside graphs
     long long* h_ctrl = nullptr;  // pinned mirror
     bool snapshot_first = true;
+    int compact = 0;          // grid of the occupied-block loops of a mostly empty system (see do_build)
+    bool no_compact = false;  // MDGB_NO_COMPACT=1 at md_create: one CTA per block always
     char msg[512] = "";
 };
 
@@ -235,7 +237,7 @@ int alloc_lists(md_system* s, int cap, bool keep = false) {
 int sync_flags(md_system* s) {
     CK(cudaMemcpyAsync(s->h_flags, s->st[0].err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s->stream));
     CK(cudaMemcpyAsync(s->h_flags + 1, s->st[0].rebuild_flag, sizeof(int32_t), cudaMemcpyDeviceToHost, s->stream));
-    CK(cudaMemcpyAsync(s->h_flags + 2, s->st[0].stats, 4 * sizeof(int32_t), cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaMemcpyAsync(s->h_flags + 2, s->st[0].stats, 5 * sizeof(int32_t), cudaMemcpyDeviceToHost, s->stream));
     CK(cudaStreamSynchronize(s->stream));
     drain_events(s);
     return MD_OK;
@@ -262,6 +264,7 @@ void enqueue_bin(md_system* s, const DevState& a, cudaStream_t st) {
     launch_scatter(a, s->atom_cell, a.cell_start, s->cursor, s->slot_key, s->slot_src, st);
     launch_cell_sort(g, a.cell_start, s->slot_key, s->slot_src, s->sorted_src, st);
     launch_gather(a, s->st[1], g, s->sorted_src, s->atom_cell, st);
+    launch_classify_blocks(a, g, st);
 }
 
 int do_bin(md_system* s, int p = 0) {
@@ -331,6 +334,23 @@ int do_build(md_system* s, int p = 0) {
             s->list_entries = (int64_t)sum;
             s->n_builds++;
             s->lists_valid = true;
+            // a system with a tenth or more of its blocks empty runs the full-list mixed
+            // force kernel and the list builder over its occupied blocks, with a grid sized
+            // for the occupied count plus headroom (more blocks later only loop further).  A
+            // rebuild inside a graph keeps the grid of the last host-side build; a new grid
+            // recaptures the graphs, and is only taken when the count outgrew the old one or
+            // fell well below it.
+            const int nocc = (int)s->h_flags[6];
+            int want = 0;
+            if (!s->no_compact && mixed(s) && !half(s) && 10 * (s->g.nblock - nocc) >= s->g.nblock)
+                want = std::min(s->g.nblock, nocc + nocc / 8 + 152);
+            if (want == 0 || s->compact == 0 || want > s->compact || 2 * want < s->compact) {
+                if (want != s->compact) {
+                    s->compact = want;
+                    for (int k = 0; k < 3; ++k) s->st[k].compact = want;
+                    s->graphs_valid = false;
+                }
+            }
             // keep the tile capacity close to the need (max_tile counts the dummy slot) so
             // that more CTAs fit per SM and every shared-memory layout stays within limits
             // (25 % headroom: later rebuilds inside graph-launched steps reuse this capacity)
@@ -923,6 +943,8 @@ int md_create(int64_t n, const double box[3], double r_cut, double skin, const m
         s->use_graphs = !(ng && ng[0] && ng[0] != '0');
         const char* nf = std::getenv("MDGB_NO_FUSE");
         s->no_fuse = nf && nf[0] && nf[0] != '0';
+        const char* nc = std::getenv("MDGB_NO_COMPACT");
+        s->no_compact = nc && nc[0] && nc[0] != '0';
     }
     s->n = n;
     s->np = round_up((int)std::max<int64_t>(n, 1), 64);
@@ -999,7 +1021,8 @@ int md_create(int64_t n, const double box[3], double r_cut, double skin, const m
         return bail(rc);
     if ((rc = dalloc(s, &d0.cell_start, (size_t)g.ncell + 1)) || (rc = dalloc(s, &d0.centre, 3 * (size_t)g.ncell)) ||
         (rc = dalloc(s, &d0.nl_cnt, n)) ||
-        (rc = dalloc(s, &d0.err, 1)) || (rc = dalloc(s, &d0.rebuild_flag, 1)) || (rc = dalloc(s, &d0.stats, 8)))
+        (rc = dalloc(s, &d0.err, 1)) || (rc = dalloc(s, &d0.rebuild_flag, 1)) || (rc = dalloc(s, &d0.stats, 8)) ||
+        (rc = dalloc(s, &d0.blk_list, (size_t)g.nblock)))
         return bail(rc);
     if (p->precision == MD_MIXED) {
         if ((rc = dalloc(s, &d0.fq, 3 * (size_t)n)) || (rc = dalloc(s, &d0.pe_atom_f, n)) ||
@@ -1034,6 +1057,7 @@ int md_create(int64_t n, const double box[3], double r_cut, double skin, const m
         d1.err = d0.err;
         d1.rebuild_flag = d0.rebuild_flag;
         d1.stats = d0.stats;
+        d1.blk_list = d0.blk_list;
         d1.fq = d0.fq;
         d1.f = d0.f;
         d1.pe_atom_f = d0.pe_atom_f;

@@ -272,4 +272,31 @@ void launch_gather(const DevState& s, const DevState& scratch, const Geometry& g
     k_copy_back<<<nb, bs, 0, st>>>(s, scratch);
 }
 
+// ---------------------------------------------------------------- occupied blocks
+// Own-atom count of every block after binning (its 8 cells are consecutive in the
+// block-major cell numbering); the ids of the blocks with atoms go to blk_list (spatial
+// order within each warp's 32 blocks, warps in the order they reach the counter) and their
+// number to stats[4].  The order of the list does not affect any result: each block writes
+// only its own atoms.
+__global__ void k_classify_blocks(DevState s, Geometry g) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    bool occ = false;
+    int b = 0;
+    if (k < g.nblock) {
+        b = spatial_block(g, k);
+        occ = s.cell_start[8 * b + 8] > s.cell_start[8 * b];
+    }
+    const unsigned mo = __ballot_sync(0xffffffffu, occ);
+    const int lane = threadIdx.x & 31;
+    int base = 0;
+    if (lane == 0 && mo) base = atomicAdd(&s.stats[4], __popc(mo));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (occ) s.blk_list[base + __popc(mo & ((1u << lane) - 1u))] = b;
+}
+
+void launch_classify_blocks(const DevState& s, const Geometry& g, cudaStream_t st) {
+    cudaMemsetAsync(s.stats + 4, 0, sizeof(int32_t), st);
+    k_classify_blocks<<<(g.nblock + 255) / 256, 256, 0, st>>>(s, g);
+}
+
 }  // namespace mdgb

@@ -260,11 +260,14 @@ __device__ __forceinline__ void finish_atom_warp(const DevState& s, const Geomet
 //             staging this atom's current FP32 coordinates or testing a pair near r_cut
 //             with its current FP64 position), the new FP32 coordinates beside it, and
 //             the skin/2 displacement test.  The force itself is not stored.
+//
+// full_block is the task of block b for the CTA that calls it; k_force_mixed_full runs one
+// block per CTA in spatial order, k_force_mixed_occ loops over the occupied blocks of a
+// compact system.
 template <bool SINGLE, bool EV, int MODE>
-__global__ void __maxnreg__(SINGLE ? MDGB_FULL_MAX_REGS : MDGB_FULL_MAX_REGS_SPECIES) k_force_mixed_full(DevState s, Geometry g, PairTable pt,
-                                                                TileOffsets to, int tile_cap, float fs2_max,
-                                                                StepOut out, double dt,
-                                                                float lim2_f) {
+__device__ __forceinline__ void full_block(const DevState& s, const Geometry& g, const PairTable& pt,
+                                           const TileOffsets& to, int tile_cap, float fs2_max, const StepOut& out,
+                                           double dt, float lim2_f, int b) {
     static_assert(!EV || MODE == FM_FORCE, "energy/virial launches only evaluate forces");
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ TileMeta m;
@@ -273,7 +276,6 @@ __global__ void __maxnreg__(SINGLE ? MDGB_FULL_MAX_REGS : MDGB_FULL_MAX_REGS_SPE
     __shared__ WarpWide wwide[FULL_THREADS / 32];
     float4* tile = reinterpret_cast<float4*>(smem);
     uint16_t* queued = reinterpret_cast<uint16_t*>(tile + tile_cap);  // own atoms left to finish_atom_warp
-    const int b = spatial_block(g, blockIdx.x);
     load_species_table(pt, stab);
     if (threadIdx.x == 0) nqueued = 0;
     tile_meta(g, s.cell_start, b, m);
@@ -405,6 +407,29 @@ __global__ void __maxnreg__(SINGLE ? MDGB_FULL_MAX_REGS : MDGB_FULL_MAX_REGS_SPE
     for (int k = threadIdx.x >> 5; k < nq; k += blockDim.x >> 5)
         finish_atom_warp<SINGLE, EV, MODE>(s, g, pt, tile, stab, m, queued[k], fs2_max, out, dt, lim2_f,
                                            wwide[threadIdx.x >> 5]);
+}
+
+template <bool SINGLE, bool EV, int MODE>
+__global__ void __maxnreg__(SINGLE ? MDGB_FULL_MAX_REGS : MDGB_FULL_MAX_REGS_SPECIES) k_force_mixed_full(DevState s, Geometry g, PairTable pt,
+                                                                TileOffsets to, int tile_cap, float fs2_max,
+                                                                StepOut out, double dt,
+                                                                float lim2_f) {
+    full_block<SINGLE, EV, MODE>(s, g, pt, to, tile_cap, fs2_max, out, dt, lim2_f, spatial_block(g, blockIdx.x));
+}
+
+// The same over the occupied blocks of a compact system: a grid of s.compact CTAs, each
+// taking every gridDim-th entry of the list.  (A separate kernel: the loop in the
+// one-block kernel cost the dense case 10 % through its register allocation.)
+template <bool SINGLE, bool EV, int MODE>
+__global__ void __maxnreg__(SINGLE ? MDGB_FULL_MAX_REGS : MDGB_FULL_MAX_REGS_SPECIES) k_force_mixed_occ(DevState s, Geometry g, PairTable pt,
+                                                                TileOffsets to, int tile_cap, float fs2_max,
+                                                                StepOut out, double dt,
+                                                                float lim2_f) {
+    const int count = s.stats[4];
+    for (int k = blockIdx.x; k < count; k += gridDim.x) {
+        full_block<SINGLE, EV, MODE>(s, g, pt, to, tile_cap, fs2_max, out, dt, lim2_f, s.blk_list[k]);
+        __syncthreads();  // the next block reuses the shared memory
+    }
 }
 
 // ---------------------------------------------------------------- mixed, half list, one colour
@@ -599,6 +624,14 @@ void init_force_kernels() {
     allow_max_smem(k_force_mixed_full<false, false, FM_KICK>);
     allow_max_smem(k_force_mixed_full<true, false, FM_KKD>);
     allow_max_smem(k_force_mixed_full<false, false, FM_KKD>);
+    allow_max_smem(k_force_mixed_occ<true, false, FM_FORCE>);
+    allow_max_smem(k_force_mixed_occ<true, true, FM_FORCE>);
+    allow_max_smem(k_force_mixed_occ<false, false, FM_FORCE>);
+    allow_max_smem(k_force_mixed_occ<false, true, FM_FORCE>);
+    allow_max_smem(k_force_mixed_occ<true, false, FM_KICK>);
+    allow_max_smem(k_force_mixed_occ<false, false, FM_KICK>);
+    allow_max_smem(k_force_mixed_occ<true, false, FM_KKD>);
+    allow_max_smem(k_force_mixed_occ<false, false, FM_KKD>);
     allow_max_smem(k_force_mixed_half<true, false>);
     allow_max_smem(k_force_mixed_half<true, true>);
     allow_max_smem(k_force_mixed_half<false, false>);
@@ -613,6 +646,20 @@ static float fs2_max_of(const PairTable& pt) {
     return 4194304.0f / sqrtf(rcmax2) * 0.999f;
 }
 
+// One full-list launch: a CTA per block, or with a compact system a grid of s.compact CTAs
+// over the occupied blocks.
+template <bool SINGLE, bool EV, int MODE>
+static void launch_full(const DevState& s, const Geometry& g, const PairTable& pt, const TileOffsets& to,
+                        int tile_cap, float fs2_max, StepOut out, double dt, float lim2_f, size_t smem,
+                        cudaStream_t st) {
+    if (s.compact)
+        k_force_mixed_occ<SINGLE, EV, MODE><<<s.compact, FULL_THREADS, smem, st>>>(s, g, pt, to, tile_cap, fs2_max,
+                                                                                 out, dt, lim2_f);
+    else
+        k_force_mixed_full<SINGLE, EV, MODE><<<g.nblock, FULL_THREADS, smem, st>>>(s, g, pt, to, tile_cap, fs2_max,
+                                                                                 out, dt, lim2_f);
+}
+
 void launch_forces_mixed(const DevState& s, const Geometry& g, const PairTable& pt, const TileOffsets& to,
                          int tile_cap, int half, int with_energy, cudaStream_t st) {
     if (s.n == 0) return;
@@ -621,17 +668,13 @@ void launch_forces_mixed(const DevState& s, const Geometry& g, const PairTable& 
     const bool single = pt.nsp == 1;
     if (!half) {
         if (single && !with_energy)
-            k_force_mixed_full<true, false, FM_FORCE><<<g.nblock, FULL_THREADS, smem, st>>>(s, g, pt, to, tile_cap,
-                                                                                          fs2_max, StepOut{}, 0.0, 0.f);
+            launch_full<true, false, FM_FORCE>(s, g, pt, to, tile_cap, fs2_max, StepOut{}, 0.0, 0.f, smem, st);
         else if (single)
-            k_force_mixed_full<true, true, FM_FORCE><<<g.nblock, FULL_THREADS, smem, st>>>(s, g, pt, to, tile_cap,
-                                                                                         fs2_max, StepOut{}, 0.0, 0.f);
+            launch_full<true, true, FM_FORCE>(s, g, pt, to, tile_cap, fs2_max, StepOut{}, 0.0, 0.f, smem, st);
         else if (!with_energy)
-            k_force_mixed_full<false, false, FM_FORCE><<<g.nblock, FULL_THREADS, smem, st>>>(s, g, pt, to, tile_cap,
-                                                                                           fs2_max, StepOut{}, 0.0, 0.f);
+            launch_full<false, false, FM_FORCE>(s, g, pt, to, tile_cap, fs2_max, StepOut{}, 0.0, 0.f, smem, st);
         else
-            k_force_mixed_full<false, true, FM_FORCE><<<g.nblock, FULL_THREADS, smem, st>>>(s, g, pt, to, tile_cap,
-                                                                                          fs2_max, StepOut{}, 0.0, 0.f);
+            launch_full<false, true, FM_FORCE>(s, g, pt, to, tile_cap, fs2_max, StepOut{}, 0.0, 0.f, smem, st);
         return;
     }
     cudaMemsetAsync(s.fq, 0, sizeof(long long) * 3 * (size_t)s.n, st);
@@ -655,8 +698,7 @@ template <bool SINGLE, int MODE>
 static void launch_full_mode(const DevState& s, const Geometry& g, const PairTable& pt, const TileOffsets& to,
                              int tile_cap, float fs2_max, StepOut out, double dt, float lim2_f, size_t smem,
                              cudaStream_t st) {
-    k_force_mixed_full<SINGLE, false, MODE><<<g.nblock, FULL_THREADS, smem, st>>>(s, g, pt, to, tile_cap, fs2_max,
-                                                                                out, dt, lim2_f);
+    launch_full<SINGLE, false, MODE>(s, g, pt, to, tile_cap, fs2_max, out, dt, lim2_f, smem, st);
 }
 
 void launch_forces_mixed_fused(const DevState& s, const Geometry& g, const PairTable& pt, const TileOffsets& to,

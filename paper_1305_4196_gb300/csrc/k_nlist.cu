@@ -210,10 +210,10 @@ __device__ __forceinline__ void tile_stage_soa(const TileMeta& m, const int* __r
 // cell at most, plus one group of read-ahead past the last cell.
 __host__ __device__ inline int soa_len(int tile_cap) { return (tile_cap + 64 * 3 + 32 + 3) & ~3; }
 
+// The lists of the own atoms of block b (the CTA's task).
 template <int HALF>
-__global__ void __launch_bounds__(NL_WARPS * 32, 3) k_build_lists(DevState s, Geometry g, TileOffsets to,
-                                                                  double rl2, float band_lo, float band_hi,
-                                                                  int list_cap, int tile_cap) {
+__device__ __forceinline__ void build_block(const DevState& s, const Geometry& g, const TileOffsets& to, double rl2,
+                                            float band_lo, float band_hi, int list_cap, int tile_cap, int b) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ TileMeta m;
     __shared__ int pp[65];
@@ -223,7 +223,6 @@ __global__ void __launch_bounds__(NL_WARPS * 32, 3) k_build_lists(DevState s, Ge
     float* tz = ty + SL;
     uint16_t* buf = reinterpret_cast<uint16_t*>(tz + SL);  // NL_WARPS x NL_RING x 32
 
-    const int b = spatial_block(g, blockIdx.x);
     tile_meta(g, s.cell_start, b, m);
     const int T = m.prefix[64];
     if (threadIdx.x == 0) atomicMax(&s.stats[1], T + 1);
@@ -296,6 +295,26 @@ __global__ void __launch_bounds__(NL_WARPS * 32, 3) k_build_lists(DevState s, Ge
     }
 }
 
+// One CTA per block in spatial order.
+template <int HALF>
+__global__ void __launch_bounds__(NL_WARPS * 32, 3) k_build_lists(DevState s, Geometry g, TileOffsets to,
+                                                                  double rl2, float band_lo, float band_hi,
+                                                                  int list_cap, int tile_cap) {
+    build_block<HALF>(s, g, to, rl2, band_lo, band_hi, list_cap, tile_cap, spatial_block(g, blockIdx.x));
+}
+
+// A compact system: a grid of s.compact CTAs over the occupied blocks.
+template <int HALF>
+__global__ void __launch_bounds__(NL_WARPS * 32, 3) k_build_lists_occ(DevState s, Geometry g, TileOffsets to,
+                                                                      double rl2, float band_lo, float band_hi,
+                                                                      int list_cap, int tile_cap) {
+    const int count = s.stats[4];
+    for (int k = blockIdx.x; k < count; k += gridDim.x) {
+        build_block<HALF>(s, g, to, rl2, band_lo, band_hi, list_cap, tile_cap, s.blk_list[k]);
+        __syncthreads();  // the next block reuses the shared memory
+    }
+}
+
 static size_t nl_smem_bytes(int list_cap, int tile_cap) {
     (void)list_cap;
     return (size_t)soa_len(tile_cap) * 3 * sizeof(float) + (size_t)NL_WARPS * 32 * NL_RING * 2;
@@ -307,6 +326,11 @@ void launch_build_lists(const DevState& s, const Geometry& g, const TileOffsets&
     size_t smem = nl_smem_bytes(list_cap, tile_cap);
     float lo = (float)(rl2 * (1.0 - 1e-4));
     float hi = (float)(rl2 * (1.0 + 1e-4));
+    if (s.compact) {
+        if (half) k_build_lists_occ<1><<<s.compact, NL_WARPS * 32, smem, st>>>(s, g, to, rl2, lo, hi, list_cap, tile_cap);
+        else k_build_lists_occ<0><<<s.compact, NL_WARPS * 32, smem, st>>>(s, g, to, rl2, lo, hi, list_cap, tile_cap);
+        return;
+    }
     if (half) k_build_lists<1><<<g.nblock, NL_WARPS * 32, smem, st>>>(s, g, to, rl2, lo, hi, list_cap, tile_cap);
     else k_build_lists<0><<<g.nblock, NL_WARPS * 32, smem, st>>>(s, g, to, rl2, lo, hi, list_cap, tile_cap);
 }
@@ -326,6 +350,8 @@ static void allow_max_smem(K kernel) {
 void init_list_kernels() {
     allow_max_smem(k_build_lists<0>);
     allow_max_smem(k_build_lists<1>);
+    allow_max_smem(k_build_lists_occ<0>);
+    allow_max_smem(k_build_lists_occ<1>);
 }
 
 // ---------------------------------------------------------------- export

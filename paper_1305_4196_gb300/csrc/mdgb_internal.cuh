@@ -223,7 +223,14 @@ struct DevState {
     double *vir_atom_d;     // FP64 path, 6 x n
     uint32_t *err;          // sticky error bits
     int32_t *rebuild_flag;  // set when some atom moved more than skin/2
-    int32_t *stats;         // [0] max list length, [1] max tile size, [2..3] sum of list lengths (u64)
+    int32_t *stats;         // [0] max list length, [1] max tile size, [2..3] sum of list lengths (u64),
+                            // [4] occupied blocks (k_classify_blocks)
+    // The occupied blocks (own atoms > 0) in spatial order, listed after every binning.  With
+    // compact > 0 the full-list mixed force kernel and the list builder run a grid of
+    // `compact` CTAs over this list instead of one CTA per block: a system that is mostly
+    // vacuum then pays nothing for its empty blocks.
+    int32_t *blk_list;
+    int compact;
 };
 
 // ---- kernel launchers (defined in the .cu files)
@@ -237,6 +244,7 @@ void launch_cell_sort(const Geometry& g, const int32_t* cell_start, const int32_
                       const int32_t* slot_src, int32_t* sorted_src, cudaStream_t st);
 void launch_gather(const DevState& s, const DevState& scratch, const Geometry& g, const int32_t* sorted_src,
                    const int32_t* atom_cell, cudaStream_t st);
+void launch_classify_blocks(const DevState& s, const Geometry& g, cudaStream_t st);
 void launch_step_ctrl(int policy, int every_k, int32_t* rebuild_flag, long long* step_counter,
                       long long* n_builds, uint32_t* err, cudaGraphConditionalHandle handle, cudaStream_t st);
 void launch_count_build(long long* n_builds, cudaStream_t st);
