@@ -51,7 +51,9 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--inner", type=int, default=100, help="MD time steps per benchmark step")
     p.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
-    p.add_argument("--list", default="full", choices=["full", "half"])
+    p.add_argument("--list", default="full", choices=["full", "half", "half_af"],
+                   help="neighbour lists: full, half (8 colours, shared-memory atomics) or half_af (8 colours, "
+                        "no atomics)")
     p.add_argument("--workload", default="lj_liquid_2048000", choices=sorted(WORKLOADS))
     p.add_argument("--no-extras", action="store_true", help="skip the FP64 / half-list comparison runs")
     p.add_argument("--cpu-steps", type=int, default=4,
@@ -280,7 +282,7 @@ def run_ours(args):
 
     stream = torch.cuda.Stream()
     prec = M.MD_MIXED if args.precision == "mixed" else M.MD_FP64
-    lst = M.MD_LIST_FULL if args.list == "full" else M.MD_LIST_HALF_COLOUR8
+    lst = {"full": M.MD_LIST_FULL, "half": M.MD_LIST_HALF_COLOUR8, "half_af": M.MD_LIST_HALF_ATOMIC_FREE}[args.list]
     s = M.System(sysm.n, sysm.box, precision=prec, list_kind=lst, stream=stream.cuda_stream)
     s.set_state(sysm.pos, sysm.vel, sysm.species)
 
@@ -421,7 +423,8 @@ def comparisons(args, sysm, M, stream, value, list_len_hom, hom=None):
         # state, all timed (the cold slab and particles contract, so lists lengthen as it runs)
         inh = make_workload("slab_nanoparticles_1192114")
         s = M.System(inh.n, inh.box, precision=M.MD_MIXED if args.precision == "mixed" else M.MD_FP64,
-                     list_kind=M.MD_LIST_FULL if args.list == "full" else M.MD_LIST_HALF_COLOUR8,
+                     list_kind={"full": M.MD_LIST_FULL, "half": M.MD_LIST_HALF_COLOUR8,
+                                "half_af": M.MD_LIST_HALF_ATOMIC_FREE}[args.list],
                      stream=stream.cuda_stream)
         s.set_state(inh.pos, inh.vel, inh.species)
         s.forces()
@@ -475,8 +478,11 @@ def comparisons(args, sysm, M, stream, value, list_len_hom, hom=None):
     runs = []
     if args.precision == "mixed":
         runs.append(("fp64_gpu", M.MD_FP64, M.MD_LIST_FULL, 100, 2))  # 200 timed steps, with rebuilds
-    runs.append(("half_colour8_mixed" if args.list == "full" else "full_mixed", M.MD_MIXED,
-                 M.MD_LIST_HALF_COLOUR8 if args.list == "full" else M.MD_LIST_FULL, args.inner, 3))
+    if args.list == "full":
+        runs.append(("half_colour8_mixed", M.MD_MIXED, M.MD_LIST_HALF_COLOUR8, args.inner, 3))
+        runs.append(("half_atomic_free_mixed", M.MD_MIXED, M.MD_LIST_HALF_ATOMIC_FREE, args.inner, 3))
+    else:
+        runs.append(("full_mixed", M.MD_MIXED, M.MD_LIST_FULL, args.inner, 3))
     for name, prec, lst, inner, steps in runs:
         s = M.System(sysm.n, sysm.box, precision=prec, list_kind=lst, stream=stream.cuda_stream)
         s.set_state(sysm.pos, sysm.vel, sysm.species)

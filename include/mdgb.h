@@ -59,6 +59,16 @@ extern "C" {
 /* ---- md_params.list_kind */
 #define MD_LIST_FULL         0  /* every pair in both atoms' lists; each list owned by one thread, no writes to j */
 #define MD_LIST_HALF_COLOUR8 1  /* each pair once (Newton's third law); forces in 8 colour phases of 2x2x2-cell blocks */
+/* Each pair once, and the forces evaluated with no atomic operation: the 8 colour phases of
+ * blocks (Sec. II.B waves), inside a block 14 phases over
+ * the half shell (the cell, then its 13 forward cells; Sec. II.D.3) separated by barriers,
+ * in which the 8 cells of the block write 8 different cells, and inside a cell's warp a
+ * schedule whose every step names distinct target atoms - the rule of Sec. II.A that no
+ * particle is updated by two workers at once, down to the threads.  (A kernel that finds a
+ * fault sets an error bit atomically, and the list build sums its statistics with one atomic
+ * per warp; neither touches a force.)  MD_MIXED only; cells of at most 63 atoms (a denser
+ * cell returns MD_ERR_CELL_OVERFLOW). */
+#define MD_LIST_HALF_ATOMIC_FREE 2
 
 /* ---- md_params.rebuild */
 #define MD_REBUILD_SKIN_HALF 0  /* rebuild when some atom moved more than skin/2 since the last build (default) */
@@ -74,7 +84,7 @@ typedef struct {
     const double *mass;    /* n_species */
     double dt;             /* time step */
     int32_t precision;     /* MD_FP64 | MD_MIXED */
-    int32_t list_kind;     /* MD_LIST_FULL | MD_LIST_HALF_COLOUR8 */
+    int32_t list_kind;     /* MD_LIST_FULL | MD_LIST_HALF_COLOUR8 | MD_LIST_HALF_ATOMIC_FREE */
     int32_t rebuild;       /* MD_REBUILD_SKIN_HALF | MD_REBUILD_EVERY_K */
     int32_t rebuild_k;     /* interval for MD_REBUILD_EVERY_K */
     void *stream;          /* cudaStream_t, or NULL for the legacy default stream */

@@ -141,7 +141,20 @@ void dfree(md_system* s, void* p) {
 }
 
 bool mixed(const md_system* s) { return s->precision == MD_MIXED; }
-bool half(const md_system* s) { return s->list_kind == MD_LIST_HALF_COLOUR8; }
+bool half(const md_system* s) { return s->list_kind != MD_LIST_FULL; }
+// the half list evaluated with no atomic operation (k_half_af.cu)
+bool af(const md_system* s) { return s->list_kind == MD_LIST_HALF_ATOMIC_FREE; }
+// shared memory of the list build / of a force launch for this system's kernels
+size_t list_smem(const md_system* s, int list_cap, int tile_cap) {
+    return af(s) ? af_sched_smem_bytes(tile_cap) : build_lists_smem(list_cap, tile_cap);
+}
+size_t fsmem(const md_system* s, int with_energy, int tile_cap) {
+    return af(s) ? af_force_smem_bytes(tile_cap) : force_smem_bytes(mixed(s), half(s), with_energy, tile_cap);
+}
+void enqueue_lists(const md_system* s, const DevState& a, cudaStream_t st) {
+    if (af(s)) launch_build_sched(a, s->g, s->to, s->rl2, s->list_cap, s->tile_cap, st);
+    else launch_build_lists(a, s->g, s->to, s->rl2, s->list_cap, s->tile_cap, half(s), st);
+}
 // md_step runs the full-list mixed path with velocity Verlet fused into the force kernel
 bool fused(const md_system* s) { return mixed(s) && !half(s) && !s->no_fuse && s->potential == 0; }
 // kernels per force evaluation: 8 colour launches (half lists), two passes (TB-SMA), else one
@@ -251,6 +264,8 @@ int check_err(md_system* s, uint32_t mask) {
     if (e & ERR_SKIN) return fail(s, MD_ERR_SKIN_VIOLATION, "an atom moved more than skin/2 between rebuilds");
     if (e & ERR_LIST_OVERFLOW) return fail(s, MD_ERR_LIST_OVERFLOW, "neighbour list overflow");
     if (e & ERR_TILE_OVERFLOW) return fail(s, MD_ERR_CELL_OVERFLOW, "tile overflow");
+    if (e & ERR_CELL_DENSE)
+        return fail(s, MD_ERR_CELL_OVERFLOW, "a cell above 63 atoms or a phase above 255 steps (atom-free half list)");
     return fail(s, MD_ERR_ARG, "device error 0x%x", e);
 }
 
@@ -294,10 +309,10 @@ int do_build(md_system* s, int p = 0) {
         const DevState a = view(s, p);
         CK(cudaMemsetAsync(a.stats, 0, 4 * sizeof(int32_t), s->stream));
         CK(cudaMemsetAsync(a.err, 0, sizeof(uint32_t), s->stream));
-        if (build_lists_smem(s->list_cap, s->tile_cap) > 226 * 1024)
+        if (list_smem(s, s->list_cap, s->tile_cap) > 226 * 1024)
             return fail(s, MD_ERR_CELL_OVERFLOW, "tile (%d atoms) and lists (%d) exceed shared memory",
                         s->tile_cap, s->list_cap);
-        launch_build_lists(a, s->g, s->to, s->rl2, s->list_cap, s->tile_cap, half(s), s->stream);
+        enqueue_lists(s, a, s->stream);
         CKL();
         s->launches += 1;
         if (ev.second) {
@@ -366,6 +381,7 @@ int do_build(md_system* s, int p = 0) {
 void enqueue_forces(md_system* s, int with_energy, cudaStream_t st) {
     const DevState& a = s->st[0];
     if (s->potential == 1) launch_tbsma(a, s->g, s->tb, s->to, s->tile_cap, s->emb, with_energy, st);
+    else if (mixed(s) && af(s)) launch_forces_half_af(a, s->g, s->pt, s->to, s->tile_cap, fs2_max_of(s->pt), with_energy, st);
     else if (mixed(s)) launch_forces_mixed(a, s->g, s->pt, s->to, s->tile_cap, half(s), with_energy, st);
     else launch_forces_fp64(a, s->g, s->pt, s->tile_cap, half(s), with_energy, st);
 }
@@ -383,9 +399,10 @@ int do_forces(md_system* s, int with_energy) {
             return fail(s, MD_ERR_CELL_OVERFLOW, "tile of %d atoms exceeds shared memory", s->tile_cap);
         launch_tbsma(a, s->g, s->tb, s->to, s->tile_cap, s->emb, with_energy, s->stream);
     } else if (mixed(s)) {
-        if (force_smem_bytes(1, half(s), with_energy, s->tile_cap) > 226 * 1024)
+        if (fsmem(s, with_energy, s->tile_cap) > 226 * 1024)
             return fail(s, MD_ERR_CELL_OVERFLOW, "tile of %d atoms exceeds shared memory", s->tile_cap);
-        launch_forces_mixed(a, s->g, s->pt, s->to, s->tile_cap, half(s), with_energy, s->stream);
+        if (af(s)) launch_forces_half_af(a, s->g, s->pt, s->to, s->tile_cap, fs2_max_of(s->pt), with_energy, s->stream);
+        else launch_forces_mixed(a, s->g, s->pt, s->to, s->tile_cap, half(s), with_energy, s->stream);
     } else {
         if (force_smem_bytes(0, half(s), with_energy, s->tile_cap) > 226 * 1024)
             return fail(s, MD_ERR_CELL_OVERFLOW, "tile of %d atoms exceeds shared memory", s->tile_cap);
@@ -446,8 +463,11 @@ int validate_params(md_system* s, const md_params* p, double r_cut) {
     if (!p->eps || !p->sigma || !p->mass) return fail(s, MD_ERR_ARG, "eps, sigma and mass are required");
     if (!(p->dt > 0.0) || !std::isfinite(p->dt)) return fail(s, MD_ERR_ARG, "dt must be positive");
     if (p->precision != MD_FP64 && p->precision != MD_MIXED) return fail(s, MD_ERR_ARG, "bad precision");
-    if (p->list_kind != MD_LIST_FULL && p->list_kind != MD_LIST_HALF_COLOUR8)
+    if (p->list_kind != MD_LIST_FULL && p->list_kind != MD_LIST_HALF_COLOUR8 &&
+        p->list_kind != MD_LIST_HALF_ATOMIC_FREE)
         return fail(s, MD_ERR_ARG, "bad list kind");
+    if (p->list_kind == MD_LIST_HALF_ATOMIC_FREE && p->precision != MD_MIXED)
+        return fail(s, MD_ERR_ARG, "MD_LIST_HALF_ATOMIC_FREE needs MD_MIXED");
     if (p->rebuild != MD_REBUILD_SKIN_HALF && p->rebuild != MD_REBUILD_EVERY_K)
         return fail(s, MD_ERR_ARG, "bad rebuild policy");
     if (p->rebuild == MD_REBUILD_EVERY_K && p->rebuild_k < 1) return fail(s, MD_ERR_ARG, "rebuild_k must be >= 1");
@@ -527,7 +547,7 @@ int capture_step(md_system* s, int mode, md_system::StepGraph& out) {
     CK(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
     enqueue_bin(s, a, cs);
     cudaMemsetAsync(a.stats, 0, 4 * sizeof(int32_t), cs);
-    launch_build_lists(a, s->g, s->to, s->rl2, s->list_cap, s->tile_cap, half(s), cs);
+    enqueue_lists(s, a, cs);
     launch_count_build(s->d_ctrl + 1, cs);
     CK(cudaStreamEndCapture(cs, &body));
     CKL();
@@ -881,8 +901,8 @@ int ensure_headroom(md_system* s) {
     }
     if (s->max_tile + std::max(64, s->max_tile / 8) > s->tile_cap) {
         const int cap = std::min(round_up(s->max_tile + s->max_tile / 4 + 64, 32), round_up((int)s->n + 1, 32));
-        if (cap > s->tile_cap && cap <= 32767 && build_lists_smem(s->list_cap, cap) <= 226 * 1024 &&
-            force_smem_bytes(mixed(s), half(s), 0, cap) <= 226 * 1024)
+        if (cap > s->tile_cap && cap <= 32767 && list_smem(s, s->list_cap, cap) <= 226 * 1024 &&
+            fsmem(s, 0, cap) <= 226 * 1024)
             s->tile_cap = cap;
     }
     return MD_OK;
@@ -938,6 +958,7 @@ int md_create(int64_t n, const double box[3], double r_cut, double skin, const m
     init_list_kernels();
     init_grad_kernels();
     init_tbsma_kernels();
+    init_half_af_kernels();
     {
         const char* ng = std::getenv("MDGB_NO_GRAPHS");
         s->use_graphs = !(ng && ng[0] && ng[0] != '0');
@@ -1022,7 +1043,8 @@ int md_create(int64_t n, const double box[3], double r_cut, double skin, const m
     if ((rc = dalloc(s, &d0.cell_start, (size_t)g.ncell + 1)) || (rc = dalloc(s, &d0.centre, 3 * (size_t)g.ncell)) ||
         (rc = dalloc(s, &d0.nl_cnt, n)) ||
         (rc = dalloc(s, &d0.err, 1)) || (rc = dalloc(s, &d0.rebuild_flag, 1)) || (rc = dalloc(s, &d0.stats, 8)) ||
-        (rc = dalloc(s, &d0.blk_list, (size_t)g.nblock)))
+        (rc = dalloc(s, &d0.blk_list, (size_t)g.nblock)) ||
+        (p->list_kind == MD_LIST_HALF_ATOMIC_FREE && (rc = dalloc(s, &d0.af_steps, (size_t)g.nblock * 8 * 14 * 2))))
         return bail(rc);
     if (p->precision == MD_MIXED) {
         if ((rc = dalloc(s, &d0.fq, 3 * (size_t)n)) || (rc = dalloc(s, &d0.pe_atom_f, n)) ||
@@ -1058,6 +1080,7 @@ int md_create(int64_t n, const double box[3], double r_cut, double skin, const m
         d1.rebuild_flag = d0.rebuild_flag;
         d1.stats = d0.stats;
         d1.blk_list = d0.blk_list;
+        d1.af_steps = d0.af_steps;
         d1.fq = d0.fq;
         d1.f = d0.f;
         d1.pe_atom_f = d0.pe_atom_f;

@@ -640,7 +640,7 @@ void init_force_kernels() {
 }
 
 // |fs2 * d| < 2^22 (the exact range of the two-part split) is guaranteed when |fs2| < 2^22 / r_cut
-static float fs2_max_of(const PairTable& pt) {
+float fs2_max_of(const PairTable& pt) {
     float rcmax2 = 0.f;
     for (int t = 0; t < pt.nsp * pt.nsp; ++t) rcmax2 = pt.rc2_f[t] > rcmax2 ? pt.rc2_f[t] : rcmax2;
     return 4194304.0f / sqrtf(rcmax2) * 0.999f;

@@ -371,6 +371,7 @@ __global__ void k_pairs_out(DevState s, Geometry g, int half, unsigned long long
         const uint16_t* rows = s.nl;
         for (int k = 0; k < cnt; ++k) {
             const int u = rows[((size_t)(k >> 3) * s.np + gi) * 8 + (k & 7)];
+            if (u >= m.prefix[64]) continue;  // an idle step of an atom-free schedule
             const int slot = tile_slot_of(m, u);
             const int gj = m.start[slot] + (u - m.prefix[slot]);
             const int oj = s.orig[gj];

@@ -27,6 +27,7 @@ enum : uint32_t {
     ERR_NONFINITE = 4u,       // non-finite pair force or coordinates
     ERR_ESCAPE = 8u,          // an atom moved more than one box length between builds
     ERR_SKIN = 16u,           // displacement > skin/2 under the fixed-interval policy
+    ERR_CELL_DENSE = 32u,     // atom-free half list: a cell above 63 atoms or a phase above 255 steps
     ERR_CELL_COUNT = 32u,     // a cell holds more atoms than a list index can address
 };
 
@@ -231,6 +232,7 @@ struct DevState {
     // vacuum then pays nothing for its empty blocks.
     int32_t *blk_list;
     int compact;
+    uint8_t *af_steps;      // atom-free half list: steps per (block, warp, phase, pass)
 };
 
 // ---- kernel launchers (defined in the .cu files)
@@ -290,6 +292,15 @@ void launch_pairs_out(const DevState& s, const Geometry& g, int half, unsigned l
                       int32_t* pairs, long long cap, cudaStream_t st);
 
 void init_force_kernels();
+float fs2_max_of(const PairTable& pt);  // largest |fs2| the two-part split takes (k_force.cu)
+// atom-free half lists (k_half_af.cu)
+void launch_build_sched(const DevState& s, const Geometry& g, const TileOffsets& to, double rl2, int list_cap,
+                        int tile_cap, cudaStream_t st);
+void launch_forces_half_af(const DevState& s, const Geometry& g, const PairTable& pt, const TileOffsets& to,
+                           int tile_cap, float fs2_max, int with_energy, cudaStream_t st);
+size_t af_sched_smem_bytes(int tile_cap);
+size_t af_force_smem_bytes(int tile_cap);
+void init_half_af_kernels();
 void init_force_fp64_kernels();
 void init_grad_kernels();
 size_t backward_smem_bytes(int fp64, int tile_cap);

@@ -34,6 +34,7 @@ MD_FP64 = 0
 MD_MIXED = 1
 MD_LIST_FULL = 0
 MD_LIST_HALF_COLOUR8 = 1
+MD_LIST_HALF_ATOMIC_FREE = 2
 MD_REBUILD_SKIN_HALF = 0
 MD_REBUILD_EVERY_K = 1
 
