@@ -92,7 +92,7 @@ typedef struct {
 
 typedef struct {
     int64_t n;             /* atoms */
-    int32_t ncell[3];      /* cells per dimension (multiples of 4) */
+    int32_t ncell[3];      /* cells per dimension (multiples of 4, or 6 for full lists) */
     int32_t list_cap;      /* current neighbour-list capacity per atom */
     int32_t tile_cap;      /* current on-chip tile capacity (atoms of a 4x4x4-cell neighbourhood) */
     int64_t n_builds;      /* neighbour-list builds so far */
@@ -116,7 +116,10 @@ typedef struct {
  * Sec. II.A).  Picks the cell grid: per dimension the largest multiple of 4
  * cells whose width is at least r_cut + skin (Sec. II.A: cells wider than the
  * interaction range; multiples of 4 so that 2x2x2-cell blocks split into 8
- * colour classes, Sec. II.D.2 blocking).  Allocates all device workspace.
+ * colour classes, Sec. II.D.2 blocking).  MD_LIST_FULL needs no colour classes
+ * and takes 6 cells on a side where 6 fit but the rule gives 4, so that the
+ * 4x4x4-cell neighbourhood of a block is not the whole box.  At least 4 cells
+ * per side.  Allocates all device workspace.
  * Errors: MD_ERR_ARG, MD_ERR_BOX_TOO_SMALL, MD_ERR_CUDA.  *out is NULL on error.
  */
 int md_create(int64_t n, const double box[3], double r_cut, double skin,
@@ -289,7 +292,8 @@ int md_set_timing(md_system *s, int enable);
  * kernels use (conflicts must be 0); n_phases = 1 puts every block into one
  * phase, where overlapping tiles must show up.  *conflicts: the total over the
  * phases.  Debug use only (not on any timed path).  Errors: MD_ERR_ARG (n_phases
- * not 1 or 8), MD_ERR_STATE, MD_ERR_CUDA.
+ * not 1 or 8, or n_phases = 8 on a full-list grid with a side of 4k+2 cells, which
+ * has no colour classes), MD_ERR_STATE, MD_ERR_CUDA.
  */
 int md_colour_conflicts(md_system *s, int32_t n_phases, int64_t *conflicts);
 

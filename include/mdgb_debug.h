@@ -22,14 +22,19 @@
 extern "C" {
 #endif
 
-/* Cells per dimension md_create() picks for box[3] and list radius r_list
- * (largest multiple of 4 with width >= r_list).  MD_ERR_BOX_TOO_SMALL (-2) if < 4. */
-int mdgb_grid_shape(const double box[3], double r_list, int32_t nc_out[3]);
+/* Cells per dimension md_create() picks for box[3], list radius r_list and list
+ * kind list_kind (MD_LIST_*): the largest multiple of 4 with width >= r_list, or 6
+ * for MD_LIST_FULL where 6 fit and that multiple is 4.
+ * MD_ERR_BOX_TOO_SMALL (-2) if < 4. */
+int mdgb_grid_shape(const double box[3], double r_list, int32_t list_kind, int32_t nc_out[3]);
 
-/* Number of 2x2x2 blocks for a grid of nc[3] cells (nc multiples of 4). */
+/* Number of 2x2x2 blocks for a grid of nc[3] cells (even, >= 4).  Grids with every
+ * side a multiple of 4 number their blocks colour class by colour class; the
+ * others (full lists only) number them linearly, x fastest. */
 int mdgb_num_blocks(const int32_t nc[3], int32_t *nblock_out);
 
-/* Colour class (0..7) of block `block`. */
+/* Colour class (0..7) of block `block` (colour-major grids only: every nc a
+ * multiple of 4). */
 int mdgb_block_colour(const int32_t nc[3], int32_t block, int32_t *colour_out);
 
 /* The 64 cells of block `block`'s tile in tile order (own 8 cells first), as

@@ -991,27 +991,26 @@ int md_create(int64_t n, const double box[3], double r_cut, double skin, const m
     s->rl2 = s->rl * s->rl;
     const double half_skin = 0.5 * skin;
     s->lim2 = half_skin * half_skin;
-    // cell grid: per dimension the largest multiple of 4 cells at least r_list wide
+    // cell grid: per dimension the largest multiple of 4 cells at least r_list wide (8
+    // colour classes of 2x2x2 blocks); full lists, which need no colours, take 6 where
+    // that would leave 4 (a tile that is the whole box)
     Geometry& g = s->g;
     for (int d = 0; d < 3; ++d) {
         if (!(box[d] > 0.0) || !std::isfinite(box[d])) return bail(MD_ERR_ARG);
         s->box[d] = box[d];
-        int nc = (int)std::floor(box[d] / (s->rl * (1.0 + 1e-12)));
-        nc -= nc % 4;
+        const int fit = (int)std::min(std::floor(box[d] / (s->rl * (1.0 + 1e-12))), 1024.0);
+        const int nc = grid_cells(fit, s->list_kind == MD_LIST_FULL);
         if (nc < 4) {
             fail(s, MD_ERR_BOX_TOO_SMALL, "box side %g < 4 r_list", box[d]);
             return bail(MD_ERR_BOX_TOO_SMALL);
         }
-        if (nc > 1024) nc = 1024;
         g.L[d] = box[d];
         g.nc[d] = nc;
         g.w[d] = box[d] / nc;
         g.inv_w[d] = nc / box[d];
-        g.nbh[d] = nc / 4;
         for (int t = 0; t < 4; ++t) s->to.off[d][t] = (float)((t - 1.5) * g.w[d]);
     }
-    g.nblock = (g.nc[0] / 2) * (g.nc[1] / 2) * (g.nc[2] / 2);
-    g.ncell = g.nblock * 8;
+    set_block_layout(g);
     set_cut_band(s);
     // initial capacities from the mean density (regrown on overflow)
     const double vol = box[0] * box[1] * box[2];
@@ -1266,6 +1265,7 @@ int md_set_params(md_system* s, const double* eps, const double* sigma, const do
 
 int md_colour_conflicts(md_system* s, int32_t n_phases, int64_t* conflicts) {
     if (!s || !conflicts || (n_phases != 1 && n_phases != 8)) return MD_ERR_ARG;
+    if (n_phases == 8 && s->g.linear) return fail(s, MD_ERR_ARG, "linear block numbering has no colour classes");
     if (!s->has_state) return fail(s, MD_ERR_STATE, "no state");
     DeviceGuard dg(s->device);
     *conflicts = 0;

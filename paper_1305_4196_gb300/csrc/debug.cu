@@ -12,12 +12,10 @@ namespace {
 bool make_geometry(const int32_t nc[3], Geometry& g) {
     if (!nc) return false;
     for (int d = 0; d < 3; ++d) {
-        if (nc[d] < 4 || nc[d] % 4 != 0) return false;
+        if (nc[d] < 4 || nc[d] % 2 != 0 || nc[d] > 1024) return false;
         g.nc[d] = nc[d];
-        g.nbh[d] = nc[d] / 4;
     }
-    g.nblock = (nc[0] / 2) * (nc[1] / 2) * (nc[2] / 2);
-    g.ncell = g.nblock * 8;
+    set_block_layout(g);
     return true;
 }
 
@@ -25,13 +23,14 @@ bool make_geometry(const int32_t nc[3], Geometry& g) {
 
 extern "C" {
 
-int mdgb_grid_shape(const double box[3], double r_list, int32_t nc_out[3]) {
-    if (!box || !nc_out || !(r_list > 0.0)) return MD_ERR_ARG;
+int mdgb_grid_shape(const double box[3], double r_list, int32_t list_kind, int32_t nc_out[3]) {
+    if (!box || !nc_out || !(r_list > 0.0) || list_kind < MD_LIST_FULL || list_kind > MD_LIST_HALF_ATOMIC_FREE)
+        return MD_ERR_ARG;
     for (int d = 0; d < 3; ++d) {
-        int nc = (int)std::floor(box[d] / (r_list * (1.0 + 1e-12)));
-        nc -= nc % 4;
+        const int fit = (int)std::min(std::floor(box[d] / (r_list * (1.0 + 1e-12))), 1024.0);
+        const int nc = grid_cells(fit, list_kind == MD_LIST_FULL);
         if (nc < 4) return MD_ERR_BOX_TOO_SMALL;
-        nc_out[d] = nc > 1024 ? 1024 : nc;
+        nc_out[d] = nc;
     }
     return MD_OK;
 }
@@ -53,7 +52,7 @@ int mdgb_num_blocks(const int32_t nc[3], int32_t* nblock_out) {
 
 int mdgb_block_colour(const int32_t nc[3], int32_t block, int32_t* colour_out) {
     Geometry g{};
-    if (!colour_out || !make_geometry(nc, g) || block < 0 || block >= g.nblock) return MD_ERR_ARG;
+    if (!colour_out || !make_geometry(nc, g) || g.linear || block < 0 || block >= g.nblock) return MD_ERR_ARG;
     int bx, by, bz;
     block_coords(g, block, bx, by, bz);
     *colour_out = (bx & 1) | ((by & 1) << 1) | ((bz & 1) << 2);

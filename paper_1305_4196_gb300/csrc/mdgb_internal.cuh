@@ -1,16 +1,22 @@
 // mdgb_internal.cuh - shared definitions of the sm_103a kernels and the C-ABI layer.
 //
-// Cell numbering.  The box is cut into nc[d] cells per dimension (multiples
-// of 4).  Cells are grouped into 2x2x2 blocks (the paper's cell-task blocking,
-// Sec. II.D.2), blocks are grouped into 8 colour classes by the parities of
-// their block coordinates, and cells are numbered block by block, colour class
-// by colour class:
+// Cell numbering.  The box is cut into nc[d] cells per dimension (even, at
+// least 4).  Cells are grouped into 2x2x2 blocks (the paper's cell-task
+// blocking, Sec. II.D.2) and numbered block by block:
 //     cell id = block id * 8 + (lx + 2 ly + 4 lz)          (l = cell parity in its block)
-//     block id = colour * (nblock / 8) + index within colour
-// so that the atoms of one block (and of one colour class) are contiguous
-// after binning.  Two blocks of the same colour are 4 cells apart in some
-// dimension, so the 4x4x4-cell neighbourhoods ("tiles") of same-colour blocks
-// never overlap: a wave of non-overlapping tasks in the sense of Sec. II.B.
+// so that the atoms of one block are contiguous after binning.  Blocks are
+// numbered in one of two ways.
+//   Colour-major (every nc[d] a multiple of 4; all half-list systems): blocks
+//   are grouped into 8 colour classes by the parities of their block
+//   coordinates,
+//       block id = colour * (nblock / 8) + index within colour,
+//   so the atoms of one colour class are contiguous too.  Two blocks of the
+//   same colour are 4 cells apart in some dimension, so the 4x4x4-cell
+//   neighbourhoods ("tiles") of same-colour blocks never overlap: a wave of
+//   non-overlapping tasks in the sense of Sec. II.B.
+//   Linear (any other even counts; md_create picks them only for full lists
+//   with a side of 6 cells): block id = bx + nb[0] (by + nb[1] bz).  Full
+//   lists write only their own block's atoms, so they need no colour classes.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -38,8 +44,10 @@ struct Geometry {
     double L[3];       // box sides
     double w[3];       // cell widths L / nc
     double inv_w[3];   // nc / L
-    int nc[3];         // cells per dimension (multiple of 4)
-    int nbh[3];        // blocks per dimension within one colour class (= nc / 4)
+    int nc[3];         // cells per dimension (even, >= 4; multiples of 4 unless linear)
+    int nb[3];         // blocks per dimension (= nc / 2)
+    int nbh[3];        // colour-major: blocks per dimension within one colour class (= nc / 4)
+    int linear;        // 1: linear block numbering (no colour classes)
     int nblock;        // number of 2x2x2 blocks
     int ncell;         // number of cells
 };
@@ -144,12 +152,20 @@ inline double cell_frame_cut_band(double w_max, int R, double rc) {
 }
 
 __host__ __device__ inline int block_id_of(const Geometry& g, int bx, int by, int bz) {
+    if (g.linear) return bx + g.nb[0] * (by + g.nb[1] * bz);
     int col = (bx & 1) | ((by & 1) << 1) | ((bz & 1) << 2);
     int within = (bx >> 1) + g.nbh[0] * ((by >> 1) + g.nbh[1] * (bz >> 1));
     return col * (g.nblock >> 3) + within;
 }
 
 __host__ __device__ inline void block_coords(const Geometry& g, int b, int& bx, int& by, int& bz) {
+    if (g.linear) {
+        bx = b % g.nb[0];
+        const int t = b / g.nb[0];
+        by = t % g.nb[1];
+        bz = t / g.nb[1];
+        return;
+    }
     int per = g.nblock >> 3;
     int col = b / per;
     int w = b - col * per;
@@ -167,9 +183,32 @@ __host__ __device__ inline void block_coords(const Geometry& g, int b, int& bx, 
 // neighbouring blocks, whose tiles share cells, so the staging reads hit L2.  (Block ids
 // themselves are colour-major, for the colour launches of the half-list kernels.)
 __host__ __device__ inline int spatial_block(const Geometry& g, int i) {
-    const int nbx = 2 * g.nbh[0], nby = 2 * g.nbh[1];
-    const int bx = i % nbx, t = i / nbx;
-    return block_id_of(g, bx, t % nby, t / nby);
+    if (g.linear) return i;
+    const int bx = i % g.nb[0], t = i / g.nb[0];
+    return block_id_of(g, bx, t % g.nb[1], t / g.nb[1]);
+}
+
+// Cells per side for a box side that fits `fit` cells of width >= r_list: the largest
+// multiple of 4, or, for full lists, 6 where that would be 4 and 6 fit.  (Other even counts
+// would serve full lists too, but cells of a multiple of 4 per side are wider and fuller:
+// at rho* = 0.8442 and r_list = 2.8, 46 cells per side instead of 44 made both the force
+// kernel and the list build about 6 % slower.)  A result below 4 means the box is too small.
+__host__ __device__ inline int grid_cells(int fit, bool full_list) {
+    const int nc4 = fit - fit % 4;
+    return (full_list && nc4 == 4 && fit >= 6) ? 6 : nc4;
+}
+
+// Fill the block fields of g from its cell counts nc[3] (even, >= 4): colour-major
+// numbering when every count is a multiple of 4, else linear.
+__host__ __device__ inline void set_block_layout(Geometry& g) {
+    g.linear = 0;
+    for (int d = 0; d < 3; ++d) {
+        g.nb[d] = g.nc[d] / 2;
+        g.nbh[d] = g.nc[d] / 4;
+        if (g.nc[d] % 4) g.linear = 1;
+    }
+    g.nblock = g.nb[0] * g.nb[1] * g.nb[2];
+    g.ncell = g.nblock * 8;
 }
 
 __host__ __device__ inline int cell_id_of(const Geometry& g, int cx, int cy, int cz) {

@@ -91,7 +91,7 @@ def test_argument_errors_before_any_cuda_call(lib):
 
 def _dbg(lib):
     L = lib._lib
-    L.mdgb_grid_shape.argtypes = [C.c_void_p, C.c_double, C.c_void_p]
+    L.mdgb_grid_shape.argtypes = [C.c_void_p, C.c_double, C.c_int32, C.c_void_p]
     L.mdgb_num_blocks.argtypes = [C.c_void_p, C.c_void_p]
     L.mdgb_block_colour.argtypes = [C.c_void_p, C.c_int32, C.c_void_p]
     L.mdgb_tile_cells.argtypes = [C.c_void_p, C.c_int32, C.c_void_p]
@@ -100,19 +100,30 @@ def _dbg(lib):
 
 @pytest.mark.parametrize("box,rl", [((16.795962, 16.795962, 16.795962), 2.8),
                                     ((134.3677, 134.3677, 134.3677), 2.8),
-                                    ((30.0, 41.0, 52.5), 2.8)])
+                                    ((30.0, 41.0, 52.5), 2.8),
+                                    ((20.0, 22.0, 17.0), 2.8)])
 def test_grid_shape(lib, box, rl):
+    """Sec. II.A: cells at least r_list wide, as many as a multiple of 4 allows (8 colour
+    classes of 2x2x2 blocks); full lists take 6 where 6 fit and that rule gives 4."""
     L = _dbg(lib)
+    for kind in (lib.MD_LIST_FULL, lib.MD_LIST_HALF_COLOUR8, lib.MD_LIST_HALF_ATOMIC_FREE):
+        nc = np.zeros(3, dtype=np.int32)
+        assert L.mdgb_grid_shape(np.array(box).ctypes.data, rl, kind, nc.ctypes.data) == 0
+        for d in range(3):
+            fit = int(np.floor(box[d] / rl))
+            assert box[d] / nc[d] >= rl
+            if kind == lib.MD_LIST_FULL and 6 <= fit < 8:
+                assert nc[d] == 6
+            else:
+                assert nc[d] % 4 == 0 and box[d] / (nc[d] + 4) < rl
+        if box[0] == 134.3677:
+            assert nc.tolist() == [44, 44, 44]
+        if box[0] == 16.795962:
+            assert nc.tolist() == [4, 4, 4]
+        if box[0] == 20.0:
+            assert nc.tolist() == ([6, 6, 6] if kind == lib.MD_LIST_FULL else [4, 4, 4])
     nc = np.zeros(3, dtype=np.int32)
-    assert L.mdgb_grid_shape(np.array(box).ctypes.data, rl, nc.ctypes.data) == 0
-    for d in range(3):
-        assert nc[d] % 4 == 0 and box[d] / nc[d] >= rl
-        # the next multiple of 4 would make cells narrower than r_list
-        assert box[d] / (nc[d] + 4) < rl
-    if box[0] == 134.3677:
-        assert nc.tolist() == [44, 44, 44]
-    if box[0] == 16.795962:
-        assert nc.tolist() == [4, 4, 4]
+    assert L.mdgb_grid_shape(np.array(box).ctypes.data, rl, 7, nc.ctypes.data) == lib.MD_ERR_ARG
 
 
 @pytest.mark.parametrize("nc", [(4, 4, 4), (8, 12, 16), (44, 44, 44)])
@@ -145,3 +156,33 @@ def test_colour_schedule_tiles_disjoint(lib, nc):
         # blocks of one colour are contiguous in the block numbering
     # own cells of a block are its 2x2x2 cells: adjacent in every dimension
     assert L.mdgb_tile_cells(ncv.ctypes.data, nb, buf.ctypes.data) != 0  # out of range
+
+
+@pytest.mark.parametrize("nc", [(6, 6, 6), (4, 6, 10), (46, 46, 46)])
+def test_linear_block_numbering(lib, nc):
+    """Grids with a side of 4k+2 cells (full lists) number their blocks linearly: the numbering
+    is a bijection, every tile holds 64 distinct cells, own cells partition the grid, block
+    b has coordinates (b mod nb_x, ...), and such grids have no colour classes."""
+    L = _dbg(lib)
+    ncv = np.array(nc, dtype=np.int32)
+    nb = np.zeros(1, dtype=np.int32)
+    assert L.mdgb_num_blocks(ncv.ctypes.data, nb.ctypes.data) == 0
+    nb = int(nb[0])
+    ncell = nc[0] * nc[1] * nc[2]
+    assert nb * 8 == ncell
+    own_seen = np.zeros(ncell, dtype=np.int32)
+    buf = np.zeros(64, dtype=np.int32)
+    nbx, nby = nc[0] // 2, nc[1] // 2
+    for b in range(nb):
+        assert L.mdgb_tile_cells(ncv.ctypes.data, b, buf.ctypes.data) == 0
+        assert len(set(buf.tolist())) == 64
+        own_seen[buf[:8]] += 1
+        bx, by, bz = b % nbx, (b // nbx) % nby, b // (nbx * nby)
+        lowest = 2 * bx + nc[0] * (2 * by + nc[1] * 2 * bz)
+        assert int(buf[:8].min()) == lowest
+    assert np.all(own_seen == 1)
+    col = np.zeros(1, dtype=np.int32)
+    assert L.mdgb_block_colour(ncv.ctypes.data, 0, col.ctypes.data) == lib.MD_ERR_ARG
+    odd = np.array([5, 6, 6], dtype=np.int32)
+    out = np.zeros(1, dtype=np.int32)
+    assert L.mdgb_num_blocks(odd.ctypes.data, out.ctypes.data) == lib.MD_ERR_ARG

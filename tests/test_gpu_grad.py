@@ -67,6 +67,22 @@ def test_backward_matches_oracle(precision):
     assert np.array_equal(gx, gx2) and np.array_equal(ge, ge2) and np.array_equal(gs, gs2)
 
 
+def test_backward_on_a_linear_block_grid():
+    """6,912 atoms in a 17.9 sigma box: full lists take 6 cells per side (3 linearly
+    numbered blocks per side, tiles of 4 of the 6 cells); FP64 derivatives at 1e-11."""
+    s, sp = ka_snapshot(n_cells=12, seed=5)
+    rc = 2.5 * KA_SIG
+    P = O.LJParams(KA_EPS, KA_SIG, rc, [1.0, 1.0])
+    G = np.random.default_rng(5).normal(size=(s.n, 3))
+    sysm = make(s, sp, "fp64", rc)
+    gx, ge, gs = sysm.forces_backward(G)
+    assert sysm.info()["ncell"] == [6, 6, 6]
+    gx_ref, ge_ref, gs_ref = O.lj_force_grad(s.pos, s.box, P, G, sp)
+    assert vec_error(gx, gx_ref) <= TOL["fp64"]
+    for t, tref in [(ge, ge_ref), (gs, gs_ref)]:
+        assert np.abs(t - tref).max() <= TOL["fp64"] * np.abs(tref).max()
+
+
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_energy_param_grad_matches_oracle(precision):
     s, sp = ka_snapshot(seed=3)

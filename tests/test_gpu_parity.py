@@ -651,6 +651,32 @@ def test_randomised_small_systems(seed):
             s.close()
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_small_box_full_list_even_cell_count(precision):
+    """Sec. II.A: full lists need no colour classes and take 6 cells per side where 6 fit and
+    a multiple of 4 would leave 4.  A 9,400-atom liquid at rho* = 0.8442 (box 22.28 sigma, 7.96 r_list) gets 6 cells and 3
+    linearly numbered blocks per side, so each tile is 4 of the 6 cells per side rather than
+    the whole box (a whole-box FP64 tile of 9,400 atoms would not fit on chip).  Pair set,
+    forces, energy, virial and a 20-step trajectory against the oracle."""
+    sysm = W.fcc_vacancies(9400, 0.8442, 0.72, seed=8)
+    s = make(sysm, precision, "full")
+    F = s.forces()
+    assert s.info()["ncell"] == [6, 6, 6]
+    assert np.array_equal(s.neighbors(), O.neighbor_pairs(sysm.pos, sysm.box, RC + SKIN))
+    P = O.LJParams.single()
+    Fref, pe_ref, vir_ref = O.lj_forces(sysm.pos, sysm.box, P)
+    assert force_error(F, Fref) <= TOL[precision]
+    pe, _, vir = s.energy_virial()
+    tol = 1e-12 if precision == "fp64" else 1e-6
+    assert abs(pe - pe_ref) <= tol * abs(pe_ref)
+    assert np.abs(vir - vir_ref).max() <= tol * np.abs(vir_ref[:3]).max()
+    s.step(20)
+    pos, _, img = s.get_state()
+    ref = O.run_nve(sysm.pos, sysm.vel, sysm.box, P, DT, SKIN, 20)
+    dx = np.abs(pos + img * sysm.box - (ref["pos"] + ref["image"] * sysm.box)).max()
+    assert dx < (1e-10 if precision == "fp64" else 1e-6)
+
+
 def test_whole_system_tile_limit_is_reported():
     """With 4 cells per side every tile is the whole system.  A system whose tile does not
     fit the kernel's shared memory (here the FP64 half-list kernel, 52 B per atom, at 6,000
