@@ -7,11 +7,4 @@ Submodules:
   batch     - ensembles of independent systems (include/mdgb_batch.h)
   autograd  - torch.autograd.Function for force-matching derivatives
   waves     - the paper's wave schedule (host tool)
-
-Ensembles step their larger systems on many streams at once; CUDA maps streams onto
-CUDA_DEVICE_MAX_CONNECTIONS hardware queues (8 unless set before the process creates
-its CUDA context), so the package asks for 32 when it is imported first.
 """
-import os as _os
-
-_os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")

@@ -17,11 +17,13 @@ _lib.md_batch_energies.argtypes = [_P, _P, _P]
 _lib.md_batch_get_state.argtypes = [_P, _P, _P, _P, C.c_int]
 _lib.md_batch_layout.argtypes = [_P, _P, _P, _P]
 _lib.md_batch_autotune.argtypes = [_P, C.c_char_p]
+_lib.md_batch_set_wait_budget.argtypes = [_P, C.c_int64, C.c_int32]
 _lib.md_batch_last_error.argtypes = [_P, C.c_char_p, C.c_int64]
 _lib.md_batch_destroy.argtypes = [_P]
 _lib.md_batch_destroy.restype = None
 for _f in ("md_batch_create", "md_batch_set_state", "md_batch_step", "md_batch_forces", "md_batch_energies",
-           "md_batch_get_state", "md_batch_layout", "md_batch_autotune", "md_batch_last_error"):
+           "md_batch_get_state", "md_batch_layout", "md_batch_autotune", "md_batch_last_error",
+           "md_batch_set_wait_budget"):
     getattr(_lib, _f).restype = C.c_int
 
 
@@ -92,6 +94,9 @@ class Batch:
 
     def autotune(self, cache_path=None):
         self._check(_lib.md_batch_autotune(self.handle, cache_path.encode() if cache_path else None))
+
+    def set_wait_budget(self, budget_cycles=0, held_system=-1):
+        self._check(_lib.md_batch_set_wait_budget(self.handle, int(budget_cycles), int(held_system)))
 
 
 def from_systems(systems, **kw) -> Batch:

@@ -1,11 +1,11 @@
 // api_batch.cu - C ABI of ensembles of independent systems (include/mdgb_batch.h).
 //
-// Systems of at most BATCH_MAX_ATOMS atoms are grouped into size buckets; each
-// bucket is one launch of k_batch_run (one CTA per system, all steps of the call),
-// with the bucket's CTA size and cell range (chosen by md_batch_autotune, else a
-// default).  The launches of a step call are captured once into a CUDA graph and
-// replayed.  Larger systems are ordinary md_system instances, each on its own
-// stream, stepped from a small pool of host threads while the launches run.
+// Every call that advances or evaluates the ensemble is one persistent launch of
+// k_ensemble_run over a work table of all systems (k_batch.cu): systems of at most
+// one_cta_max atoms (or with too small a box for 2x2x2-cell blocks) are one task each, run
+// by one CTA for the whole call; larger ones are split into phases of block and chunk tasks
+// that any CTA may take.  The launch is captured into a CUDA graph per (steps, flags),
+// together with the resets of its scheduler words, and replayed.
 #include "mdgb.h"
 #include "mdgb_batch.h"
 #include "mdgb_batch_internal.cuh"
@@ -16,15 +16,16 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
-#include <thread>
 #include <vector>
 
 using namespace mdgb;
 
 namespace {
 
-constexpr int NBUCKET = 5;  // [.., 512), [512, 1024), [1024, 2048), [2048, 4096), [4096, 8192]
+constexpr int NBUCKET = 5;  // one-CTA systems: [.., 512), [512, 1024), [1024, 2048), [2048, 4096), [4096, 8192]
 const int BUCKET_HI[NBUCKET] = {512, 1024, 2048, 4096, BATCH_MAX_ATOMS + 1};
+constexpr long long DEFAULT_BUDGET = 1LL << 34;  // cycles without work before a CTA gives up (~9 s)
+constexpr int DEFAULT_ONE_CTA_MAX = 2048;
 
 int bucket_of(int64_t n) {
     for (int k = 0; k < NBUCKET; ++k)
@@ -36,35 +37,42 @@ int bucket_of(int64_t n) {
 
 struct md_batch {
     int device = 0;
+    int sms = 0;
     cudaStream_t stream = nullptr;
     cudaStream_t cap_stream = nullptr;  // capture only records; the legacy stream cannot capture
-    cudaStream_t bucket_streams[NBUCKET] = {};  // one branch of the captured graph per size bucket
-    cudaEvent_t fork_ev = nullptr, join_ev[NBUCKET] = {};
     int nsys = 0;
     std::vector<int64_t> n, a0;
     std::vector<double> box;  // 3 per system
     double r_cut = 0, skin = 0, dt = 0;
-    md_params params{};
     double eps = 1, sigma = 1, mass = 1;
     PairTable pt{};
     int64_t ntot = 0;
     BatchState st{};
+    EnsArrays ea{};
     double *d_pe = nullptr, *d_ke = nullptr;
-    float* pe_atom = nullptr;
     double* d_aos = nullptr;  // N_total x 3 staging for AoS input/output
-    struct Bucket {
-        int threads = 256, R = 1;
-        std::vector<int> ids;
-        BatchSys* d_sys = nullptr;
-        int nmax = 0, cmax = 0;
-    };
-    Bucket bk[NBUCKET];
-    std::vector<int> path;  // 0: one CTA, 1: md_system
-    std::vector<md_system*> big;
-    std::vector<int> big_ids;
-    std::vector<cudaStream_t> big_streams;
+    int32_t* d_sys_of = nullptr;  // system of each atom (output wrap)
+    double* d_box = nullptr;      // 3 per system
+    // launch shape (md_batch_autotune may change it)
+    int threads = 256;
+    int one_cta_max = DEFAULT_ONE_CTA_MAX;
+    int R[NBUCKET] = {1, 1, 1, 1, 1};
+    // the work table for the current shape
+    std::vector<int> path;  // 0: one CTA, 1: block tasks
+    std::vector<BatchSys> one;
+    std::vector<EnsBlockSys> blk;
+    std::vector<EnsEntry> ent;
+    BatchSys* d_one = nullptr;
+    EnsBlockSys* d_blk = nullptr;
+    EnsEntry* d_ent = nullptr;
+    unsigned long long* d_ctl_init = nullptr;
+    int64_t ncell_blk = 0;  // cells of the block systems
+    int nmax = 0, cmax = 0, tile_slots = 0, grid = 0;
+    size_t smem = 0;
+    // test hook: a held entry and a budget (launched without a graph)
+    int hold = -1;
+    long long budget = DEFAULT_BUDGET;
     bool has_state = false, have_forces = false;
-    // graph of the launches of one md_batch_step call
     cudaGraphExec_t gexec = nullptr;
     int g_steps = -1, g_flags = -1;
     std::vector<void*> allocs;
@@ -121,72 +129,164 @@ BatchSys make_sys(const md_batch* b, int k, int R) {
     return y;
 }
 
-int upload_bucket(md_batch* b, int k) {
-    md_batch::Bucket& B = b->bk[k];
-    if (B.ids.empty()) return MD_OK;
-    std::vector<BatchSys> h;
-    B.nmax = 0;
-    B.cmax = 0;
-    for (int id : B.ids) {
-        h.push_back(make_sys(b, id, B.R));
-        B.nmax = std::max(B.nmax, h.back().n);
-        B.cmax = std::max(B.cmax, h.back().ncell);
+// Block-task geometry: per side the largest even number of cells at least r_cut + skin
+// wide (at most 1024).  False if some side has fewer than 6: with 4 the tile would be the
+// whole box, with cells up to 3/2 (r_cut + skin) wide and about 3 times the atoms of the
+// narrowest ones, which would set every CTA's shared memory.
+bool make_blk(const md_batch* b, int k, EnsBlockSys& y) {
+    y = EnsBlockSys{};
+    y.a0 = b->a0[k];
+    y.id = k;
+    y.n = (int)b->n[k];
+    y.ncell = 1;
+    for (int d = 0; d < 3; ++d) {
+        const double L = b->box[3 * k + d];
+        int nc = (int)std::min(std::floor(L / ((b->r_cut + b->skin) * (1.0 + 1e-12))), 1024.0);
+        nc -= nc % 2;
+        if (nc < 6) return false;
+        y.nc[d] = nc;
+        y.nb[d] = nc / 2;
+        y.L[d] = L;
+        y.w[d] = L / nc;
+        y.inv_w[d] = nc / L;
+        for (int t = 0; t < 4; ++t) y.off[d][t] = (float)((t - 1.5) * y.w[d]);
+        y.ncell *= nc;
     }
-    B.nmax = (B.nmax + 7) & ~7;
-    if (!B.d_sys && balloc(b, &B.d_sys, B.ids.size())) return MD_ERR_CUDA;
-    BCK(cudaMemcpy(B.d_sys, h.data(), sizeof(BatchSys) * h.size(), cudaMemcpyHostToDevice));
-    if (b->gexec) {
-        cudaGraphExecDestroy(b->gexec);
-        b->gexec = nullptr;
+    y.nblock = y.nb[0] * y.nb[1] * y.nb[2];
+    return true;
+}
+
+// Tile slots a block task of system y may need: 64 cells of up to 1.6 times the mean
+// occupancy plus a margin.
+int tile_need(const EnsBlockSys& y) {
+    const double rho = y.n / (y.L[0] * y.L[1] * y.L[2]);
+    return 64 * ((int)std::ceil(1.6 * rho * y.w[0] * y.w[1] * y.w[2]) + 4);
+}
+
+bool is_block(const md_batch* b, int k) {
+    EnsBlockSys y;
+    return b->n[k] > 0 && make_blk(b, k, y) && (b->n[k] > b->one_cta_max || b->n[k] > BATCH_MAX_ATOMS);
+}
+
+void drop_graph(md_batch* b) {
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    b->gexec = nullptr;
+    b->g_steps = b->g_flags = -1;
+}
+
+// Work table, geometry and launch shape for the current threads / one_cta_max / R; the
+// device arrays were sized at create for the largest table (every system an entry, every
+// blockable system a block system).
+int build_table(md_batch* b) {
+    drop_graph(b);
+    b->path.assign(b->nsys, 0);
+    b->one.clear();
+    b->blk.clear();
+    b->ent.clear();
+    b->nmax = b->cmax = 0;
+    b->ncell_blk = 0;
+    int tile = 0;
+    std::vector<int> order(b->nsys);
+    for (int k = 0; k < b->nsys; ++k) order[k] = k;
+    // the longest tasks first: one-CTA systems by size, then block systems by size
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return b->n[x] > b->n[y]; });
+    std::vector<EnsEntry> e_one, e_blk;
+    for (int k : order) {
+        if (b->n[k] == 0) continue;
+        if (is_block(b, k)) {
+            EnsBlockSys y;
+            make_blk(b, k, y);
+            y.c0 = b->ncell_blk;
+            y.s0 = b->ncell_blk + (int64_t)b->blk.size();
+            b->ncell_blk += y.ncell;
+            tile = std::max(tile, tile_need(y));
+            e_blk.push_back(EnsEntry{1, (int)b->blk.size(), (y.n + ENS_ATOM_CHUNK - 1) / ENS_ATOM_CHUNK,
+                                     (y.ncell + ENS_CELL_CHUNK - 1) / ENS_CELL_CHUNK, y.nblock});
+            b->blk.push_back(y);
+            b->path[k] = 1;
+        } else {
+            if (b->n[k] > BATCH_MAX_ATOMS)
+                return bfail(b, MD_ERR_BOX_TOO_SMALL, "system %d: %lld atoms in a box of fewer than 6 (r_cut + skin) per side",
+                             k, (long long)b->n[k]);
+            const BatchSys y1 = make_sys(b, k, b->R[bucket_of(b->n[k])]);
+            if (y1.ncell > BATCH_MAX_CELLS) return bfail(b, MD_ERR_CELL_OVERFLOW, "system %d: too many cells", k);
+            b->nmax = std::max(b->nmax, y1.n);
+            b->cmax = std::max(b->cmax, y1.ncell);
+            e_one.push_back(EnsEntry{0, (int)b->one.size(), 0, 0, 0});
+            b->one.push_back(y1);
+        }
     }
+    b->nmax = (b->nmax + 7) & ~7;
+    b->ent = e_one;
+    b->ent.insert(b->ent.end(), e_blk.begin(), e_blk.end());
+    // shared memory: the larger of the one-CTA layout and the tile; the tile takes what is left
+    size_t smem = b->one.empty() ? 0 : batch_smem_bytes(b->nmax, b->cmax);
+    if (!b->blk.empty()) smem = std::max(smem, std::max(ens_tile_smem_bytes(tile), ens_list_smem(tile)));
+    smem = (smem + 15) & ~(size_t)15;
+    int optin = 0;
+    BCK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, b->device));
+    if (smem + 8192 > (size_t)optin)
+        return bfail(b, MD_ERR_CELL_OVERFLOW, "an ensemble task needs %zu B of shared memory", smem);
+    b->smem = smem;
+    b->tile_slots = (int)(smem / sizeof(float4)) - 1;
+    const int per_sm = ensemble_ctas_per_sm(b->threads, smem);
+    if (per_sm < 1) return bfail(b, MD_ERR_CUDA, "the ensemble kernel does not fit an SM at %d threads", b->threads);
+    b->grid = per_sm * b->sms;
+    // initial scheduler words: one-CTA systems at their task, block systems at START
+    std::vector<unsigned long long> init(b->ent.size(), 0ull);
+    for (size_t e = 0; e < b->ent.size(); ++e)
+        if (b->ent[e].kind == 1) init[e] = (unsigned long long)ENS_START << 32;
+    // the block systems' lists and coordinates belong to the old table
+    if (b->ea.valid) BCK(cudaMemsetAsync(b->ea.valid, 0, sizeof(int32_t) * (size_t)b->nsys, b->stream));
+    if (b->ea.rebuild) BCK(cudaMemsetAsync(b->ea.rebuild, 0, sizeof(int32_t) * (size_t)b->nsys, b->stream));
+    if (!b->ent.empty()) {
+        BCK(cudaMemcpy(b->d_ent, b->ent.data(), sizeof(EnsEntry) * b->ent.size(), cudaMemcpyHostToDevice));
+        BCK(cudaMemcpy(b->d_ctl_init, init.data(), sizeof(unsigned long long) * init.size(), cudaMemcpyHostToDevice));
+    }
+    if (!b->one.empty()) BCK(cudaMemcpy(b->d_one, b->one.data(), sizeof(BatchSys) * b->one.size(), cudaMemcpyHostToDevice));
+    if (!b->blk.empty())
+        BCK(cudaMemcpy(b->d_blk, b->blk.data(), sizeof(EnsBlockSys) * b->blk.size(), cudaMemcpyHostToDevice));
     return MD_OK;
 }
 
-bool bucket_fits(const md_batch* b, int k, int threads, int R) {
-    int nmax = 0, cmax = 0;
-    for (int id : b->bk[k].ids) {
-        const BatchSys y = make_sys(b, id, R);
-        nmax = std::max(nmax, y.n);
-        cmax = std::max(cmax, y.ncell);
+// Reset the scheduler words (and the block systems' cell counts) and launch, on stream s.
+int enqueue_ensemble(md_batch* b, int n_steps, int flags, cudaStream_t s) {
+    const int nent = (int)b->ent.size();
+    if (nent == 0) return MD_OK;
+    BCK(cudaMemcpyAsync(b->ea.ctl, b->d_ctl_init, sizeof(unsigned long long) * nent, cudaMemcpyDeviceToDevice, s));
+    BCK(cudaMemsetAsync(b->ea.done, 0, sizeof(int32_t) * nent, s));
+    BCK(cudaMemsetAsync(b->ea.g_done, 0, sizeof(int32_t), s));
+    if (b->ncell_blk > 0) BCK(cudaMemsetAsync(b->ea.count, 0, sizeof(int32_t) * b->ncell_blk, s));
+    if (b->hold >= 0 && b->hold < nent) {
+        const unsigned long long w = (unsigned long long)ENS_HOLD << 32;
+        BCK(cudaMemcpyAsync(b->ea.ctl + b->hold, &w, sizeof(w), cudaMemcpyHostToDevice, s));
+        BCK(cudaStreamSynchronize(s));  // w lives on this stack frame
     }
-    if (cmax > BATCH_MAX_CELLS) return false;
-    int dev = 0, optin = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    return threads <= BATCH_MAX_THREADS && batch_smem_bytes((nmax + 7) & ~7, cmax) + 8192 <= (size_t)optin;
+    EnsArrays ea = b->ea;
+    ea.budget = b->budget;
+    launch_ensemble(b->d_ent, nent, b->d_one, b->d_blk, b->st, ea, b->pt, n_steps, flags, b->dt, b->threads, b->grid,
+                    b->nmax, b->cmax, b->tile_slots, b->smem, b->d_pe, b->d_ke, s);
+    BCK(cudaGetLastError());
+    return MD_OK;
 }
 
-// the launches of one step call: every non-empty bucket
-void enqueue_buckets(md_batch* b, int n_steps, int flags, cudaStream_t s) {
-    for (auto& B : b->bk) {
-        if (B.ids.empty()) continue;
-        launch_batch_run(B.d_sys, (int)B.ids.size(), b->st, b->pt, n_steps, flags, b->dt, B.threads, B.nmax, B.cmax,
-                         b->d_pe, b->d_ke, b->pe_atom, s);
+int run_ensemble(md_batch* b, int n_steps, int flags) {
+    if (b->ent.empty()) return MD_OK;
+    if (b->hold >= 0 || b->budget != DEFAULT_BUDGET) {  // the test hook: a direct launch
+        drop_graph(b);
+        return enqueue_ensemble(b, n_steps, flags, b->stream);
     }
-}
-
-int run_buckets(md_batch* b, int n_steps, int flags) {
-    bool any = false;
-    for (auto& B : b->bk) any |= !B.ids.empty();
-    if (!any) return MD_OK;
     if (!(b->gexec && b->g_steps == n_steps && b->g_flags == flags)) {
-        if (b->gexec) cudaGraphExecDestroy(b->gexec);
-        b->gexec = nullptr;
+        drop_graph(b);
         cudaGraph_t g = nullptr;
-        // the buckets touch disjoint systems: one parallel branch each, so that they share the
-        // GPU instead of running one after another
         BCK(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
-        BCK(cudaEventRecord(b->fork_ev, b->cap_stream));
-        for (int k = 0; k < NBUCKET; ++k) {
-            md_batch::Bucket& B = b->bk[k];
-            if (B.ids.empty()) continue;
-            BCK(cudaStreamWaitEvent(b->bucket_streams[k], b->fork_ev, 0));
-            launch_batch_run(B.d_sys, (int)B.ids.size(), b->st, b->pt, n_steps, flags, b->dt, B.threads, B.nmax,
-                             B.cmax, b->d_pe, b->d_ke, b->pe_atom, b->bucket_streams[k]);
-            BCK(cudaEventRecord(b->join_ev[k], b->bucket_streams[k]));
-            BCK(cudaStreamWaitEvent(b->cap_stream, b->join_ev[k], 0));
+        const int rc = enqueue_ensemble(b, n_steps, flags, b->cap_stream);
+        const cudaError_t ec = cudaStreamEndCapture(b->cap_stream, &g);
+        if (rc) {
+            if (g) cudaGraphDestroy(g);
+            return rc;
         }
-        BCK(cudaStreamEndCapture(b->cap_stream, &g));
+        if (ec != cudaSuccess) return bfail(b, MD_ERR_CUDA, "graph capture: %s", cudaGetErrorString(ec));
         cudaError_t e = cudaGraphInstantiate(&b->gexec, g, 0);
         cudaGraphDestroy(g);
         if (e != cudaSuccess) return bfail(b, MD_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
@@ -211,14 +311,39 @@ __global__ void k_aos_in(int64_t ntot, const double* __restrict__ pos, const dou
     st.species[i] = sp ? sp[i] : 0;
 }
 
-__global__ void k_aos_out(int64_t lo, int64_t hi, BatchState st, int what, double* __restrict__ out,
+// One coordinate wrapped into [0, L) (one box length at most, as the binning does) and its
+// image counter: positions of block systems are wrapped only when they are binned.
+__device__ __forceinline__ void wrap_out(double& x, int32_t& img, double L) {
+    if (x >= L) {
+        x -= L;
+        img += 1;
+    } else if (x < 0.0) {
+        x += L;
+        img -= 1;
+    }
+}
+
+__global__ void k_aos_out(int64_t ntot, BatchState st, const int32_t* __restrict__ sys_of,
+                          const double* __restrict__ box, int what, double* __restrict__ out,
                           int32_t* __restrict__ img) {
-    const int64_t i = lo + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= hi) return;
-    if (what == 0) {
-        out[3 * i] = st.x[i];
-        out[3 * i + 1] = st.y[i];
-        out[3 * i + 2] = st.z[i];
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= ntot) return;
+    if (what == 0 || what == 3) {
+        const double* B = box + 3 * (int64_t)sys_of[i];
+        double x = st.x[i], y = st.y[i], z = st.z[i];
+        int32_t ix = st.ix[i], iy = st.iy[i], iz = st.iz[i];
+        wrap_out(x, ix, B[0]);
+        wrap_out(y, iy, B[1]);
+        wrap_out(z, iz, B[2]);
+        if (what == 0) {
+            out[3 * i] = x;
+            out[3 * i + 1] = y;
+            out[3 * i + 2] = z;
+        } else {
+            img[3 * i] = ix;
+            img[3 * i + 1] = iy;
+            img[3 * i + 2] = iz;
+        }
     } else if (what == 1) {
         out[3 * i] = st.vx[i];
         out[3 * i + 1] = st.vy[i];
@@ -228,10 +353,6 @@ __global__ void k_aos_out(int64_t lo, int64_t hi, BatchState st, int what, doubl
         out[3 * i] = (double)st.fq[i] * q;
         out[3 * i + 1] = (double)st.fq[st.ntot + i] * q;
         out[3 * i + 2] = (double)st.fq[2 * st.ntot + i] * q;
-    } else {
-        img[3 * i] = st.ix[i];
-        img[3 * i + 1] = st.iy[i];
-        img[3 * i + 2] = st.iz[i];
     }
 }
 
@@ -239,38 +360,60 @@ int check_batch_err(md_batch* b) {
     uint32_t e = 0;
     BCK(cudaMemcpy(&e, b->st.err, sizeof(uint32_t), cudaMemcpyDeviceToHost));
     if (!e) return MD_OK;
+    cudaMemset(b->st.err, 0, sizeof(uint32_t));
+    cudaMemsetAsync(b->ea.valid, 0, sizeof(int32_t) * (size_t)b->nsys, b->stream);
+    cudaStreamSynchronize(b->stream);
+    b->have_forces = false;
+    if (e & ERR_TIMEOUT)
+        return bfail(b, MD_ERR_TIMEOUT, "a CTA of the ensemble launch found no work for its whole wait budget");
     if (e & ERR_NONFINITE) return bfail(b, MD_ERR_NONFINITE, "non-finite force or coordinate");
     if (e & ERR_ESCAPE) return bfail(b, MD_ERR_NONFINITE, "an atom moved more than one box length in a step");
+    if (e & ERR_TILE_OVERFLOW) return bfail(b, MD_ERR_CELL_OVERFLOW, "a cell neighbourhood exceeded shared memory");
+    if (e & ERR_LIST_OVERFLOW) return bfail(b, MD_ERR_LIST_OVERFLOW, "a neighbour list exceeded its capacity");
     return bfail(b, MD_ERR_CUDA, "device error 0x%x", e);
 }
 
-// call f(k) for every large system from a pool of host threads; first nonzero code wins
-template <typename F>
-int for_big(md_batch* b, F&& f) {
-    const int m = (int)b->big.size();
-    if (m == 0) return MD_OK;
-    // one host thread per core: each waits on its system's steps in turn
-    const int nt = std::min(m, std::max(8, (int)std::thread::hardware_concurrency()));
-    std::vector<int> rc(nt, MD_OK);
-    std::vector<std::thread> th;
-    for (int t = 0; t < nt; ++t)
-        th.emplace_back([&, t]() {
-            cudaSetDevice(b->device);
-            for (int k = t; k < m; k += nt)
-                if (rc[t] == MD_OK) rc[t] = f(k);
-        });
-    for (auto& x : th) x.join();
-    for (int k = 0; k < m; ++k) {
-        const int t = k % nt;
-        if (rc[t] != MD_OK) {
-            char buf[256] = "";
-            md_last_error(b->big[k], buf, sizeof(buf));
-            if (buf[0]) return bfail(b, rc[t], "system %d: %s", b->big_ids[k], buf);
-        }
+// Time 10 steps of the whole ensemble with the current shape (warm-up step first), with the
+// state saved before and restored after.
+struct Snapshot {
+    double* d = nullptr;
+    int32_t* i = nullptr;
+    long long* f = nullptr;
+};
+
+void snap(md_batch* b, Snapshot& sn, bool restore) {
+    const size_t n = (size_t)b->ntot;
+    double* D[6] = {b->st.x, b->st.y, b->st.z, b->st.vx, b->st.vy, b->st.vz};
+    int32_t* I[3] = {b->st.ix, b->st.iy, b->st.iz};
+    for (int c = 0; c < 6; ++c)
+        cudaMemcpyAsync(restore ? D[c] : sn.d + c * n, restore ? sn.d + c * n : D[c], sizeof(double) * n,
+                        cudaMemcpyDeviceToDevice, b->stream);
+    for (int c = 0; c < 3; ++c)
+        cudaMemcpyAsync(restore ? I[c] : sn.i + c * n, restore ? sn.i + c * n : I[c], sizeof(int32_t) * n,
+                        cudaMemcpyDeviceToDevice, b->stream);
+    cudaMemcpyAsync(restore ? b->st.fq : sn.f, restore ? sn.f : b->st.fq, sizeof(long long) * 3 * n,
+                    cudaMemcpyDeviceToDevice, b->stream);
+}
+
+float time_shape(md_batch* b, Snapshot& sn, cudaEvent_t e0, cudaEvent_t e1) {
+    if (build_table(b)) return 1e30f;
+    if (enqueue_ensemble(b, 1, 0, b->stream)) return 1e30f;
+    cudaEventRecord(e0, b->stream);
+    if (enqueue_ensemble(b, 10, BATCH_HAVE_FORCES, b->stream)) return 1e30f;
+    cudaEventRecord(e1, b->stream);
+    if (cudaEventSynchronize(e1) != cudaSuccess) return 1e30f;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    snap(b, sn, true);
+    cudaMemsetAsync(b->ea.valid, 0, sizeof(int32_t) * (size_t)b->nsys, b->stream);
+    cudaMemsetAsync(b->ea.rebuild, 0, sizeof(int32_t) * (size_t)b->nsys, b->stream);
+    uint32_t e = 0;
+    cudaMemcpy(&e, b->st.err, sizeof(uint32_t), cudaMemcpyDeviceToHost);
+    if (e) {
+        cudaMemset(b->st.err, 0, sizeof(uint32_t));
+        return 1e30f;
     }
-    for (int t = 0; t < nt; ++t)
-        if (rc[t] != MD_OK) return bfail(b, rc[t], "a system on the md_system path failed");
-    return MD_OK;
+    return ms;
 }
 
 }  // namespace
@@ -290,26 +433,16 @@ int md_batch_create(int32_t n_systems, const int64_t* n_atoms, const double* box
         return code;
     };
     cudaGetDevice(&b->device);
+    cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->device);
     b->stream = static_cast<cudaStream_t>(p->stream);
     if (cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) != cudaSuccess) return bail(MD_ERR_CUDA);
-    if (cudaEventCreateWithFlags(&b->fork_ev, cudaEventDisableTiming) != cudaSuccess) return bail(MD_ERR_CUDA);
-    for (int k = 0; k < NBUCKET; ++k)
-        if (cudaStreamCreateWithFlags(&b->bucket_streams[k], cudaStreamNonBlocking) != cudaSuccess ||
-            cudaEventCreateWithFlags(&b->join_ev[k], cudaEventDisableTiming) != cudaSuccess)
-            return bail(MD_ERR_CUDA);
     b->nsys = n_systems;
     b->r_cut = r_cut;
     b->skin = skin;
     b->dt = p->dt;
-    b->params = *p;
     b->eps = p->eps[0];
     b->sigma = p->sigma[0];
     b->mass = p->mass[0];
-    b->params.eps = &b->eps;
-    b->params.sigma = &b->sigma;
-    b->params.mass = &b->mass;
-    b->params.rcut = nullptr;
-    b->params.list_kind = MD_LIST_FULL;
     // pair constants as the main path builds them (one species)
     b->pt.nsp = 1;
     b->pt.sig2_f[0] = (float)(b->sigma * b->sigma);
@@ -325,9 +458,10 @@ int md_batch_create(int32_t n_systems, const int64_t* n_atoms, const double* box
     b->n.assign(n_atoms, n_atoms + n_systems);
     b->box.assign(boxes, boxes + 3 * n_systems);
     b->a0.resize(n_systems);
-    b->path.assign(n_systems, 0);
+    int64_t cells_max = 0, nblk_max = 0;
+    double band = 0.0, rho_max = 0.0;
     for (int k = 0; k < n_systems; ++k) {
-        if (b->n[k] < 0) return bail(MD_ERR_ARG);
+        if (b->n[k] < 0 || b->n[k] > 0x7fffffffLL) return bail(MD_ERR_ARG);
         b->a0[k] = b->ntot;
         b->ntot += b->n[k];
         for (int d = 0; d < 3; ++d)
@@ -335,65 +469,70 @@ int md_batch_create(int32_t n_systems, const int64_t* n_atoms, const double* box
                 bfail(b, MD_ERR_BOX_TOO_SMALL, "system %d: box side %g < 2 r_cut", k, boxes[3 * k + d]);
                 return bail(MD_ERR_BOX_TOO_SMALL);
             }
-        const int bu = bucket_of(b->n[k]);
-        if (bu >= 0) {
-            b->bk[bu].ids.push_back(k);
-        } else {
-            b->path[k] = 1;
-            b->big_ids.push_back(k);
-        }
-    }
-    // largest systems first within a bucket: CTAs start in index order, so the longest ones
-    // are not left for the end of the launch
-    for (auto& B : b->bk)
-        std::stable_sort(B.ids.begin(), B.ids.end(), [&](int x, int y) { return b->n[x] > b->n[y]; });
-    // FP64 decision band: the widest any system needs, for either cell divisor
-    double band = 0.0;
-    for (int k = 0; k < n_systems; ++k)
+        // FP64 decision band: the widest any system needs, on either path and cell divisor
         for (int R = 1; R <= 2; ++R) {
             const BatchSys y = make_sys(b, k, R);
             band = std::max(band, cell_frame_cut_band(std::max(y.w[0], std::max(y.w[1], y.w[2])), R, r_cut));
         }
+        EnsBlockSys y;
+        if (make_blk(b, k, y)) {
+            band = std::max(band,
+                            tile_frame_cut_band(std::max(y.w[0], std::max(y.w[1], y.w[2])), 0.5 * skin, r_cut));
+            cells_max += y.ncell;
+            nblk_max += 1;
+            rho_max = std::max(rho_max, b->n[k] / (y.L[0] * y.L[1] * y.L[2]));
+        }
+    }
     b->pt.cut_band = (float)band;
     set_band_thresholds(b->pt);
     int rc;
     BatchState& st = b->st;
+    EnsArrays& ea = b->ea;
     st.ntot = b->ntot;
-    if ((rc = balloc(b, &st.x, b->ntot)) || (rc = balloc(b, &st.y, b->ntot)) || (rc = balloc(b, &st.z, b->ntot)) ||
-        (rc = balloc(b, &st.vx, b->ntot)) || (rc = balloc(b, &st.vy, b->ntot)) ||
-        (rc = balloc(b, &st.vz, b->ntot)) || (rc = balloc(b, &st.ix, b->ntot)) ||
-        (rc = balloc(b, &st.iy, b->ntot)) || (rc = balloc(b, &st.iz, b->ntot)) ||
-        (rc = balloc(b, &st.species, b->ntot)) || (rc = balloc(b, &st.fq, 3 * (size_t)b->ntot)) ||
-        (rc = balloc(b, &st.err, 1)) || (rc = balloc(b, &b->d_pe, n_systems)) ||
-        (rc = balloc(b, &b->d_ke, n_systems)) || (rc = balloc(b, &b->pe_atom, b->ntot)) ||
-        (rc = balloc(b, &b->d_aos, 3 * (size_t)b->ntot)))
+    // Verlet lists of the block systems: 1.5 times the mean count in the list sphere at the
+    // densest such system, plus 32, in chunks of 8 (a longer list reports MD_ERR_LIST_OVERFLOW)
+    const double rl = r_cut + skin;
+    ea.list_chunks = (int)((std::ceil(1.5 * 4.0 / 3.0 * M_PI * rl * rl * rl * rho_max) + 32 + 7) / 8);
+    ea.rl2 = rl * rl;
+    ea.rl2_lo = (float)(ea.rl2 * (1.0 - 1e-4));
+    ea.rl2_hi = (float)(ea.rl2 * (1.0 + 1e-4));
+    ea.lim2_f = (float)(0.25 * skin * skin);
+    const size_t nt = (size_t)b->ntot, ns = (size_t)n_systems;
+    if ((rc = balloc(b, &st.x, nt)) || (rc = balloc(b, &st.y, nt)) || (rc = balloc(b, &st.z, nt)) ||
+        (rc = balloc(b, &st.vx, nt)) || (rc = balloc(b, &st.vy, nt)) || (rc = balloc(b, &st.vz, nt)) ||
+        (rc = balloc(b, &st.ix, nt)) || (rc = balloc(b, &st.iy, nt)) || (rc = balloc(b, &st.iz, nt)) ||
+        (rc = balloc(b, &st.species, nt)) || (rc = balloc(b, &st.fq, 3 * nt)) || (rc = balloc(b, &st.err, 1)) ||
+        (rc = balloc(b, &b->d_pe, ns)) || (rc = balloc(b, &b->d_ke, ns)) || (rc = balloc(b, &b->d_aos, 3 * nt)) ||
+        (rc = balloc(b, &ea.xa, nt)) || (rc = balloc(b, &ea.ya, nt)) || (rc = balloc(b, &ea.za, nt)) ||
+        (rc = balloc(b, &ea.cell_of, nt)) || (rc = balloc(b, &ea.perm_u, nt)) || (rc = balloc(b, &ea.perm_s, nt)) ||
+        (rc = balloc(b, &ea.scell, nt)) || (rc = balloc(b, &ea.xs, nt)) || (rc = balloc(b, &ea.xsb, nt)) ||
+        (rc = balloc(b, &ea.xs_ref, nt)) || (rc = balloc(b, &ea.nl_cnt, nt)) ||
+        (rc = balloc(b, &ea.nl, nt * (size_t)ea.list_chunks)) || (rc = balloc(b, &ea.rebuild, ns)) ||
+        (rc = balloc(b, &ea.valid, ns)) || (rc = balloc(b, &b->d_sys_of, nt)) || (rc = balloc(b, &b->d_box, 3 * ns)) ||
+        (rc = balloc(b, &ea.pe_atom, nt)) ||
+        (rc = balloc(b, &ea.count, (size_t)cells_max)) || (rc = balloc(b, &ea.cursor, (size_t)cells_max)) ||
+        (rc = balloc(b, &ea.cstart, (size_t)(cells_max + nblk_max))) || (rc = balloc(b, &ea.ctl, ns)) ||
+        (rc = balloc(b, &ea.done, ns)) || (rc = balloc(b, &ea.g_done, 1)) || (rc = balloc(b, &b->d_ctl_init, ns)) ||
+        (rc = balloc(b, &b->d_ent, ns)) || (rc = balloc(b, &b->d_one, ns)) || (rc = balloc(b, &b->d_blk, ns)))
         return bail(rc);
-    if (cudaMemset(st.err, 0, sizeof(uint32_t)) != cudaSuccess) return bail(MD_ERR_CUDA);
-    // default launch shapes; md_batch_autotune may change them
-    const int def_threads[NBUCKET] = {128, 128, 256, 256, 512};
-    for (int k = 0; k < NBUCKET; ++k) {
-        b->bk[k].threads = def_threads[k];
-        b->bk[k].R = 1;
-        if (!b->bk[k].ids.empty() && !bucket_fits(b, k, b->bk[k].threads, 1)) {
-            bfail(b, MD_ERR_CELL_OVERFLOW, "bucket %d does not fit in shared memory", k);
-            return bail(MD_ERR_CELL_OVERFLOW);
-        }
-        if ((rc = upload_bucket(b, k))) return bail(rc);
+    // slot maps start as valid indices, so that a step that gave up after an error reads
+    // only inside its system
+    if (cudaMemset(st.err, 0, sizeof(uint32_t)) != cudaSuccess || cudaMemset(b->d_pe, 0, sizeof(double) * ns) ||
+        cudaMemset(b->d_ke, 0, sizeof(double) * ns) || cudaMemset(ea.valid, 0, sizeof(int32_t) * ns) ||
+        cudaMemset(ea.rebuild, 0, sizeof(int32_t) * ns) || cudaMemset(ea.perm_u, 0, sizeof(int32_t) * nt) ||
+        cudaMemset(ea.perm_s, 0, sizeof(int32_t) * nt))
+        return bail(MD_ERR_CUDA);
+    {
+        std::vector<int32_t> sys_of(nt);
+        for (int k = 0; k < n_systems; ++k)
+            for (int64_t i = 0; i < b->n[k]; ++i) sys_of[b->a0[k] + i] = k;
+        if (nt && cudaMemcpy(b->d_sys_of, sys_of.data(), sizeof(int32_t) * nt, cudaMemcpyHostToDevice) != cudaSuccess)
+            return bail(MD_ERR_CUDA);
+        if (cudaMemcpy(b->d_box, boxes, sizeof(double) * 3 * ns, cudaMemcpyHostToDevice) != cudaSuccess)
+            return bail(MD_ERR_CUDA);
     }
-    // larger systems: ordinary systems on their own streams
-    for (int k : b->big_ids) {
-        cudaStream_t s = nullptr;
-        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return bail(MD_ERR_CUDA);
-        b->big_streams.push_back(s);
-        md_params q = b->params;
-        q.stream = s;
-        md_system* m = nullptr;
-        if ((rc = md_create(b->n[k], &b->box[3 * k], r_cut, skin, &q, &m))) {
-            bfail(b, rc, "system %d (%lld atoms) on the md_system path could not be created", k, (long long)b->n[k]);
-            return bail(rc);
-        }
-        b->big.push_back(m);
-    }
+    // default launch shape; md_batch_autotune may change it
+    if ((rc = build_table(b))) return bail(rc);
     *out = b;
     return MD_OK;
 }
@@ -420,13 +559,12 @@ int md_batch_set_state(md_batch* b, const double* pos, const double* vel, const 
     if (b->ntot > 0) k_aos_in<<<(unsigned)((b->ntot + 255) / 256), 256, 0, b->stream>>>(b->ntot, P, V, S, b->st);
     BCK(cudaGetLastError());
     BCK(cudaStreamSynchronize(b->stream));
-    int rc = for_big(b, [&](int k) {
-        const int64_t o = 3 * b->a0[b->big_ids[k]];
-        return md_set_state(b->big[k], P + o, V + o, S ? S + b->a0[b->big_ids[k]] : nullptr, 1);
-    });
     if (tmp) cudaFree(tmp);
     if (tsp) cudaFree(tsp);
-    if (rc) return rc;
+    BCK(cudaMemset(b->st.err, 0, sizeof(uint32_t)));
+    BCK(cudaMemsetAsync(b->ea.valid, 0, sizeof(int32_t) * (size_t)b->nsys, b->stream));
+    BCK(cudaMemsetAsync(b->ea.rebuild, 0, sizeof(int32_t) * (size_t)b->nsys, b->stream));
+    BCK(cudaStreamSynchronize(b->stream));
     b->has_state = true;
     b->have_forces = false;
     return MD_OK;
@@ -436,11 +574,9 @@ int md_batch_step(md_batch* b, int32_t n_steps) {
     if (!b || n_steps < 0) return MD_ERR_ARG;
     if (!b->has_state) return bfail(b, MD_ERR_STATE, "no state: call md_batch_set_state first");
     if (n_steps == 0) return MD_OK;
-    int rc = run_buckets(b, n_steps, b->have_forces ? BATCH_HAVE_FORCES : 0);
+    int rc = run_ensemble(b, n_steps, b->have_forces ? BATCH_HAVE_FORCES : 0);
     if (rc) return rc;
-    rc = for_big(b, [&](int k) { return md_step(b->big[k], n_steps); });
     BCK(cudaStreamSynchronize(b->stream));
-    if (rc) return rc;
     if ((rc = check_batch_err(b))) return rc;
     b->have_forces = true;
     return MD_OK;
@@ -451,48 +587,31 @@ int md_batch_forces(md_batch* b, double* f_out, int device_ptrs) {
     if (!b->has_state) return bfail(b, MD_ERR_STATE, "no state");
     int rc;
     if (!b->have_forces) {
-        enqueue_buckets(b, 0, 0, b->stream);
-        BCK(cudaGetLastError());
+        if ((rc = run_ensemble(b, 0, 0))) return rc;
+        BCK(cudaStreamSynchronize(b->stream));
+        if ((rc = check_batch_err(b))) return rc;
         b->have_forces = true;
     }
     if (!f_out) return MD_OK;
     double* dst = device_ptrs ? f_out : b->d_aos;
-    for (int k = 0; k < b->nsys; ++k) {
-        if (b->path[k] != 0 || b->n[k] == 0) continue;
-        const int64_t lo = b->a0[k], hi = lo + b->n[k];
-        k_aos_out<<<(unsigned)((hi - lo + 255) / 256), 256, 0, b->stream>>>(lo, hi, b->st, 2, dst, nullptr);
-    }
+    if (b->ntot > 0) k_aos_out<<<(unsigned)((b->ntot + 255) / 256), 256, 0, b->stream>>>(b->ntot, b->st, b->d_sys_of, b->d_box, 2,
+                                                                           dst, nullptr);
     BCK(cudaGetLastError());
     BCK(cudaStreamSynchronize(b->stream));
-    if ((rc = check_batch_err(b))) return rc;
     if (!device_ptrs) BCK(cudaMemcpy(f_out, b->d_aos, sizeof(double) * 3 * b->ntot, cudaMemcpyDeviceToHost));
-    return for_big(b, [&](int k) {
-        return md_forces(b->big[k], f_out + 3 * b->a0[b->big_ids[k]], device_ptrs);
-    });
+    return MD_OK;
 }
 
 int md_batch_energies(md_batch* b, double* pe, double* ke) {
     if (!b || !pe || !ke) return MD_ERR_ARG;
     if (!b->has_state) return bfail(b, MD_ERR_STATE, "no state");
     int rc;
-    enqueue_buckets(b, 0, BATCH_ENERGY, b->stream);
-    BCK(cudaGetLastError());
-    b->have_forces = true;
-    std::vector<double> hp(b->nsys, 0.0), hk(b->nsys, 0.0);
-    BCK(cudaMemcpyAsync(hp.data(), b->d_pe, sizeof(double) * b->nsys, cudaMemcpyDeviceToHost, b->stream));
-    BCK(cudaMemcpyAsync(hk.data(), b->d_ke, sizeof(double) * b->nsys, cudaMemcpyDeviceToHost, b->stream));
+    if ((rc = run_ensemble(b, 0, BATCH_ENERGY))) return rc;
+    BCK(cudaMemcpyAsync(pe, b->d_pe, sizeof(double) * b->nsys, cudaMemcpyDeviceToHost, b->stream));
+    BCK(cudaMemcpyAsync(ke, b->d_ke, sizeof(double) * b->nsys, cudaMemcpyDeviceToHost, b->stream));
     BCK(cudaStreamSynchronize(b->stream));
     if ((rc = check_batch_err(b))) return rc;
-    rc = for_big(b, [&](int k) {
-        double e = 0, q = 0;
-        int r = md_energy_virial(b->big[k], &e, &q, nullptr);
-        hp[b->big_ids[k]] = e;
-        hk[b->big_ids[k]] = q;
-        return r;
-    });
-    if (rc) return rc;
-    std::copy(hp.begin(), hp.end(), pe);
-    std::copy(hk.begin(), hk.end(), ke);
+    b->have_forces = true;
     return MD_OK;
 }
 
@@ -506,12 +625,9 @@ int md_batch_get_state(md_batch* b, double* pos, double* vel, int32_t* image, in
         if (w == 2 && !image) continue;
         double* dst = device_ptrs ? o : b->d_aos;
         int32_t* idst = device_ptrs ? image : reinterpret_cast<int32_t*>(b->d_aos);
-        for (int k = 0; k < b->nsys; ++k) {
-            if (b->path[k] != 0 || b->n[k] == 0) continue;
-            const int64_t lo = b->a0[k], hi = lo + b->n[k];
-            k_aos_out<<<(unsigned)((hi - lo + 255) / 256), 256, 0, b->stream>>>(lo, hi, b->st, w == 2 ? 3 : w, dst,
-                                                                             idst);
-        }
+        if (b->ntot > 0)
+            k_aos_out<<<(unsigned)((b->ntot + 255) / 256), 256, 0, b->stream>>>(b->ntot, b->st, b->d_sys_of, b->d_box,
+                                                                                w == 2 ? 3 : w, dst, idst);
         BCK(cudaGetLastError());
         BCK(cudaStreamSynchronize(b->stream));
         if (!device_ptrs) {
@@ -519,21 +635,31 @@ int md_batch_get_state(md_batch* b, double* pos, double* vel, int32_t* image, in
             else BCK(cudaMemcpy(image, b->d_aos, sizeof(int32_t) * 3 * b->ntot, cudaMemcpyDeviceToHost));
         }
     }
-    return for_big(b, [&](int k) {
-        const int64_t o = 3 * b->a0[b->big_ids[k]];
-        return md_get_state(b->big[k], pos ? pos + o : nullptr, vel ? vel + o : nullptr, image ? image + o : nullptr,
-                            device_ptrs);
-    });
+    return MD_OK;
 }
 
 int md_batch_layout(md_batch* b, int32_t* path, int32_t* threads, int32_t* cell_range) {
     if (!b) return MD_ERR_ARG;
     for (int k = 0; k < b->nsys; ++k) {
-        const int bu = b->path[k] == 0 ? bucket_of(b->n[k]) : -1;
+        const bool one = b->path[k] == 0 && b->n[k] > 0;
         if (path) path[k] = b->path[k];
-        if (threads) threads[k] = bu >= 0 ? b->bk[bu].threads : 0;
-        if (cell_range) cell_range[k] = bu >= 0 ? b->bk[bu].R : 0;
+        if (threads) threads[k] = b->threads;
+        if (cell_range) cell_range[k] = one ? b->R[bucket_of(b->n[k])] : 1;
     }
+    return MD_OK;
+}
+
+int md_batch_set_wait_budget(md_batch* b, int64_t budget_cycles, int32_t held_system) {
+    if (!b || budget_cycles < 0 || held_system < -1 || held_system >= b->nsys) return MD_ERR_ARG;
+    b->budget = budget_cycles == 0 ? DEFAULT_BUDGET : budget_cycles;
+    b->hold = -1;
+    if (held_system >= 0)
+        for (size_t e = 0; e < b->ent.size(); ++e) {
+            const EnsEntry& en = b->ent[e];
+            const int id = en.kind == 0 ? b->one[en.idx].id : b->blk[en.idx].id;
+            if (id == held_system) b->hold = (int)e;
+        }
+    drop_graph(b);
     return MD_OK;
 }
 
@@ -542,9 +668,12 @@ int md_batch_autotune(md_batch* b, const char* cache_path) {
     if (!b->has_state) return bfail(b, MD_ERR_STATE, "no state: the autotuner times real steps");
     cudaDeviceProp prop;
     BCK(cudaGetDeviceProperties(&prop, b->device));
-    // cached choices for this GPU: bucket k -> (threads, R), or none for a bucket never tuned
-    int cached[NBUCKET][2];
-    for (int k = 0; k < NBUCKET; ++k) cached[k][0] = cached[k][1] = 0;
+    bool present[NBUCKET] = {};
+    for (int k = 0; k < b->nsys; ++k) {
+        const int bu = bucket_of(b->n[k]);
+        if (b->n[k] > 0 && bu >= 0) present[bu] = true;
+    }
+    // a cached shape for this GPU: threads, one-CTA limit and R per bucket
     if (cache_path) {
         FILE* f = std::fopen(cache_path, "r");
         if (f) {
@@ -553,109 +682,77 @@ int md_batch_autotune(md_batch* b, const char* cache_path) {
             std::fclose(f);
             buf[len] = 0;
             const std::string s(buf);
-            if (s.find(std::string("\"gpu\": \"") + prop.name + "\"") != std::string::npos) {
-                for (int k = 0; k < NBUCKET; ++k) {
-                    const std::string key = "\"bucket_" + std::to_string(k) + "\": [";
-                    const size_t at = s.find(key);
-                    int th = 0, R = 0;
-                    if (at != std::string::npos && std::sscanf(s.c_str() + at + key.size(), "%d, %d", &th, &R) == 2 &&
-                        (th == 128 || th == 256 || th == 512) && (R == 1 || R == 2)) {
-                        cached[k][0] = th;
-                        cached[k][1] = R;
-                    }
-                }
+            int th = 0, lim = 0, R[NBUCKET] = {0, 0, 0, 0, 0};
+            bool ok = s.find(std::string("\"gpu\": \"") + prop.name + "\"") != std::string::npos;
+            const size_t at = s.find("\"shape\": [");
+            ok = ok && at != std::string::npos &&
+                 std::sscanf(s.c_str() + at + 10, "%d, %d, %d, %d, %d, %d, %d", &th, &lim, &R[0], &R[1], &R[2], &R[3],
+                             &R[4]) == 7 &&
+                 (th == 128 || th == 256 || th == 512) && (lim == 1024 || lim == 2048 || lim == 4096);
+            for (int k = 0; k < NBUCKET; ++k) ok = ok && (R[k] == 1 || R[k] == 2);
+            if (ok) {
+                b->threads = th;
+                b->one_cta_max = lim;
+                for (int k = 0; k < NBUCKET; ++k) b->R[k] = R[k];
+                if (build_table(b) == MD_OK) return MD_OK;
             }
         }
     }
-    bool need = false, from_cache[NBUCKET] = {};
-    for (int k = 0; k < NBUCKET; ++k) {
-        md_batch::Bucket& B = b->bk[k];
-        if (B.ids.empty()) continue;
-        if (cached[k][0] && bucket_fits(b, k, cached[k][0], cached[k][1])) {
-            B.threads = cached[k][0];
-            B.R = cached[k][1];
-            if (upload_bucket(b, k)) return MD_ERR_CUDA;
-            from_cache[k] = true;
-        } else {
-            need = true;
-        }
-    }
-    if (!need) return MD_OK;
-    // time 10 steps per candidate on a copy of the state, restored afterwards
+    // time 10 steps per candidate on a copy of the state, restored afterwards: the launch
+    // size, then the one-CTA limit, then the cell divisor of each size bucket present
     const size_t n = (size_t)b->ntot;
-    double* dsave = nullptr;
-    int32_t* isave = nullptr;
-    long long* fsave = nullptr;
-    BCK(cudaMalloc(&dsave, sizeof(double) * 6 * std::max<size_t>(n, 1)));
-    BCK(cudaMalloc(&isave, sizeof(int32_t) * 3 * std::max<size_t>(n, 1)));
-    BCK(cudaMalloc(&fsave, sizeof(long long) * 3 * std::max<size_t>(n, 1)));
-    double* D[6] = {b->st.x, b->st.y, b->st.z, b->st.vx, b->st.vy, b->st.vz};
-    int32_t* I[3] = {b->st.ix, b->st.iy, b->st.iz};
-    auto snap = [&](bool restore) {
-        for (int c = 0; c < 6; ++c)
-            cudaMemcpyAsync(restore ? D[c] : dsave + c * n, restore ? dsave + c * n : D[c], sizeof(double) * n,
-                            cudaMemcpyDeviceToDevice, b->stream);
-        for (int c = 0; c < 3; ++c)
-            cudaMemcpyAsync(restore ? I[c] : isave + c * n, restore ? isave + c * n : I[c], sizeof(int32_t) * n,
-                            cudaMemcpyDeviceToDevice, b->stream);
-        cudaMemcpyAsync(restore ? b->st.fq : fsave, restore ? fsave : b->st.fq, sizeof(long long) * 3 * n,
-                        cudaMemcpyDeviceToDevice, b->stream);
-    };
-    snap(false);
+    Snapshot sn;
+    BCK(cudaMalloc(&sn.d, sizeof(double) * 6 * std::max<size_t>(n, 1)));
+    BCK(cudaMalloc(&sn.i, sizeof(int32_t) * 3 * std::max<size_t>(n, 1)));
+    BCK(cudaMalloc(&sn.f, sizeof(long long) * 3 * std::max<size_t>(n, 1)));
+    snap(b, sn, false);
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    const int cand_t[3] = {128, 256, 512};
-    std::string json = std::string("{\"gpu\": \"") + prop.name + "\"";
-    for (int k = 0; k < NBUCKET; ++k) {
-        md_batch::Bucket& B = b->bk[k];
-        float best = 1e30f;
-        int bt = B.threads, bR = B.R;
-        if (!B.ids.empty() && !from_cache[k]) {
-            for (int R = 1; R <= 2; ++R)
-                for (int th : cand_t) {
-                    if (!bucket_fits(b, k, th, R)) continue;
-                    B.threads = th;
-                    B.R = R;
-                    if (upload_bucket(b, k)) return MD_ERR_CUDA;
-                    launch_batch_run(B.d_sys, (int)B.ids.size(), b->st, b->pt, 1, 0, b->dt, B.threads, B.nmax, B.cmax,
-                                     b->d_pe, b->d_ke, b->pe_atom, b->stream);  // warm-up
-                    cudaEventRecord(e0, b->stream);
-                    launch_batch_run(B.d_sys, (int)B.ids.size(), b->st, b->pt, 10, BATCH_HAVE_FORCES, b->dt,
-                                     B.threads, B.nmax, B.cmax, b->d_pe, b->d_ke, b->pe_atom, b->stream);
-                    cudaEventRecord(e1, b->stream);
-                    BCK(cudaEventSynchronize(e1));
-                    float ms = 0.f;
-                    cudaEventElapsedTime(&ms, e0, e1);
-                    snap(true);
-                    if (ms < best) {
-                        best = ms;
-                        bt = th;
-                        bR = R;
-                    }
-                }
-            B.threads = bt;
-            B.R = bR;
-            if (upload_bucket(b, k)) return MD_ERR_CUDA;
-            cached[k][0] = bt;
-            cached[k][1] = bR;
-        }
-        if (cached[k][0])  // buckets never tuned are left out of the cache
-            json += ", \"bucket_" + std::to_string(k) + "\": [" + std::to_string(cached[k][0]) + ", " +
-                    std::to_string(cached[k][1]) + "]";
+    const int hold = b->hold;
+    const long long budget = b->budget;
+    b->hold = -1;
+    b->budget = DEFAULT_BUDGET;
+    float best = time_shape(b, sn, e0, e1);
+    for (int th : {128, 512}) {
+        const int keep = b->threads;
+        b->threads = th;
+        const float ms = time_shape(b, sn, e0, e1);
+        if (ms < best) best = ms;
+        else b->threads = keep;
     }
-    json += "}\n";
+    for (int lim : {1024, 4096}) {
+        const int keep = b->one_cta_max;
+        b->one_cta_max = lim;
+        const float ms = time_shape(b, sn, e0, e1);
+        if (ms < best) best = ms;
+        else b->one_cta_max = keep;
+    }
+    for (int k = 0; k < NBUCKET; ++k) {
+        if (!present[k]) continue;
+        b->R[k] = 2;
+        const float ms = time_shape(b, sn, e0, e1);
+        if (ms < best) best = ms;
+        else b->R[k] = 1;
+    }
+    b->hold = hold;
+    b->budget = budget;
+    const int rc = build_table(b);
+    snap(b, sn, true);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     BCK(cudaStreamSynchronize(b->stream));
-    cudaFree(dsave);
-    cudaFree(isave);
-    cudaFree(fsave);
-    if (cudaMemset(b->st.err, 0, sizeof(uint32_t)) != cudaSuccess) return MD_ERR_CUDA;
+    cudaFree(sn.d);
+    cudaFree(sn.i);
+    cudaFree(sn.f);
+    if (rc) return rc;
+    BCK(cudaMemset(b->st.err, 0, sizeof(uint32_t)));
+    b->have_forces = false;
     if (cache_path) {
         FILE* f = std::fopen(cache_path, "w");
         if (f) {
-            std::fputs(json.c_str(), f);
+            std::fprintf(f, "{\"gpu\": \"%s\", \"shape\": [%d, %d, %d, %d, %d, %d, %d]}\n", prop.name, b->threads,
+                         b->one_cta_max, b->R[0], b->R[1], b->R[2], b->R[3], b->R[4]);
             std::fclose(f);
         }
     }
@@ -671,14 +768,7 @@ int md_batch_last_error(md_batch* b, char* buf, int64_t len) {
 void md_batch_destroy(md_batch* b) {
     if (!b) return;
     if (b->gexec) cudaGraphExecDestroy(b->gexec);
-    for (md_system* m : b->big) md_destroy(m);
-    for (cudaStream_t s : b->big_streams) cudaStreamDestroy(s);
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
-    for (int k = 0; k < NBUCKET; ++k) {
-        if (b->bucket_streams[k]) cudaStreamDestroy(b->bucket_streams[k]);
-        if (b->join_ev[k]) cudaEventDestroy(b->join_ev[k]);
-    }
-    if (b->fork_ev) cudaEventDestroy(b->fork_ev);
     for (void* p : b->allocs) cudaFree(p);
     delete b;
 }

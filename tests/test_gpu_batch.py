@@ -2,10 +2,11 @@
 
 Inputs: seeded systems of uneven size from workloads.batch_ensemble (fcc sites with
 vacancies at exact density, Gaussian jitter, thermal velocities), the shape of the
-512-system ensemble workload, with sizes chosen so that both execution paths (one
-CTA per system, and md_system for the larger ones) are exercised.  Bars: forces
-within 2e-5 (per atom, against the RMS), potential energy within 1e-6, kinetic
-energy within 1e-12; bit-identical repeats; short trajectories close to the oracle's.
+512-system ensemble workload, with sizes chosen so that both execution paths of the
+one persistent launch (one CTA per system, and block tasks shared by all CTAs for the
+larger ones) are exercised.  Bars: forces within 2e-5 (per atom, against the RMS),
+potential energy within 1e-6, kinetic energy within 1e-12; bit-identical repeats; short
+trajectories close to the oracle's.
 """
 import os
 import tempfile
@@ -25,6 +26,7 @@ from paper_1305_4196_gb300 import workloads as W  # noqa: E402
 
 B.build()
 from paper_1305_4196_gb300 import batch as BA  # noqa: E402
+from paper_1305_4196_gb300 import mdgb as M  # noqa: E402
 
 P = O.LJParams.single()
 
@@ -91,11 +93,11 @@ def test_energy_after_100_steps_matches_oracle():
     """The potential is unshifted, so the total energy jumps by u(r_cut) whenever a pair
     crosses the cutoff and drifts while an fcc start melts; the reference for the energy
     after 100 steps is therefore the FP64 oracle's own trajectory (per atom, within 1e-4)."""
-    systems = [W.fcc_vacancies(n, 0.8, 0.9, seed=5 + n) for n in (300, 900, 2500)]
+    systems = [W.fcc_vacancies(n, 0.8, 0.9, seed=5 + n) for n in (300, 900, 6000)]
     b = BA.from_systems(systems)
+    assert b.layout()[0].tolist() == [0, 0, 1]  # the 6,000-atom system runs as block tasks
     b.step(100)
     pe, ke = b.energies()
-    assert np.all(b.layout()[0] == 0)
     for k, s in enumerate(systems):
         ref = O.run_nve(s.pos, s.vel, s.box, P, 0.005, 0.3, 100, history=True)
         e_ref = ref["pe"][-1] + ref["ke"][-1]
@@ -111,14 +113,12 @@ def test_autotune_writes_and_reads_its_cache():
     after = b.get_state()
     assert all(np.array_equal(x, y) for x, y in zip(before, after))  # the state is restored
     text = open(path).read()
-    # sizes 338, 417 | 1758 | 4370, 4653, 7216: buckets 0, 2 and 4 are tuned, 1 and 3 hold no system
-    assert '"gpu":' in text and all(f'"bucket_{k}":' in text for k in (0, 2, 4))
-    assert '"bucket_1":' not in text and '"bucket_3":' not in text
-    _, th, R = b.layout()
+    assert '"gpu":' in text and '"shape": [' in text
+    lay = b.layout()
     c = BA.from_systems(systems)
     c.autotune(path)
-    _, th2, R2 = c.layout()
-    assert np.array_equal(th, th2) and np.array_equal(R, R2)
+    lay2 = c.layout()
+    assert all(np.array_equal(x, y) for x, y in zip(lay, lay2))
     for s, F in zip(systems, split(c.forces(), systems)):
         assert force_error(F, O.lj_forces(s.pos, s.box, P)[0]) <= 2e-5
 
@@ -157,3 +157,50 @@ def test_full_ensemble_sampled_systems():
         sl = slice(offs[k], offs[k + 1])
         Fref, _, _ = O.lj_forces(pos[sl], systems[k].box, P)
         assert force_error(F[sl], Fref) <= 2e-5, k
+
+
+def test_cutoff_decided_by_the_definition_in_block_tasks():
+    """Pairs at r_cut (1 -/+ 1e-7), 5 sigma apart, in a 2,200-atom system, which runs as
+    block tasks."""
+    box = np.array([55.0, 55.0, 55.0])
+    pos = W.threshold_pairs(1100, box, 2.5, 1e-7, seed=31)
+    s = W.System(pos, np.zeros_like(pos), np.zeros(len(pos), dtype=np.int32), box)
+    b = BA.from_systems([s])
+    assert b.layout()[0].tolist() == [1]
+    Fref, _, _ = O.lj_forces(s.pos, s.box, P)
+    F = b.forces()
+    assert np.abs(Fref).max() > 0.03
+    assert np.abs(F - Fref).max() <= 2e-5 * np.abs(Fref).max()
+
+
+def test_close_pairs_in_block_tasks_exact():
+    """Pairs at 0.6 sigma (force terms beyond the 32-bit split) in a block-task system are
+    finished by the exact pass: forces match the oracle."""
+    s = W.fcc_vacancies(6000, 0.8, 0.9, seed=41)
+    pos = s.pos.copy()
+    for i in range(0, 40, 4):
+        pos[i + 1] = W.wrap(pos[i] + np.array([0.6, 0.0, 0.0]), s.box)
+    s2 = W.System(pos, s.vel, s.species, s.box)
+    b = BA.from_systems([s2])
+    assert b.layout()[0].tolist() == [1]
+    Fref, _, _ = O.lj_forces(pos, s.box, P)
+    assert np.abs(b.forces() - Fref).max() <= 2e-5 * np.abs(Fref).max()
+
+
+def test_wait_timeout_is_reported_without_a_fault():
+    """A held system never becomes ready, so the CTAs run out of work and out of their wait
+    budget: the call returns MD_ERR_TIMEOUT, the context stays usable, and after a new state
+    the ensemble steps exactly like a fresh one."""
+    systems = ensemble(k=6, seed=13, n_max=6000)
+    b = BA.from_systems(systems)
+    b.set_wait_budget(2_000_000, held_system=int(np.argmax([s.n for s in systems])))
+    with pytest.raises(M.MDError) as e:
+        b.step(5)
+    assert e.value.code == M.MD_ERR_TIMEOUT
+    b.set_wait_budget(0, -1)
+    b.set_state(np.ascontiguousarray(np.concatenate([s.pos for s in systems])),
+                np.ascontiguousarray(np.concatenate([s.vel for s in systems])))
+    b.step(5)
+    c = BA.from_systems(systems)
+    c.step(5)
+    assert all(np.array_equal(x, y) for x, y in zip(b.get_state(), c.get_state()))
