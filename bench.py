@@ -239,6 +239,12 @@ def algorithmic_force_bytes(n, entries, precision):
     return n * per_atom + 4 * entries
 
 
+def algorithmic_half_bytes(n, entries, precision):
+    """The same for a half-list (Newton-3) evaluation: each pair once, and per atom also the
+    24 B of force read back when the reactions of a block's tile are added to it."""
+    return algorithmic_force_bytes(n, entries, precision) + 24 * n
+
+
 def algorithmic_fused_bytes(n, entries):
     """The same for the force kernel with the velocity-Verlet updates fused in: the force
     part without the force write (16 + 4 B per atom, 4 B per entry) plus the update's
@@ -323,9 +329,13 @@ def run_ours(args):
     if fused:
         abytes = algorithmic_fused_bytes(sysm.n, info1["list_entries"])
         kname = "k_force_mixed_full<1, 0, FM_KKD> (forces + velocity Verlet)"
-    else:
+    elif args.list == "full":
         abytes = algorithmic_force_bytes(sysm.n, info1["list_entries"], args.precision)
         kname = "k_force_mixed_full" if args.precision == "mixed" else "k_force_fp64_full"
+    else:
+        abytes = algorithmic_half_bytes(sysm.n, info1["list_entries"], args.precision)
+        kname = {"half": "k_force_mixed_half" if args.precision == "mixed" else "k_force_fp64_half",
+                 "half_af": "k_force_half_af"}[args.list] + " (8 colour launches per evaluation)"
     achieved = abytes / (f_ms * 1e-3) / 1e9
     roofline = {"bound": "hbm", "kernel": kname,
                 "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
@@ -345,7 +355,8 @@ def run_ours(args):
     i_f1 = s.info()
     s.set_timing(False)
     fo_ms = (i_f1["force_ms"] - i_f0["force_ms"]) / max(i_f1["timed_force_evals"] - i_f0["timed_force_evals"], 1)
-    fo_bytes = algorithmic_force_bytes(sysm.n, i_f1["list_entries"], args.precision)
+    fo_bytes = (algorithmic_force_bytes if args.list == "full" else algorithmic_half_bytes)(
+        sysm.n, i_f1["list_entries"], args.precision)
     roofline["force_kernel_alone"] = {"avg_launch_ms": fo_ms, "algorithmic_bytes": fo_bytes,
                                       "achieved": fo_bytes / (fo_ms * 1e-3) / 1e9,
                                       "frac": fo_bytes / (fo_ms * 1e-3) / 1e9 / peak,
