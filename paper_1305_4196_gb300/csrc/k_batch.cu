@@ -985,6 +985,9 @@ __device__ __forceinline__ int ld_relaxed_s32(const int* p) {
 // ever waits.  A CTA that finds no work keeps looking until every entry is done; if it finds
 // none for ea.budget cycles it sets ERR_TIMEOUT and ends (as do all others, once they see
 // the bit), so the host gets MD_ERR_TIMEOUT instead of a hung launch.
+#ifndef CLAIM_MANY
+#define CLAIM_MANY 4
+#endif
 // Up to 128 registers a thread: capped at 64 (four 256-thread CTAs per SM) the block tasks
 // spill and the 512-system ensemble ran 20 % slower (2.66 against 2.20 ms per step) than
 // with two CTAs per SM unspilled.
@@ -1022,8 +1025,9 @@ __global__ void __launch_bounds__(BATCH_MAX_THREADS, 1)
                 unsigned long long w = live ? ld_relaxed_u64(ea.ctl + e) : 0ull;
                 const uint32_t p = (uint32_t)(w >> 32), nx = (uint32_t)w;
                 const int T = live && p < ENS_HOLD ? ens_ntasks(ent[e], p, K) : 0;
-                // two tasks at once from phases of eight or more: half the claims
-                const int want = (int)nx + 2 <= T && T >= 8 ? 2 : 1;
+                // several tasks at once from large phases: fewer claims
+                const int want = (int)nx + CLAIM_MANY <= T && T >= 16 * CLAIM_MANY ? CLAIM_MANY
+                                 : ((int)nx + 2 <= T && T >= 8 ? 2 : 1);
                 bool can = (int)nx < T;
                 unsigned m = __ballot_sync(0xffffffffu, can);
                 while (m) {
