@@ -204,3 +204,23 @@ def test_wait_timeout_is_reported_without_a_fault():
     c = BA.from_systems(systems)
     c.step(5)
     assert all(np.array_equal(x, y) for x, y in zip(b.get_state(), c.get_state()))
+
+
+def test_empty_system_in_the_ensemble():
+    """A system of no atoms beside a one-CTA and a block system: it has no work and zero
+    energies, and the others match the oracle."""
+    a = W.fcc_vacancies(300, 0.8, 0.9, seed=51)
+    c = W.fcc_vacancies(7000, 0.8, 0.9, seed=52)
+    empty = W.System(np.zeros((0, 3)), np.zeros((0, 3)), np.zeros(0, dtype=np.int32), np.array([10.0, 10.0, 10.0]))
+    systems = [a, empty, c]
+    b = BA.from_systems(systems)
+    assert b.layout()[0].tolist() == [0, 0, 1]
+    F = b.forces()
+    for s, Fs in zip(systems, split(F, systems)):
+        if s.n:
+            assert force_error(Fs, O.lj_forces(s.pos, s.box, P)[0]) <= 2e-5
+    pe, ke = b.energies()
+    assert pe[1] == 0.0 and ke[1] == 0.0
+    b.step(5)
+    pos, _, _ = b.get_state()
+    assert pos.shape == (a.n + c.n, 3) and np.isfinite(pos).all()
