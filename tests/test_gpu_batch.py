@@ -141,7 +141,7 @@ def test_cutoff_decided_by_the_definition():
 
 def test_full_ensemble_sampled_systems():
     """The benchmark's ensemble itself: 512 systems, 3.6 million atoms, autotuned, 10 steps.
-    Forces of sampled systems on both paths (one CTA per system and md_system), at the
+    Forces of sampled systems on both paths (one CTA per system and block tasks), at the
     state the GPU reached, match the oracle's."""
     systems = W.batch_ensemble(512, seed=4)
     b = BA.from_systems(systems)
