@@ -549,6 +549,8 @@ def batch_ensemble_timing(stream, steps=200, autotune=True):
            "unit": METRIC, "seconds": dt, "kernel_launches_per_call": 1,
            "one_cta_systems": int((path == 0).sum()), "block_task_systems": int((path == 1).sum()),
            "one_cta_atoms": int(sum(s.n for s, p in zip(systems, path) if p == 0)),
+           "largest_one_cta_system": int(max([s.n for s, p in zip(systems, path) if p == 0], default=0)),
+           "smallest_block_task_system": int(min([s.n for s, p in zip(systems, path) if p == 1], default=0)),
            "autotune_seconds": t_tune, "tuned_threads": int(threads[0]),
            "tuned_cell_range_by_size": sorted({int(r) for r in R[path == 0]})}
     b.close()
