@@ -1,12 +1,13 @@
-// k_batch.cu - ensembles of small independent systems, one CTA per system.
+// k_batch.cu - ensembles of independent systems in one persistent launch.
 //
 // The paper notes that its task functor can carry which copy of a system a task
-// works on, so that replicas share one schedule (Sec. II.C).  On the GPU an ensemble
-// of small periodic systems (a few hundred to a few thousand atoms) is run by one
-// persistent launch in which each CTA owns one whole system for all of its time
-// steps: the system's FP32 coordinates and linked cells live in shared memory, and
-// no two CTAs ever touch the same particle, so the launch needs no synchronisation
-// between CTAs at all.  Per step the CTA
+// works on, so that replicas share one schedule (Sec. II.C).  Here every call on an
+// ensemble is one launch of k_ensemble_run (at the end of this file), whose CTAs take
+// tasks from a device work table over all systems.  Two kinds of system:
+//
+// A small system (a few hundred to a few thousand atoms) is one task: one CTA owns it
+// for all time steps of the call; its FP32 coordinates and linked cells live in shared
+// memory and no other CTA touches it.  Per step the CTA
 //   * re-bins its atoms into cells at least r_cut / R wide (counting sort in shared
 //     memory; atoms of a cell kept in index order),
 //   * evaluates the cutoff LJ force on every atom over the (2R+1)^3 surrounding cells:
@@ -19,6 +20,9 @@
 //   * and integrates velocity Verlet in FP64.
 // There is no neighbour list: the cells are rebuilt every step, which for systems of
 // this size costs less than a list build would.
+//
+// A larger system is advanced in phases of tasks that any CTA may take, with Verlet
+// lists (the block systems below).
 #include "mdgb_batch_internal.cuh"
 #include "nl_scan.cuh"
 
