@@ -696,6 +696,13 @@ def test_small_box_full_list_even_cell_count(precision):
     ref = O.run_nve(sysm.pos, sysm.vel, sysm.box, P, DT, SKIN, 20)
     dx = np.abs(pos + img * sysm.box - (ref["pos"] + ref["image"] * sysm.box)).max()
     assert dx < (1e-10 if precision == "fp64" else 1e-6)
+    # 3 blocks per side cannot be split into the 8 parity classes of Sec. II.A: the race
+    # detector refuses 8 phases on this grid, while one phase of all 27 blocks still shows
+    # the overlap of neighbouring tiles.
+    with pytest.raises(M.MDError) as ei:
+        s.colour_conflicts(8)
+    assert ei.value.code == M.MD_ERR_ARG
+    assert s.colour_conflicts(1) > 0
 
 
 def test_whole_system_tile_limit_is_reported():
