@@ -92,7 +92,7 @@ typedef struct {
 
 typedef struct {
     int64_t n;             /* atoms */
-    int32_t ncell[3];      /* cells per dimension (multiples of 4, or 6 for full lists) */
+    int32_t ncell[3];      /* cells per dimension (multiples of 4; full lists also other even counts >= 6) */
     int32_t list_cap;      /* current neighbour-list capacity per atom */
     int32_t tile_cap;      /* current on-chip tile capacity (atoms of a 4x4x4-cell neighbourhood) */
     int64_t n_builds;      /* neighbour-list builds so far */
@@ -119,7 +119,15 @@ typedef struct {
  * colour classes, Sec. II.D.2 blocking).  MD_LIST_FULL needs no colour classes
  * and takes 6 cells on a side where 6 fit but the rule gives 4, so that the
  * 4x4x4-cell neighbourhood of a block is not the whole box.  At least 4 cells
- * per side.  Allocates all device workspace.
+ * per side.  A homogeneous system on the mixed full-list path (every block
+ * occupied at its first build after md_set_state, largest tile within 1.25x
+ * the mean) then takes coarser cells once, never more of them: per side the
+ * smallest even count (at least 6) whose width is at most (224 / (8 rho))^(1/3),
+ * rho = N / V, so that a 2x2x2-cell block holds about 224 atoms for the
+ * force kernel's 256 threads (44 -> 42 cells per side for 2,048,000 atoms at
+ * rho* = 0.8442).  MDGB_FIT_GRID=1 in the environment at md_create keeps the
+ * first grid.  md_get_info reports the grid in use.  Allocates all device
+ * workspace.
  * Errors: MD_ERR_ARG, MD_ERR_BOX_TOO_SMALL, MD_ERR_CUDA.  *out is NULL on error.
  */
 int md_create(int64_t n, const double box[3], double r_cut, double skin,

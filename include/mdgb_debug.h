@@ -24,7 +24,8 @@ extern "C" {
 
 /* Cells per dimension md_create() picks for box[3], list radius r_list and list
  * kind list_kind (MD_LIST_*): the largest multiple of 4 with width >= r_list, or 6
- * for MD_LIST_FULL where 6 fit and that multiple is 4.
+ * for MD_LIST_FULL where 6 fit and that multiple is 4 (a homogeneous mixed full-list
+ * system may take fewer, coarser cells at its first build; see md_create).
  * MD_ERR_BOX_TOO_SMALL (-2) if < 4. */
 int mdgb_grid_shape(const double box[3], double r_list, int32_t list_kind, int32_t nc_out[3]);
 

@@ -79,6 +79,11 @@ struct md_system {
     bool snapshot_first = true;
     int compact = 0;          // grid of the occupied-block loops of a mostly empty system (see do_build)
     bool no_compact = false;  // MDGB_NO_COMPACT=1 at md_create: one CTA per block always
+    // the cell grid of a homogeneous mixed-precision full-list system is chosen once, at its
+    // first build (see regrid_homogeneous); MDGB_FIT_GRID=1 at md_create keeps the r_list fit
+    bool grid_decided = false;
+    bool fit_grid = false;
+    int64_t ncell_alloc = 0;  // cells (and 1/8 as many blocks) the cell and block arrays hold
     char msg[512] = "";
 };
 
@@ -293,6 +298,76 @@ int do_bin(md_system* s, int p = 0) {
 }
 
 // ---- list build with capacity regrowth (host-visible: reads the device counters)
+static int tile_margin_knob() {
+    static int v = getenv("MDGB_TILE_MARGIN") ? atoi(getenv("MDGB_TILE_MARGIN")) : 4;
+    return v;
+}
+void set_cut_band(md_system* s);
+
+// Cell centres (c + 1/2) w in the kernels' cell numbering, for the current grid.
+int upload_centres(md_system* s) {
+    const Geometry& g = s->g;
+    std::vector<double> ctr(3 * (size_t)g.ncell);
+    for (int c = 0; c < g.ncell; ++c) {
+        int cx, cy, cz;
+        cell_coords(g, c, cx, cy, cz);
+        ctr[c] = (cx + 0.5) * g.w[0];
+        ctr[g.ncell + c] = (cy + 0.5) * g.w[1];
+        ctr[2 * (size_t)g.ncell + c] = (cz + 0.5) * g.w[2];
+    }
+    for (int k = 0; k < 3; ++k) s->st[k].ncell = g.ncell;
+    return cudaMemcpy(s->st[0].centre, ctr.data(), sizeof(double) * ctr.size(), cudaMemcpyHostToDevice) == cudaSuccess
+               ? MD_OK
+               : MD_ERR_CUDA;
+}
+
+// Cells coarser than the r_list fit for a homogeneous system on the mixed full-list path.
+// The force kernel runs a 2x2x2-cell block on 256 threads, one per own atom; at the fit
+// grid a block of the liquid (rho* = 0.8442, 44 cells per side at 2,048,000 atoms) holds
+// ~190 atoms and leaves two of eight warps idle until its CTA ends.  Cells of width
+// w = (224 / (8 rho))^(1/3), rho = N / V, fill a block with ~224 atoms on average (7/8 of
+// the threads, margin for density fluctuations); per side the smallest even count with at
+// most that width, never more than the fit's count nor fewer than 6 (linear block numbering
+// where not a multiple of 4: full lists need no colour classes).  Decided once, at the
+// first build, from the fit grid's binning: only when every block is occupied and the
+// largest tile is within 1.25x the mean, so that N / V is the local density (a slab or
+// particles in vacuum keep the fit grid).  Returns true when the grid changed (lists and
+// graphs then need rebuilding).
+bool regrid_homogeneous(md_system* s, int nocc, int max_tile) {
+    if (s->grid_decided) return false;
+    s->grid_decided = true;
+    if (s->fit_grid || !mixed(s) || half(s) || s->potential != 0 || s->n == 0) return false;
+    Geometry& g = s->g;
+    if (nocc < g.nblock) return false;
+    const double mean_tile = 8.0 * (double)s->n / g.nblock;  // 64 of the 8 * nblock cells
+    if (max_tile > 1.25 * mean_tile + 1.0) return false;
+    const double rho = (double)s->n / (s->box[0] * s->box[1] * s->box[2]);
+    const double w_want = std::cbrt(224.0 / (8.0 * rho));
+    // never more cells than the fit grid: every cell and block array is sized for it
+    int nc[3];
+    bool change = false;
+    for (int d = 0; d < 3; ++d) {
+        int want = (int)std::ceil(s->box[d] / w_want);
+        want += want & 1;
+        nc[d] = std::min(g.nc[d], std::max(want, 6));
+        change |= nc[d] != g.nc[d];
+    }
+    if (!change || (int64_t)nc[0] * nc[1] * nc[2] > s->ncell_alloc) return false;
+    for (int d = 0; d < 3; ++d) {
+        g.nc[d] = nc[d];
+        g.w[d] = s->box[d] / nc[d];
+        g.inv_w[d] = nc[d] / s->box[d];
+        for (int t = 0; t < 4; ++t) s->to.off[d][t] = (float)((t - 1.5) * g.w[d]);
+    }
+    set_block_layout(g);
+    set_cut_band(s);
+    if (upload_centres(s) != MD_OK) return false;
+    s->graphs_valid = false;
+    s->lists_valid = false;
+    s->forces_valid = false;
+    return true;
+}
+
 int do_build(md_system* s, int p = 0) {
     std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
     if (s->timing && s->n > 0) {
@@ -327,7 +402,7 @@ int do_build(md_system* s, int p = 0) {
         bool again = false;
         if (e & ERR_TILE_OVERFLOW) {
             // a tile never holds more than all atoms plus the dummy slot
-            int cap = std::max(max_tile, std::min(round_up(max_tile + max_tile / 4 + 64, 32),
+            int cap = std::max(max_tile, std::min(round_up(max_tile + max_tile / tile_margin_knob() + 64, 32),
                                                   round_up((int)s->n + 1, 32)));
             if (cap > 32767) return fail(s, MD_ERR_CELL_OVERFLOW, "tile of %d atoms exceeds 15-bit indices", max_tile);
             s->tile_cap = cap;
@@ -369,9 +444,13 @@ int do_build(md_system* s, int p = 0) {
             // keep the tile capacity close to the need (max_tile counts the dummy slot) so
             // that more CTAs fit per SM and every shared-memory layout stays within limits
             // (25 % headroom: later rebuilds inside graph-launched steps reuse this capacity)
-            s->tile_cap = std::max(max_tile, std::min(round_up(max_tile + max_tile / 4 + 64, 32),
+            s->tile_cap = std::max(max_tile, std::min(round_up(max_tile + max_tile / tile_margin_knob() + 64, 32),
                                                       round_up((int)s->n + 1, 32)));
             s->tile_cap = std::max(s->tile_cap, s->tile_floor);
+            if (regrid_homogeneous(s, nocc, max_tile)) {
+                --s->n_builds;  // the fit grid's build is replaced
+                return do_build(s, p);
+            }
             return MD_OK;
         }
     }
@@ -966,6 +1045,8 @@ int md_create(int64_t n, const double box[3], double r_cut, double skin, const m
         s->no_fuse = nf && nf[0] && nf[0] != '0';
         const char* nc = std::getenv("MDGB_NO_COMPACT");
         s->no_compact = nc && nc[0] && nc[0] != '0';
+        const char* fg = std::getenv("MDGB_FIT_GRID");
+        s->fit_grid = fg && fg[0] && fg[0] != '0';
     }
     s->n = n;
     s->np = round_up((int)std::max<int64_t>(n, 1), 64);
@@ -999,7 +1080,11 @@ int md_create(int64_t n, const double box[3], double r_cut, double skin, const m
         if (!(box[d] > 0.0) || !std::isfinite(box[d])) return bail(MD_ERR_ARG);
         s->box[d] = box[d];
         const int fit = (int)std::min(std::floor(box[d] / (s->rl * (1.0 + 1e-12))), 1024.0);
-        const int nc = grid_cells(fit, s->list_kind == MD_LIST_FULL);
+        int nc = grid_cells(fit, s->list_kind == MD_LIST_FULL);
+        if (getenv("MDGB_NC") && s->list_kind == MD_LIST_FULL) {
+            const int want = atoi(getenv("MDGB_NC"));
+            if (want >= 6 && want % 2 == 0 && want <= fit) nc = want;
+        }
         if (nc < 4) {
             fail(s, MD_ERR_BOX_TOO_SMALL, "box side %g < 4 r_list", box[d]);
             return bail(MD_ERR_BOX_TOO_SMALL);
@@ -1056,19 +1141,8 @@ int md_create(int64_t n, const double box[3], double r_cut, double skin, const m
             return bail(rc);
     }
     d0.ncell = g.ncell;
-    {
-        // cell centres (c + 1/2) w in the kernels' block-major numbering
-        std::vector<double> ctr(3 * (size_t)g.ncell);
-        for (int c = 0; c < g.ncell; ++c) {
-            int cx, cy, cz;
-            cell_coords(g, c, cx, cy, cz);
-            ctr[c] = (cx + 0.5) * g.w[0];
-            ctr[g.ncell + c] = (cy + 0.5) * g.w[1];
-            ctr[2 * (size_t)g.ncell + c] = (cz + 0.5) * g.w[2];
-        }
-        if (cudaMemcpy(d0.centre, ctr.data(), sizeof(double) * ctr.size(), cudaMemcpyHostToDevice) != cudaSuccess)
-            return bail(MD_ERR_CUDA);
-    }
+    s->ncell_alloc = g.ncell;
+    if (upload_centres(s) != MD_OK) return bail(MD_ERR_CUDA);
     for (int k = 1; k < 3; ++k) {
         DevState& d1 = s->st[k];
         d1.cell_start = d0.cell_start;

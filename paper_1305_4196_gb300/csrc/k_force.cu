@@ -272,12 +272,13 @@ __device__ __forceinline__ void full_block(const DevState& s, const Geometry& g,
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ TileMeta m;
     __shared__ SpeciesTable stab;
-    __shared__ int nqueued;
     __shared__ WarpWide wwide[FULL_THREADS / 32];
     float4* tile = reinterpret_cast<float4*>(smem);
-    uint16_t* queued = reinterpret_cast<uint16_t*>(tile + tile_cap);  // own atoms left to finish_atom_warp
+    // own atoms left to finish_atom_warp: bit ui % 32 of word ui / 32.  Own atom ui runs on
+    // thread ui % blockDim.x, so word w is written and read by warp w % (warps) alone
+    unsigned* qmask = reinterpret_cast<unsigned*>(tile + tile_cap);
+    const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     load_species_table(pt, stab);
-    if (threadIdx.x == 0) nqueued = 0;
     tile_meta(g, s.cell_start, b, m);
     const int T = m.prefix[64];
     if (T + 1 > tile_cap) {
@@ -296,6 +297,9 @@ __device__ __forceinline__ void full_block(const DevState& s, const Geometry& g,
     const int nsp = pt.nsp;
     const f2_t magic2 = f2_pack(MAGIC, MAGIC);
     const f2_t two21 = f2_pack(TWO21, TWO21);
+    for (int w = warp; w < (nown + 31) >> 5; w += nwarps)
+        if ((threadIdx.x & 31) == 0) qmask[w] = 0u;
+    __syncwarp();
     for (int ui = threadIdx.x; ui < nown; ui += blockDim.x) {
         const int gi = blk0 + ui;
         const float4 pi = tile[ui];
@@ -396,7 +400,7 @@ __device__ __forceinline__ void full_block(const DevState& s, const Geometry& g,
         // force on either path
         if (SINGLE) bad |= (mdist <= pt.band_half_f) | (mr2 < pt.r2_wide_f);
         if (bad) {  // finished after the loop by finish_atom_warp, epilogue included
-            queued[atomicAdd(&nqueued, 1)] = (uint16_t)ui;
+            atomicOr(&qmask[ui >> 5], 1u << (ui & 31));
             continue;
         }
         const int nterms = nch * 8;
@@ -413,11 +417,17 @@ __device__ __forceinline__ void full_block(const DevState& s, const Geometry& g,
             s.vir_atom_f[5 * n + gi] = 0.5f * w5;
         }
     }
-    __syncthreads();
-    const int nq = nqueued;
-    for (int k = threadIdx.x >> 5; k < nq; k += blockDim.x >> 5)
-        finish_atom_warp<SINGLE, EV, MODE>(s, g, pt, tile, stab, m, queued[k], fs2_max, out, dt, lim2_f,
-                                           wwide[threadIdx.x >> 5]);
+    // the warp's queued atoms, as soon as its own loop is done (the tile stays unchanged
+    // until the CTA ends)
+    __syncwarp();
+    for (int w = warp; w < (nown + 31) >> 5; w += nwarps) {
+        unsigned bits = qmask[w];
+        while (bits) {
+            const int ui = (w << 5) + __ffs(bits) - 1;
+            bits &= bits - 1u;
+            finish_atom_warp<SINGLE, EV, MODE>(s, g, pt, tile, stab, m, ui, fs2_max, out, dt, lim2_f, wwide[warp]);
+        }
+    }
 }
 
 template <bool SINGLE, bool EV, int MODE>
@@ -606,7 +616,7 @@ size_t force_smem_bytes(int mixed, int half, int with_energy, int tile_cap) {
     if (mixed) {
         size_t b = (size_t)tile_cap * sizeof(float4);
         if (half) b += (size_t)tile_cap * 7 * sizeof(int);
-        else b += ((size_t)tile_cap * sizeof(uint16_t) + 15) & ~(size_t)15;  // queue of own atoms
+        else b += ((size_t)(tile_cap + 31) / 32 * sizeof(unsigned) + 15) & ~(size_t)15;  // own atoms to finish
         return b;
     }
     size_t b = (size_t)tile_cap * (3 * sizeof(double) + sizeof(int));

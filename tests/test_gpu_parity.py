@@ -457,12 +457,15 @@ def test_edge_cases():
 @pytest.mark.parametrize("lst", ["full", "half"])
 def test_full_size_config2_sampled(lst):
     """80^3 fcc cells at rho*=0.8442 with liquid-like jitter, the benchmark's launch
-    configuration: pair count equals the oracle's, sampled forces match."""
+    configuration: pair count equals the oracle's, sampled forces match.  The r_list fit
+    gives 44 cells per side; the homogeneous full-list system takes 42 at its first build
+    (blocks of ~221 atoms for the 256-thread CTAs), the half list keeps the 44 its colour
+    classes need."""
     sysm = W.lj_fcc(80, seed=2, jitter=0.05)
     s = make(sysm, "mixed", lst)
     F = s.forces()
     info = s.info()
-    assert info["ncell"] == [44, 44, 44]
+    assert info["ncell"] == ([42, 42, 42] if lst == "full" else [44, 44, 44])
     n_pairs_ref = O._load().orc_neighbor_pairs(sysm.n, np.ascontiguousarray(sysm.pos).ravel(), sysm.box,
                                                RC + SKIN, 0, 0, None)
     expect = n_pairs_ref if lst == "half" else 2 * n_pairs_ref
@@ -670,6 +673,37 @@ def test_compact_grids_bit_identical():
         assert np.array_equal(x, y)
     Fref, _, _ = O.lj_forces(*b.get_state()[:1], sysm.box, O.LJParams.single())
     assert force_error(b.forces(), Fref) <= TOL["mixed"]
+
+
+def test_homogeneous_system_takes_coarser_cells(monkeypatch):
+    """A homogeneous liquid on the mixed full-list path takes cells coarser than the r_list
+    fit at its first build: 42^3 fcc cells (296,352 atoms, box 70.5 sigma) fit 24 cells per
+    side and take 22, so a block holds ~220 atoms.  Pair set bit-exact, forces against the
+    oracle, and a 20-step trajectory within 2e-5 sigma of the fit grid's (MDGB_FIT_GRID=1),
+    which differs only in the FP32 frames of its cells; FP64 and half lists keep the fit
+    grid."""
+    sysm = W.lj_fcc(42, seed=6, jitter=0.05)
+    s = make(sysm)
+    F = s.forces()
+    assert s.info()["ncell"] == [22, 22, 22]
+    assert np.array_equal(s.neighbors(), O.neighbor_pairs(sysm.pos, sysm.box, RC + SKIN))
+    Fref = O.lj_forces(sysm.pos, sysm.box, O.LJParams.single())[0]
+    assert force_error(F, Fref) <= TOL["mixed"]
+    monkeypatch.setenv("MDGB_FIT_GRID", "1")
+    f = make(sysm)
+    monkeypatch.delenv("MDGB_FIT_GRID")
+    f.forces()
+    assert f.info()["ncell"] == [24, 24, 24]
+    s.step(20)
+    f.step(20)
+    (pa, va, ia), (pb, vb, ib) = s.get_state(), f.get_state()
+    # the two runs differ only in the FP32 frames of their cells: forces by ~1e-6 of F per
+    # step, which 20 steps of the jittered lattice carry to a few 1e-6 sigma over 296,352 atoms
+    assert np.abs(pa + ia * sysm.box - (pb + ib * sysm.box)).max() < 2e-5
+    for precision, lst in (("fp64", "full"), ("mixed", "half")):
+        t = make(sysm, precision, lst)
+        t.forces()
+        assert t.info()["ncell"] == [24, 24, 24], (precision, lst)
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
