@@ -119,15 +119,16 @@ typedef struct {
  * colour classes, Sec. II.D.2 blocking).  MD_LIST_FULL needs no colour classes
  * and takes 6 cells on a side where 6 fit but the rule gives 4, so that the
  * 4x4x4-cell neighbourhood of a block is not the whole box.  At least 4 cells
- * per side.  A homogeneous system on the mixed full-list path (every block
- * occupied at its first build after md_set_state, largest tile within 1.25x
- * the mean) then takes coarser cells once, never more of them: per side the
- * smallest even count (at least 6) whose width is at most (224 / (8 rho))^(1/3),
- * rho = N / V, so that a 2x2x2-cell block holds about 224 atoms for the
- * force kernel's 256 threads (44 -> 42 cells per side for 2,048,000 atoms at
- * rho* = 0.8442).  MDGB_FIT_GRID=1 in the environment at md_create keeps the
- * first grid.  md_get_info reports the grid in use.  Allocates all device
- * workspace.
+ * per side.  A system on the mixed full-list path then takes coarser cells once,
+ * at its first build after md_set_state, never more of them: per side the
+ * smallest even count (at least 6) whose width is at most (A / (8 rho))^(1/3),
+ * so that a 2x2x2-cell block holds about A atoms for the force kernel's 256
+ * threads.  Homogeneous systems (every block occupied, largest tile within 1.25x
+ * the mean) take A = 224 and rho = N / V (44 -> 42 cells per side for
+ * 2,048,000 atoms at rho* = 0.8442); others A = 200 and rho = the density the
+ * average atom sees at the first grid (sum of squared cell counts / N / cell
+ * volume).  MDGB_FIT_GRID=1 in the environment at md_create keeps the first
+ * grid.  md_get_info reports the grid in use.  Allocates all device workspace.
  * Errors: MD_ERR_ARG, MD_ERR_BOX_TOO_SMALL, MD_ERR_CUDA.  *out is NULL on error.
  */
 int md_create(int64_t n, const double box[3], double r_cut, double skin,

@@ -321,28 +321,43 @@ int upload_centres(md_system* s) {
                : MD_ERR_CUDA;
 }
 
-// Cells coarser than the r_list fit for a homogeneous system on the mixed full-list path.
-// The force kernel runs a 2x2x2-cell block on 256 threads, one per own atom; at the fit
-// grid a block of the liquid (rho* = 0.8442, 44 cells per side at 2,048,000 atoms) holds
-// ~190 atoms and leaves two of eight warps idle until its CTA ends.  Cells of width
-// w = (224 / (8 rho))^(1/3), rho = N / V, fill a block with ~224 atoms on average (7/8 of
-// the threads, margin for density fluctuations); per side the smallest even count with at
-// most that width, never more than the fit's count nor fewer than 6 (linear block numbering
-// where not a multiple of 4: full lists need no colour classes).  Decided once, at the
-// first build, from the fit grid's binning: only when every block is occupied and the
-// largest tile is within 1.25x the mean, so that N / V is the local density (a slab or
-// particles in vacuum keep the fit grid).  Returns true when the grid changed (lists and
-// graphs then need rebuilding).
-bool regrid_homogeneous(md_system* s, int nocc, int max_tile) {
+// Cells coarser than the r_list fit on the mixed full-list path.  The force kernel runs a
+// 2x2x2-cell block on 256 threads, one per own atom; at the fit grid a block of the liquid
+// (rho* = 0.8442, 44 cells per side at 2,048,000 atoms) holds ~190 atoms and leaves two of
+// eight warps idle until its CTA ends.  Decided once, at the first build, from the fit
+// grid's binning:
+//  * homogeneous (every block occupied, largest tile within 1.25x the mean): cells of width
+//    w = (224 / (8 rho))^(1/3), rho = N / V, fill a block with ~224 atoms on average (7/8
+//    of the threads, margin for density fluctuations);
+//  * otherwise (a slab, particles in vacuum): rho is the density the average atom sees
+//    (sum of squared cell counts over N, per cell volume) and the target 200 atoms, since
+//    the largest tiles of such systems sit further above their mean (surfaces, a cold solid
+//    that contracts) and must keep the shared memory of 5 CTAs per SM.
+// Per side the smallest even count with at most that width, never more than the fit's
+// count nor fewer than 6 (linear block numbering where not a multiple of 4: full lists need
+// no colour classes).  Returns true when the grid changed (lists and graphs then need
+// rebuilding).
+bool regrid_first_build(md_system* s, int nocc, int max_tile) {
     if (s->grid_decided) return false;
     s->grid_decided = true;
     if (s->fit_grid || !mixed(s) || half(s) || s->potential != 0 || s->n == 0) return false;
     Geometry& g = s->g;
-    if (nocc < g.nblock) return false;
     const double mean_tile = 8.0 * (double)s->n / g.nblock;  // 64 of the 8 * nblock cells
-    if (max_tile > 1.25 * mean_tile + 1.0) return false;
-    const double rho = (double)s->n / (s->box[0] * s->box[1] * s->box[2]);
-    const double w_want = std::cbrt(224.0 / (8.0 * rho));
+    double rho, target;
+    if (nocc == g.nblock && max_tile <= 1.25 * mean_tile + 1.0) {
+        rho = (double)s->n / (s->box[0] * s->box[1] * s->box[2]);
+        target = 224.0;
+    } else {
+        std::vector<int32_t> cs((size_t)g.ncell + 1);
+        if (cudaMemcpy(cs.data(), s->st[0].cell_start, sizeof(int32_t) * cs.size(), cudaMemcpyDeviceToHost) !=
+            cudaSuccess)
+            return false;
+        double sq = 0.0;
+        for (int c = 0; c < g.ncell; ++c) sq += (double)(cs[c + 1] - cs[c]) * (double)(cs[c + 1] - cs[c]);
+        rho = sq / (double)s->n / (g.w[0] * g.w[1] * g.w[2]);
+        target = 200.0;
+    }
+    const double w_want = std::cbrt(target / (8.0 * rho));
     // never more cells than the fit grid: every cell and block array is sized for it
     int nc[3];
     bool change = false;
@@ -447,7 +462,7 @@ int do_build(md_system* s, int p = 0) {
             s->tile_cap = std::max(max_tile, std::min(round_up(max_tile + max_tile / tile_margin_knob() + 64, 32),
                                                       round_up((int)s->n + 1, 32)));
             s->tile_cap = std::max(s->tile_cap, s->tile_floor);
-            if (regrid_homogeneous(s, nocc, max_tile)) {
+            if (regrid_first_build(s, nocc, max_tile)) {
                 --s->n_builds;  // the fit grid's build is replaced
                 return do_build(s, p);
             }

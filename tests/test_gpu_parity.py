@@ -585,14 +585,16 @@ def test_skin_violation_is_reported(precision):
     assert ei.value.code == M.MD_ERR_SKIN_VIOLATION
 
 
-def test_redo_after_tile_growth_in_a_long_chunk():
+def test_redo_after_tile_growth_in_a_long_chunk(monkeypatch):
     """The strongly inhomogeneous workload (fcc slab plus 40 particles in vacuum, 1,192,114
-    atoms, T* = 0.3) in one 500-step call: the cold slab contracts, so a rebuild inside a
-    chunk of graph-launched steps outgrows the captured tile capacity and the chunk is redone
-    from its snapshot with grown capacities.  The redo must converge (the grown capacity is
-    kept through the rebuild of the restored state), and sampled forces at the end match
-    the oracle."""
+    atoms, T* = 0.3) in one 500-step call on the r_list fit grid (MDGB_FIT_GRID=1; the
+    coarser grid its first build would pick starts with tiles large enough that this run
+    needs no redo): the cold slab contracts, so a rebuild inside a chunk of graph-launched
+    steps outgrows the captured tile capacity and the chunk is redone from its snapshot
+    with grown capacities.  The redo must converge (the grown capacity is kept through the
+    rebuild of the restored state), and sampled forces at the end match the oracle."""
     sysm = W.slab_nanoparticles(152.0, rho=0.8442, T=0.3, seed=3)
+    monkeypatch.setenv("MDGB_FIT_GRID", "1")
     s = make(sysm)
     s.step(100)
     s.step(500)
