@@ -29,6 +29,13 @@ extern "C" {
  * MD_ERR_BOX_TOO_SMALL (-2) if < 4. */
 int mdgb_grid_shape(const double box[3], double r_list, int32_t list_kind, int32_t nc_out[3]);
 
+/* Cells on a side of length `side` in the coarser grid a mixed full-list system takes at
+ * its first build (see md_create): the smallest even count, at least 6, whose width is at
+ * most (per_block / (8 rho))^(1/3), so that a 2x2x2-cell block holds about per_block atoms
+ * at density rho; never more than fit_nc (>= 4), the count of the first grid.
+ * MD_ERR_ARG (-1) for a non-positive or non-finite side, rho or per_block, or fit_nc < 4. */
+int mdgb_coarse_cells(double side, double rho, double per_block, int32_t fit_nc, int32_t *nc_out);
+
 /* Number of 2x2x2 blocks for a grid of nc[3] cells (even, >= 4).  Grids with every
  * side a multiple of 4 number their blocks colour class by colour class; the
  * others (full lists only) number them linearly, x fastest. */

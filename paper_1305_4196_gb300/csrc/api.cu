@@ -357,14 +357,11 @@ bool regrid_first_build(md_system* s, int nocc, int max_tile) {
         rho = sq / (double)s->n / (g.w[0] * g.w[1] * g.w[2]);
         target = 200.0;
     }
-    const double w_want = std::cbrt(target / (8.0 * rho));
     // never more cells than the fit grid: every cell and block array is sized for it
     int nc[3];
     bool change = false;
     for (int d = 0; d < 3; ++d) {
-        int want = (int)std::ceil(s->box[d] / w_want);
-        want += want & 1;
-        nc[d] = std::min(g.nc[d], std::max(want, 6));
+        nc[d] = coarse_cells(s->box[d], rho, target, g.nc[d]);
         change |= nc[d] != g.nc[d];
     }
     if (!change || (int64_t)nc[0] * nc[1] * nc[2] > s->ncell_alloc) return false;

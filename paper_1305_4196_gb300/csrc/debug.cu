@@ -35,6 +35,14 @@ int mdgb_grid_shape(const double box[3], double r_list, int32_t list_kind, int32
     return MD_OK;
 }
 
+int mdgb_coarse_cells(double side, double rho, double per_block, int32_t fit_nc, int32_t* nc_out) {
+    if (!nc_out || !(side > 0.0) || !(rho > 0.0) || !(per_block > 0.0) || fit_nc < 4 || !std::isfinite(side) ||
+        !std::isfinite(rho) || !std::isfinite(per_block))
+        return MD_ERR_ARG;
+    *nc_out = coarse_cells(side, rho, per_block, fit_nc);
+    return MD_OK;
+}
+
 int mdgb_cut_band(int32_t frame, double w_max, double half_skin, int32_t R, double r_cut, double* band_out) {
     if (!band_out || !(w_max > 0.0) || !(half_skin >= 0.0) || !(r_cut > 0.0) || (frame != 0 && frame != 1) ||
         (frame == 1 && (R < 1 || R > 2)))

@@ -198,6 +198,18 @@ __host__ __device__ inline int grid_cells(int fit, bool full_list) {
     return (full_list && nc4 == 4 && fit >= 6) ? 6 : nc4;
 }
 
+// Cells per side for the coarser grid a mixed full-list system takes at its first build:
+// the smallest even count, at least 6, whose width side / count is at most
+// (per_block / (8 rho))^(1/3) - a 2x2x2-cell block then holds about per_block atoms at
+// density rho - and never more than fit_nc, the count the arrays were sized for.
+__host__ __device__ inline int coarse_cells(double side, double rho, double per_block, int fit_nc) {
+    const double w = cbrt(per_block / (8.0 * rho));
+    int want = (int)ceil(side / w);
+    want += want & 1;
+    want = want < 6 ? 6 : want;
+    return want < fit_nc ? want : fit_nc;
+}
+
 // Fill the block fields of g from its cell counts nc[3] (even, >= 4): colour-major
 // numbering when every count is a multiple of 4, else linear.
 __host__ __device__ inline void set_block_layout(Geometry& g) {

@@ -95,7 +95,38 @@ def _dbg(lib):
     L.mdgb_num_blocks.argtypes = [C.c_void_p, C.c_void_p]
     L.mdgb_block_colour.argtypes = [C.c_void_p, C.c_int32, C.c_void_p]
     L.mdgb_tile_cells.argtypes = [C.c_void_p, C.c_int32, C.c_void_p]
+    L.mdgb_coarse_cells.argtypes = [C.c_double, C.c_double, C.c_double, C.c_int32, C.c_void_p]
     return L
+
+
+@pytest.mark.parametrize("side,rho,per_block,fit,expect", [
+    (134.3677, 0.8442, 224.0, 44, 42),    # 2,048,000-atom liquid
+    (107.4942, 0.8442, 224.0, 36, 34),    # 1,048,576 atoms
+    (214.9883, 0.8442, 224.0, 76, 68),    # 8,388,608 atoms
+    (335.9193, 0.8442, 224.0, 116, 106),  # 32,000,000 atoms
+    (67.1838, 0.8442, 224.0, 20, 20),     # 256,000 atoms: the fit is already coarser
+    (151.1637, 0.864, 200.0, 52, 50),     # slab + nanoparticles, density the atoms see
+    (14.94, 1.2, 224.0, 4, 4),            # whole-box tiles stay: never more cells
+    (22.5, 0.1721, 224.0, 8, 6),          # a dilute gas: at least 6
+])
+def test_coarse_cells(lib, side, rho, per_block, fit, expect):
+    """The coarser grid of a mixed full-list system: the smallest even count (at least 6)
+    whose cells are at most (per_block / (8 rho))^(1/3) wide, never more than the fit.  The
+    expected counts are worked by hand from that definition for the benchmark workloads."""
+    L = _dbg(lib)
+    out = C.c_int32(0)
+    assert L.mdgb_coarse_cells(side, rho, per_block, fit, C.byref(out)) == 0
+    nc = out.value
+    assert nc == expect
+    w_max = (per_block / (8 * rho)) ** (1 / 3)
+    assert nc <= fit
+    if nc < fit:
+        assert nc % 2 == 0 and nc >= 6 and side / nc <= w_max
+        # the next even count down would be too coarse (or below 6)
+        assert nc == 6 or side / (nc - 2) > w_max
+    assert L.mdgb_coarse_cells(side, rho, per_block, 3, C.byref(out)) == lib.MD_ERR_ARG
+    assert L.mdgb_coarse_cells(side, 0.0, per_block, fit, C.byref(out)) == lib.MD_ERR_ARG
+    assert L.mdgb_coarse_cells(float("nan"), rho, per_block, fit, C.byref(out)) == lib.MD_ERR_ARG
 
 
 @pytest.mark.parametrize("box,rl", [((16.795962, 16.795962, 16.795962), 2.8),
