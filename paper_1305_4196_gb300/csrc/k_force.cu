@@ -469,25 +469,32 @@ __global__ void __launch_bounds__(F_THREADS) k_force_mixed_half(DevState s, Geom
     __shared__ long long wq[WQ][3];
     __shared__ int wq_u[WQ];
     __shared__ int nwq;
+    // Reaction sums only for the tile entries a half list reaches (the own cells and their
+    // forward neighbours come first in the tile, Sec. II.D.3): 6 x rcap, hx, lx, hy, ly, hz,
+    // lz, with the split's offset taken off each term; then each entry's term count in 16
+    // bits, two to a word (an entry has fewer terms than the tile has atoms, < 2^15).
+    const int rcap = half_recv_cap(tile_cap);
     float4* tile = reinterpret_cast<float4*>(smem);
-    unsigned* acc = reinterpret_cast<unsigned*>(tile + tile_cap);  // 6 x tile_cap: hx, lx, hy, ly, hz, lz
-    int* nterm = reinterpret_cast<int*>(acc + 6 * tile_cap);        // tile_cap
+    unsigned* acc = reinterpret_cast<unsigned*>(tile + tile_cap);
+    unsigned* cnt2 = acc + 6 * rcap;
     const int b = block0 + blockIdx.x;
     if (threadIdx.x == 0) nwq = 0;
     tile_meta(g, s.cell_start, b, m);
     const int T = m.prefix[64];
-    if (T + 1 > tile_cap) {
+    const int recv = m.prefix[TILE_RECV_CELLS];
+    if (T + 1 > tile_cap || recv > rcap) {
         if (threadIdx.x == 0) atomicOr(s.err, ERR_TILE_OVERFLOW);
         return;
     }
     tile_stage_f32_cells(m, s.xr, to, tile);
     stage_dummy_f32(tile, T);
-    for (int u = threadIdx.x; u <= T; u += blockDim.x) {
+    for (int u = threadIdx.x; u < recv; u += blockDim.x) {
 #pragma unroll
-        for (int c = 0; c < 6; ++c) acc[c * tile_cap + u] = 0u;
-        nterm[u] = 0;
+        for (int c = 0; c < 6; ++c) acc[c * rcap + u] = 0u;
+        if ((u & 1) == 0) cnt2[u >> 1] = 0u;
     }
     __syncthreads();
+    const unsigned magic_bits = __float_as_uint(MAGIC);
     const int blk0 = m.start[0];
     const int nown = m.prefix[8];
     const int64_t n = s.n;
@@ -543,13 +550,15 @@ __global__ void __launch_bounds__(F_THREADS) k_force_mixed_half(DevState s, Geom
                     atomicOr(s.err, ERR_NONFINITE);
                 }
             }
-            atomicAdd(&acc[0 * tile_cap + u], bx.hi);
-            atomicAdd(&acc[1 * tile_cap + u], bx.lo);
-            atomicAdd(&acc[2 * tile_cap + u], by.hi);
-            atomicAdd(&acc[3 * tile_cap + u], by.lo);
-            atomicAdd(&acc[4 * tile_cap + u], bz.hi);
-            atomicAdd(&acc[5 * tile_cap + u], bz.lo);
-            atomicAdd(&nterm[u], 1);
+            if (u < recv) {  // else the padding's dummy slot: a zero term
+                atomicAdd(&acc[0 * rcap + u], bx.hi - magic_bits);
+                atomicAdd(&acc[1 * rcap + u], bx.lo - magic_bits);
+                atomicAdd(&acc[2 * rcap + u], by.hi - magic_bits);
+                atomicAdd(&acc[3 * rcap + u], by.lo - magic_bits);
+                atomicAdd(&acc[4 * rcap + u], bz.hi - magic_bits);
+                atomicAdd(&acc[5 * rcap + u], bz.lo - magic_bits);
+                atomicAdd(&cnt2[u >> 1], 1u << ((u & 1) << 4));
+            }
             if (EV) {
                 const float c4 = SINGLE ? pt.c4_f[0] : pt.c4_f[t];
                 const float fs = fs2 * (1.0f / FS_SCALE);
@@ -562,14 +571,15 @@ __global__ void __launch_bounds__(F_THREADS) k_force_mixed_half(DevState s, Geom
                 w5 = fmaf(dy, fs * dz, w5);
             }
         })
-        // own atom's part goes through the same tile accumulator
-        atomicAdd(&acc[0 * tile_cap + ui], ax.hi);
-        atomicAdd(&acc[1 * tile_cap + ui], ax.lo);
-        atomicAdd(&acc[2 * tile_cap + ui], ay.hi);
-        atomicAdd(&acc[3 * tile_cap + ui], ay.lo);
-        atomicAdd(&acc[4 * tile_cap + ui], az.hi);
-        atomicAdd(&acc[5 * tile_cap + ui], az.lo);
-        atomicAdd(&nterm[ui], nch * 8);
+        // own atom's part goes through the same tile accumulator, its nch * 8 offsets removed
+        const unsigned bias = (unsigned)(nch * 8) * magic_bits;
+        atomicAdd(&acc[0 * rcap + ui], ax.hi - bias);
+        atomicAdd(&acc[1 * rcap + ui], ax.lo - bias);
+        atomicAdd(&acc[2 * rcap + ui], ay.hi - bias);
+        atomicAdd(&acc[3 * rcap + ui], ay.lo - bias);
+        atomicAdd(&acc[4 * rcap + ui], az.hi - bias);
+        atomicAdd(&acc[5 * rcap + ui], az.lo - bias);
+        atomicAdd(&cnt2[ui >> 1], (unsigned)(nch * 8) << ((ui & 1) << 4));
         if (EV) {
             s.pe_atom_f[gi] = pe;
             s.vir_atom_f[gi] = w0;
@@ -582,20 +592,20 @@ __global__ void __launch_bounds__(F_THREADS) k_force_mixed_half(DevState s, Geom
     }
     __syncthreads();
     // add the tile back: this CTA is the only one of its colour touching these atoms
-    for (int u = threadIdx.x; u < T; u += blockDim.x) {
-        const int nt = nterm[u];
+    for (int u = threadIdx.x; u < recv; u += blockDim.x) {
+        const unsigned nt = (cnt2[u >> 1] >> ((u & 1) << 4)) & 0xffffu;
         if (nt == 0) continue;
         // each term's high part is below 2^22 in magnitude: more than FIX_SPLIT_MAX_TERMS
         // terms on one atom (densities several times a liquid's) could wrap the 32-bit sum
         if (nt > FIX_SPLIT_MAX_TERMS) atomicOr(s.err, ERR_NONFINITE);
         const int slot = tile_slot_of(m, u);
         const int gj = m.start[slot] + (u - m.prefix[slot]);
-        FixAcc fx{acc[0 * tile_cap + u], acc[1 * tile_cap + u]};
-        FixAcc fy{acc[2 * tile_cap + u], acc[3 * tile_cap + u]};
-        FixAcc fz{acc[4 * tile_cap + u], acc[5 * tile_cap + u]};
-        s.fq[gj] += fix_final(fx, nt);
-        s.fq[n + gj] += fix_final(fy, nt);
-        s.fq[2 * n + gj] += fix_final(fz, nt);
+        FixAcc fx{acc[0 * rcap + u], acc[1 * rcap + u]};
+        FixAcc fy{acc[2 * rcap + u], acc[3 * rcap + u]};
+        FixAcc fz{acc[4 * rcap + u], acc[5 * rcap + u]};
+        s.fq[gj] += fix_final(fx, 0);
+        s.fq[n + gj] += fix_final(fy, 0);
+        s.fq[2 * n + gj] += fix_final(fz, 0);
     }
     __syncthreads();
     if (threadIdx.x == 0) {  // the queued large terms, exact in 64 bits
@@ -615,7 +625,10 @@ size_t force_smem_bytes(int mixed, int half, int with_energy, int tile_cap) {
     (void)with_energy;
     if (mixed) {
         size_t b = (size_t)tile_cap * sizeof(float4);
-        if (half) b += (size_t)tile_cap * 7 * sizeof(int);
+        if (half) {  // reaction sums and 16-bit term counts of the entries a half list reaches
+            const size_t r = (size_t)half_recv_cap(tile_cap);
+            b += r * 6 * sizeof(unsigned) + (((r + 1) / 2 * sizeof(unsigned) + 15) & ~(size_t)15);
+        }
         else b += ((size_t)(tile_cap + 31) / 32 * sizeof(unsigned) + 15) & ~(size_t)15;  // own atoms to finish
         return b;
     }

@@ -38,8 +38,11 @@ __device__ __forceinline__ void build_block(const DevState& s, const Geometry& g
 
     tile_meta(g, s.cell_start, b, m);
     const int T = m.prefix[64];
-    if (threadIdx.x == 0) atomicMax(&s.stats[1], T + 1);
-    if (T + 1 > tile_cap) {
+    // the tile capacity this block needs: its atoms and the dummy slot, and for half lists
+    // also room for the mixed kernel's reaction sums over the cells a half list reaches
+    const int need = HALF ? max(T + 1, tile_cap_for_recv(m.prefix[TILE_RECV_CELLS])) : T + 1;
+    if (threadIdx.x == 0) atomicMax(&s.stats[1], need);
+    if (need > tile_cap) {
         if (threadIdx.x == 0) atomicOr(s.err, ERR_TILE_OVERFLOW);
         return;
     }

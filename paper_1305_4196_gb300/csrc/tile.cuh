@@ -24,18 +24,50 @@ struct TileTables {
     int8_t coord_of_idx[64];  // tile slot -> tile coordinate
 };
 
+// Tile cell (x, y, z) (0..3 each; the block's own cells are 1..2) is a Newton-3 half-shell
+// target of some own cell: the cell itself, or a forward neighbour (dz > 0; dz = 0 and
+// dy > 0; dz = dy = 0 and dx > 0; Sec. II.D.3).  Half-list reactions only reach these.
+__host__ __device__ constexpr bool tile_receives(int x, int y, int z) {
+    for (int oz = 1; oz <= 2; ++oz)
+        for (int oy = 1; oy <= 2; ++oy)
+            for (int ox = 1; ox <= 2; ++ox) {
+                const int dx = x - ox, dy = y - oy, dz = z - oz;
+                if (dx < -1 || dx > 1 || dy < -1 || dy > 1 || dz < -1 || dz > 1) continue;
+                if (dz > 0 || (dz == 0 && (dy > 0 || (dy == 0 && dx >= 0)))) return true;
+            }
+    return false;
+}
+
+// Slots: the 8 own cells first, then the other cells a half list reaches, then the rest.
+// So the own atoms are tile entries 0 .. prefix[8] - 1 and every half-list target lies in
+// entries 0 .. prefix[TILE_RECV_CELLS] - 1.
+constexpr int TILE_RECV_CELLS = 43;
+
 __host__ __device__ constexpr TileTables make_tile_tables() {
     TileTables t{};
-    int k = 8;
+    int k = 8, r = TILE_RECV_CELLS;
     for (int c = 0; c < 64; ++c) {
         int x = c & 3, y = (c >> 2) & 3, z = c >> 4;
         bool own = x >= 1 && x <= 2 && y >= 1 && y <= 2 && z >= 1 && z <= 2;
-        int i = own ? (x - 1) + 2 * (y - 1) + 4 * (z - 1) : k++;
+        int i = own ? (x - 1) + 2 * (y - 1) + 4 * (z - 1) : (tile_receives(x, y, z) ? k++ : r++);
         t.idx_of_coord[c] = (int8_t)i;
         t.coord_of_idx[i] = (int8_t)c;
     }
     return t;
 }
+
+__host__ __device__ constexpr int count_tile_receivers() {
+    int k = 0;
+    for (int c = 0; c < 64; ++c) k += tile_receives(c & 3, (c >> 2) & 3, c >> 4) ? 1 : 0;
+    return k;
+}
+static_assert(count_tile_receivers() == TILE_RECV_CELLS, "half-shell targets of a 2x2x2 block");
+
+// Entries of the reaction sums a mixed half-list CTA keeps for a tile capacity: 11/16 of
+// it (the 43 of 64 cells a half list reaches hold about 2/3 of a tile's atoms), and the
+// smallest tile capacity whose share holds `recv` entries.
+__host__ __device__ inline int half_recv_cap(int tile_cap) { return ((tile_cap * 11 + 15) / 16 + 31) & ~31; }
+__host__ __device__ inline int tile_cap_for_recv(int recv) { return (recv * 16 + 10) / 11; }
 
 static __constant__ TileTables c_tiles = make_tile_tables();
 
