@@ -335,12 +335,13 @@ int upload_centres(md_system* s) {
 //    that contracts) and must keep the shared memory of 5 CTAs per SM.
 // Per side the smallest even count with at most that width, never more than the fit's
 // count nor fewer than 6 (linear block numbering where not a multiple of 4: full lists need
-// no colour classes).  Returns true when the grid changed (lists and graphs then need
-// rebuilding).
-bool regrid_first_build(md_system* s, int nocc, int max_tile) {
-    if (s->grid_decided) return false;
+// no colour classes).  *changed tells whether the grid changed (lists and graphs then need
+// rebuilding); MD_ERR_CUDA if the new cell centres could not be copied to the device.
+int regrid_first_build(md_system* s, int nocc, int max_tile, bool* changed) {
+    *changed = false;
+    if (s->grid_decided) return MD_OK;
     s->grid_decided = true;
-    if (s->fit_grid || !mixed(s) || half(s) || s->potential != 0 || s->n == 0) return false;
+    if (s->fit_grid || !mixed(s) || half(s) || s->potential != 0 || s->n == 0) return MD_OK;
     Geometry& g = s->g;
     const double mean_tile = 8.0 * (double)s->n / g.nblock;  // 64 of the 8 * nblock cells
     double rho, target;
@@ -351,7 +352,7 @@ bool regrid_first_build(md_system* s, int nocc, int max_tile) {
         std::vector<int32_t> cs((size_t)g.ncell + 1);
         if (cudaMemcpy(cs.data(), s->st[0].cell_start, sizeof(int32_t) * cs.size(), cudaMemcpyDeviceToHost) !=
             cudaSuccess)
-            return false;
+            return fail(s, MD_ERR_CUDA, "reading the cell counts for the grid choice failed");
         double sq = 0.0;
         for (int c = 0; c < g.ncell; ++c) sq += (double)(cs[c + 1] - cs[c]) * (double)(cs[c + 1] - cs[c]);
         rho = sq / (double)s->n / (g.w[0] * g.w[1] * g.w[2]);
@@ -364,7 +365,7 @@ bool regrid_first_build(md_system* s, int nocc, int max_tile) {
         nc[d] = coarse_cells(s->box[d], rho, target, g.nc[d]);
         change |= nc[d] != g.nc[d];
     }
-    if (!change || (int64_t)nc[0] * nc[1] * nc[2] > s->ncell_alloc) return false;
+    if (!change || (int64_t)nc[0] * nc[1] * nc[2] > s->ncell_alloc) return MD_OK;
     for (int d = 0; d < 3; ++d) {
         g.nc[d] = nc[d];
         g.w[d] = s->box[d] / nc[d];
@@ -373,11 +374,12 @@ bool regrid_first_build(md_system* s, int nocc, int max_tile) {
     }
     set_block_layout(g);
     set_cut_band(s);
-    if (upload_centres(s) != MD_OK) return false;
     s->graphs_valid = false;
     s->lists_valid = false;
     s->forces_valid = false;
-    return true;
+    *changed = true;
+    if (upload_centres(s) != MD_OK) return fail(s, MD_ERR_CUDA, "copying the cell centres of the new grid failed");
+    return MD_OK;
 }
 
 int do_build(md_system* s, int p = 0) {
@@ -459,7 +461,9 @@ int do_build(md_system* s, int p = 0) {
             s->tile_cap = std::max(max_tile, std::min(round_up(max_tile + max_tile / tile_margin_knob() + 64, 32),
                                                       round_up((int)s->n + 1, 32)));
             s->tile_cap = std::max(s->tile_cap, s->tile_floor);
-            if (regrid_first_build(s, nocc, max_tile)) {
+            bool changed = false;
+            if ((rc = regrid_first_build(s, nocc, max_tile, &changed))) return rc;
+            if (changed) {
                 --s->n_builds;  // the fit grid's build is replaced
                 return do_build(s, p);
             }
