@@ -708,6 +708,31 @@ def test_homogeneous_system_takes_coarser_cells(monkeypatch):
         assert t.info()["ncell"] == [24, 24, 24], (precision, lst)
 
 
+def test_inhomogeneous_system_takes_coarser_cells(monkeypatch):
+    """An fcc slab with 10 nanoparticles in vacuum (190,154 atoms, box 90.7 sigma, most
+    blocks empty) on the mixed full-list path: the fit grid has 32 cells per side, and the
+    first build takes 30 from the density its atoms see (200 atoms per block), running the
+    compact kernels over the occupied blocks of a linearly numbered grid.  Pair set
+    bit-exact, forces against the oracle, and a 20-step trajectory within 2e-5 sigma of the
+    fit grid's (MDGB_FIT_GRID=1)."""
+    sysm = W.slab_nanoparticles(L=91.0, n_particles=10, r_min=3.0, r_max=6.0, seed=5)
+    s = make(sysm)
+    F = s.forces()
+    assert s.info()["ncell"] == [30, 30, 30]
+    assert np.array_equal(s.neighbors(), O.neighbor_pairs(sysm.pos, sysm.box, RC + SKIN))
+    Fref = O.lj_forces(sysm.pos, sysm.box, O.LJParams.single())[0]
+    assert force_error(F, Fref) <= TOL["mixed"]
+    monkeypatch.setenv("MDGB_FIT_GRID", "1")
+    f = make(sysm)
+    monkeypatch.delenv("MDGB_FIT_GRID")
+    f.forces()
+    assert f.info()["ncell"] == [32, 32, 32]
+    s.step(20)
+    f.step(20)
+    (pa, _, ia), (pb, _, ib) = s.get_state(), f.get_state()
+    assert np.abs(pa + ia * sysm.box - (pb + ib * sysm.box)).max() < 2e-5
+
+
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_small_box_full_list_even_cell_count(precision):
     """Sec. II.A: full lists need no colour classes and take 6 cells per side where 6 fit and
