@@ -146,3 +146,25 @@ def test_full_size_bulk_copper():
     assert force_error(F, Fref) <= 2e-5
     pe, _, _ = s.energy_virial()
     assert abs(pe - E_ref) <= 1e-6 * abs(E_ref)
+
+
+def test_on_a_coarser_linear_grid():
+    """The two TB-SMA passes on the coarser, linearly numbered grid a pair-potential system
+    takes at its first build: a 296,352-atom LJ-unit liquid (42^3 fcc cells at rho* = 0.8442,
+    22 instead of 24 cells per side), switched to a TB-SMA parameter set in the same units
+    (A = 0.1, xi = 1, p = 10, q = 2.5, r0 = 1.12, r_cut = 2.5).  Forces, energy and virial
+    against the oracle at the mixed bars."""
+    sysm = W.lj_fcc(42, seed=6, jitter=0.05)
+    s = M.System(sysm.n, sysm.box, r_cut=2.5, skin=0.3, precision=M.MD_MIXED)
+    s.set_state(sysm.pos, sysm.vel, sysm.species)
+    s.forces()
+    assert s.info()["ncell"] == [22, 22, 22]
+    P = O.TBSMAParams(0.1, 1.0, 10.0, 2.5, 1.12, 2.5)
+    s.set_tbsma(P.A, P.xi, P.p, P.q, P.r0, P.rc)
+    F = s.forces()
+    Fref, E_ref, vir_ref = O.tbsma_forces(sysm.pos, sysm.box, P)
+    assert force_error(F, Fref) <= 2e-5
+    pe, _, vir = s.energy_virial()
+    assert abs(pe - E_ref) <= 1e-6 * abs(E_ref)
+    assert np.abs(vir - vir_ref).max() <= 1e-6 * np.abs(vir_ref[:3]).max()
+
