@@ -223,3 +223,24 @@ def test_backward_at_the_force_matching_size(precision):
     F = sysm.forces()
     Fref = O.lj_forces(s.pos, s.box, P, sp)[0]
     assert vec_error(F, Fref) <= (1e-12 if precision == "fp64" else 2e-5)
+
+
+def test_backward_on_the_coarser_grid():
+    """The mixed backward pass on the coarser, linearly numbered grid a homogeneous system
+    takes at its first build: a 296,352-atom liquid (42^3 fcc cells at rho* = 0.8442, 22
+    instead of 24 cells per side); dL/dx element by element against the oracle, and
+    dL/deps, dL/dsigma to the per-term bar (2e-5 of the sum of |term|)."""
+    w = W.lj_fcc(42, seed=6, jitter=0.05)
+    sysm = M.System(w.n, w.box, r_cut=2.5, skin=0.3, precision=M.MD_MIXED)
+    sysm.set_state(w.pos, w.vel, w.species)
+    sysm.forces()
+    assert sysm.info()["ncell"] == [22, 22, 22]
+    P = O.LJParams.single()
+    G = np.random.default_rng(3).normal(size=(w.n, 3))
+    gx, ge, gs = sysm.forces_backward(G)
+    gx_ref, ge_ref, gs_ref = O.lj_force_grad(w.pos, w.box, P, G, w.species)
+    ae, as_ = O.lj_force_grad_scale(w.pos, w.box, P, G, w.species)
+    assert vec_error(gx, gx_ref) <= TOL["mixed"]
+    for t, tref, scale in [(ge, ge_ref, ae), (gs, gs_ref, as_)]:
+        assert np.all(np.abs(t - tref) <= TOL["mixed"] * scale)
+
