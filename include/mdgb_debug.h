@@ -45,8 +45,9 @@ int mdgb_num_blocks(const int32_t nc[3], int32_t *nblock_out);
  * multiple of 4). */
 int mdgb_block_colour(const int32_t nc[3], int32_t block, int32_t *colour_out);
 
-/* The 64 cells of block `block`'s tile in tile order (own 8 cells first), as
- * linear cell indices cx + nc[0]*(cy + nc[1]*cz). */
+/* The 64 cells of block `block`'s tile in tile order (own 8 cells first, then the
+ * other 35 cells a Newton-3 half list of the own cells reaches, then the remaining 21),
+ * as linear cell indices cx + nc[0]*(cy + nc[1]*cz). */
 int mdgb_tile_cells(const int32_t nc[3], int32_t block, int32_t cells_out[64]);
 
 /* The mixed path's FP64 decision band around r_cut^2: pairs whose FP32 r^2 lies

@@ -157,6 +157,33 @@ def test_grid_shape(lib, box, rl):
     assert L.mdgb_grid_shape(np.array(box).ctypes.data, rl, 7, nc.ctypes.data) == lib.MD_ERR_ARG
 
 
+@pytest.mark.parametrize("nc", [(8, 8, 8), (6, 6, 6), (12, 10, 14)])
+def test_tile_order_puts_half_shell_targets_first(lib, nc):
+    """Sec. II.D.3: a half list of an own cell holds the cell itself and its 13 forward
+    neighbours (dz > 0; dz = 0, dy > 0; dz = dy = 0, dx > 0).  The tile lists the 8 own
+    cells first and then every other cell such a list reaches, so that the half-list
+    kernel's reaction sums cover tile slots 0..42 only; the 21 cells after them are
+    reached by no half list of the block (checked by brute force over the offsets)."""
+    L = _dbg(lib)
+    ncv = np.array(nc, dtype=np.int32)
+    nb = np.zeros(1, dtype=np.int32)
+    assert L.mdgb_num_blocks(ncv.ctypes.data, nb.ctypes.data) == 0
+    buf = np.zeros(64, dtype=np.int32)
+    fwd = [(dx, dy, dz) for dz in (-1, 0, 1) for dy in (-1, 0, 1) for dx in (-1, 0, 1)
+           if dz > 0 or (dz == 0 and (dy > 0 or (dy == 0 and dx >= 0)))]
+    assert len(fwd) == 14
+    for b in sorted({0, int(nb[0]) // 2, int(nb[0]) - 1}):
+        assert L.mdgb_tile_cells(ncv.ctypes.data, b, buf.ctypes.data) == 0
+        cells = buf.tolist()
+        coords = [(c % nc[0], (c // nc[0]) % nc[1], c // (nc[0] * nc[1])) for c in cells]
+        reached = set()
+        for (x, y, z) in coords[:8]:
+            for dx, dy, dz in fwd:
+                reached.add(((x + dx) % nc[0]) + nc[0] * (((y + dy) % nc[1]) + nc[1] * ((z + dz) % nc[2])))
+        assert set(cells[:43]) == reached
+        assert not reached & set(cells[43:])
+
+
 @pytest.mark.parametrize("nc", [(4, 4, 4), (8, 12, 16), (44, 44, 44)])
 def test_colour_schedule_tiles_disjoint(lib, nc):
     """Sec. II.A/II.B: tasks in one wave must not overlap.  Every block's 4x4x4 tile
