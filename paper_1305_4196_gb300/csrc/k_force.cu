@@ -471,14 +471,18 @@ __global__ void __launch_bounds__(F_THREADS) k_force_mixed_half(DevState s, Geom
     __shared__ int nwq;
     // Reaction sums only for the tile entries a half list reaches (the own cells and their
     // forward neighbours come first in the tile, Sec. II.D.3): 6 x rcap, hx, lx, hy, ly, hz,
-    // lz, with the split's offset taken off each term; then each entry's term count in 16
-    // bits, two to a word (an entry has fewer terms than the tile has atoms, < 2^15).
+    // lz, with the split's offset taken off each term; then, where a block needs them,
+    // each entry's term count in 16 bits, two to a word (fewer than the tile's atoms, < 2^15).
     const int rcap = half_recv_cap(tile_cap);
     float4* tile = reinterpret_cast<float4*>(smem);
     unsigned* acc = reinterpret_cast<unsigned*>(tile + tile_cap);
     unsigned* cnt2 = acc + 6 * rcap;
+    __shared__ int max_nch;  // the longest own list, in chunks
     const int b = block0 + blockIdx.x;
-    if (threadIdx.x == 0) nwq = 0;
+    if (threadIdx.x == 0) {
+        nwq = 0;
+        max_nch = 0;
+    }
     tile_meta(g, s.cell_start, b, m);
     const int T = m.prefix[64];
     const int recv = m.prefix[TILE_RECV_CELLS];
@@ -486,6 +490,8 @@ __global__ void __launch_bounds__(F_THREADS) k_force_mixed_half(DevState s, Geom
         if (threadIdx.x == 0) atomicOr(s.err, ERR_TILE_OVERFLOW);
         return;
     }
+    for (int ui = threadIdx.x; ui < m.prefix[8]; ui += blockDim.x)
+        atomicMax(&max_nch, (s.nl_cnt[m.start[0] + ui] + 7) >> 3);
     tile_stage_f32_cells(m, s.xr, to, tile);
     stage_dummy_f32(tile, T);
     for (int u = threadIdx.x; u < recv; u += blockDim.x) {
@@ -499,6 +505,11 @@ __global__ void __launch_bounds__(F_THREADS) k_force_mixed_half(DevState s, Geom
     const int nown = m.prefix[8];
     const int64_t n = s.n;
     const int np = s.np;
+    // Each term's high part is below 2^22 in magnitude, so a 32-bit sum stays exact up to
+    // FIX_SPLIT_MAX_TERMS terms.  An entry takes at most its own list's terms (own atoms)
+    // and one reaction per own atom, so the counts are only kept for blocks where that
+    // bound exceeds the limit (small boxes with whole-box tiles, high densities)
+    const bool count = nown + 8 * max_nch > FIX_SPLIT_MAX_TERMS;
     for (int ui = threadIdx.x; ui < nown; ui += blockDim.x) {
         const int gi = blk0 + ui;
         const float4 pi = tile[ui];
@@ -557,7 +568,7 @@ __global__ void __launch_bounds__(F_THREADS) k_force_mixed_half(DevState s, Geom
                 atomicAdd(&acc[3 * rcap + u], by.lo - magic_bits);
                 atomicAdd(&acc[4 * rcap + u], bz.hi - magic_bits);
                 atomicAdd(&acc[5 * rcap + u], bz.lo - magic_bits);
-                atomicAdd(&cnt2[u >> 1], 1u << ((u & 1) << 4));
+                if (count) atomicAdd(&cnt2[u >> 1], 1u << ((u & 1) << 4));
             }
             if (EV) {
                 const float c4 = SINGLE ? pt.c4_f[0] : pt.c4_f[t];
@@ -579,7 +590,7 @@ __global__ void __launch_bounds__(F_THREADS) k_force_mixed_half(DevState s, Geom
         atomicAdd(&acc[3 * rcap + ui], ay.lo - bias);
         atomicAdd(&acc[4 * rcap + ui], az.hi - bias);
         atomicAdd(&acc[5 * rcap + ui], az.lo - bias);
-        atomicAdd(&cnt2[ui >> 1], (unsigned)(nch * 8) << ((ui & 1) << 4));
+        if (count) atomicAdd(&cnt2[ui >> 1], (unsigned)(nch * 8) << ((ui & 1) << 4));
         if (EV) {
             s.pe_atom_f[gi] = pe;
             s.vir_atom_f[gi] = w0;
@@ -593,11 +604,12 @@ __global__ void __launch_bounds__(F_THREADS) k_force_mixed_half(DevState s, Geom
     __syncthreads();
     // add the tile back: this CTA is the only one of its colour touching these atoms
     for (int u = threadIdx.x; u < recv; u += blockDim.x) {
-        const unsigned nt = (cnt2[u >> 1] >> ((u & 1) << 4)) & 0xffffu;
-        if (nt == 0) continue;
-        // each term's high part is below 2^22 in magnitude: more than FIX_SPLIT_MAX_TERMS
-        // terms on one atom (densities several times a liquid's) could wrap the 32-bit sum
-        if (nt > FIX_SPLIT_MAX_TERMS) atomicOr(s.err, ERR_NONFINITE);
+        if (count) {
+            const unsigned nt = (cnt2[u >> 1] >> ((u & 1) << 4)) & 0xffffu;
+            if (nt == 0) continue;
+            // more than FIX_SPLIT_MAX_TERMS terms on one atom could wrap its 32-bit sums
+            if (nt > FIX_SPLIT_MAX_TERMS) atomicOr(s.err, ERR_NONFINITE);
+        }
         const int slot = tile_slot_of(m, u);
         const int gj = m.start[slot] + (u - m.prefix[slot]);
         FixAcc fx{acc[0 * rcap + u], acc[1 * rcap + u]};
