@@ -79,8 +79,8 @@ struct md_system {
     bool snapshot_first = true;
     int compact = 0;          // grid of the occupied-block loops of a mostly empty system (see do_build)
     bool no_compact = false;  // MDGB_NO_COMPACT=1 at md_create: one CTA per block always
-    // the cell grid of a homogeneous mixed-precision full-list system is chosen once, at its
-    // first build (see regrid_homogeneous); MDGB_FIT_GRID=1 at md_create keeps the r_list fit
+    // the cell grid of a mixed-precision full-list system is chosen once, at its first build
+    // (regrid_first_build); MDGB_FIT_GRID=1 at md_create keeps the r_list fit
     bool grid_decided = false;
     bool fit_grid = false;
     int64_t ncell_alloc = 0;  // cells (and 1/8 as many blocks) the cell and block arrays hold
@@ -298,10 +298,6 @@ int do_bin(md_system* s, int p = 0) {
 }
 
 // ---- list build with capacity regrowth (host-visible: reads the device counters)
-static int tile_margin_knob() {
-    static int v = getenv("MDGB_TILE_MARGIN") ? atoi(getenv("MDGB_TILE_MARGIN")) : 4;
-    return v;
-}
 void set_cut_band(md_system* s);
 
 // Cell centres (c + 1/2) w in the kernels' cell numbering, for the current grid.
@@ -416,7 +412,7 @@ int do_build(md_system* s, int p = 0) {
         bool again = false;
         if (e & ERR_TILE_OVERFLOW) {
             // a tile never holds more than all atoms plus the dummy slot
-            int cap = std::max(max_tile, std::min(round_up(max_tile + max_tile / tile_margin_knob() + 64, 32),
+            int cap = std::max(max_tile, std::min(round_up(max_tile + max_tile / 4 + 64, 32),
                                                   round_up((int)s->n + 1, 32)));
             if (cap > 32767) return fail(s, MD_ERR_CELL_OVERFLOW, "tile of %d atoms exceeds 15-bit indices", max_tile);
             s->tile_cap = cap;
@@ -458,7 +454,7 @@ int do_build(md_system* s, int p = 0) {
             // keep the tile capacity close to the need (max_tile counts the dummy slot) so
             // that more CTAs fit per SM and every shared-memory layout stays within limits
             // (25 % headroom: later rebuilds inside graph-launched steps reuse this capacity)
-            s->tile_cap = std::max(max_tile, std::min(round_up(max_tile + max_tile / tile_margin_knob() + 64, 32),
+            s->tile_cap = std::max(max_tile, std::min(round_up(max_tile + max_tile / 4 + 64, 32),
                                                       round_up((int)s->n + 1, 32)));
             s->tile_cap = std::max(s->tile_cap, s->tile_floor);
             bool changed = false;
@@ -1096,11 +1092,7 @@ int md_create(int64_t n, const double box[3], double r_cut, double skin, const m
         if (!(box[d] > 0.0) || !std::isfinite(box[d])) return bail(MD_ERR_ARG);
         s->box[d] = box[d];
         const int fit = (int)std::min(std::floor(box[d] / (s->rl * (1.0 + 1e-12))), 1024.0);
-        int nc = grid_cells(fit, s->list_kind == MD_LIST_FULL);
-        if (getenv("MDGB_NC") && s->list_kind == MD_LIST_FULL) {
-            const int want = atoi(getenv("MDGB_NC"));
-            if (want >= 6 && want % 2 == 0 && want <= fit) nc = want;
-        }
+        const int nc = grid_cells(fit, s->list_kind == MD_LIST_FULL);
         if (nc < 4) {
             fail(s, MD_ERR_BOX_TOO_SMALL, "box side %g < 4 r_list", box[d]);
             return bail(MD_ERR_BOX_TOO_SMALL);
