@@ -119,8 +119,8 @@ typedef struct {
  * colour classes, Sec. II.D.2 blocking).  MD_LIST_FULL needs no colour classes
  * and takes 6 cells on a side where 6 fit but the rule gives 4, so that the
  * 4x4x4-cell neighbourhood of a block is not the whole box.  At least 4 cells
- * per side.  A system on the mixed full-list path then takes coarser cells once,
- * at its first build after md_set_state, never more of them: per side the
+ * per side.  A Lennard-Jones system on the mixed full-list path then takes coarser
+ * cells once, at its first build after md_set_state, never more of them: per side the
  * smallest even count (at least 6) whose width is at most (A / (8 rho))^(1/3),
  * so that a 2x2x2-cell block holds about A atoms for the force kernel's 256
  * threads.  Homogeneous systems (every block occupied, largest tile within 1.25x
