@@ -344,7 +344,8 @@ def run_ours(args):
                 else None,
                 "traffic_note": "ncu dram read+write of a 1,048,576-atom launch scaled by atoms",
                 "algorithmic_bytes": abytes, "avg_launch_ms": f_ms, "launches_timed": info1["timed_force_evals"],
-                "force_share_of_step": info1["force_ms"] / ms}
+                "launches": info1["force_evals"] - info0["force_evals"],
+                "force_share_of_step": f_ms * (info1["force_evals"] - info0["force_evals"]) / ms}
 
     # the force kernel alone (md_forces: no integration), against the force-only cost model
     s.set_timing(True)

@@ -172,8 +172,8 @@ int md_forces(md_system *s, double *f_out, int device_ptrs);
  * Integrate n_steps velocity-Verlet steps: v += dt F/(2m); x += dt v;
  * rebuild lists if the policy says so; F = F(x); v += dt F/(2m).
  * Steps run as CUDA-graph launches (the rebuild decision taken on the device in a
- * conditional node per step; one step per graph while md_set_timing is on, else
- * graphs of 8 steps where possible); the host reads the device status once per
+ * conditional node per step; graphs of 8 steps where possible, else one step per
+ * graph); the host reads the device status once per
  * chunk of up to 200 steps.  If a rebuild inside a chunk outgrows the
  * list or tile capacity, the chunk is redone from a snapshot of its starting
  * state after the capacities have been regrown (md_info.n_redos counts these).
@@ -285,9 +285,12 @@ int md_get_info(md_system *s, md_info *out);
 
 /*
  * Turn per-phase device timing on (enable != 0) or off.  While on, the
- * library brackets every force evaluation and every binning + list build with
- * CUDA events on its stream and adds their elapsed times to md_info.force_ms
- * and md_info.build_ms (the counters restart when timing is switched on).
+ * library brackets force evaluations and every binning + list build with CUDA
+ * events on its stream and adds their elapsed times to md_info.force_ms and
+ * md_info.build_ms; md_info.timed_force_evals and timed_builds count the
+ * bracketed ones (the counters restart when timing is switched on).  In md_step's
+ * 8-step graphs only the first step's force kernel is bracketed, so that the
+ * events barely slow the steps they measure; every other force evaluation is.
  */
 int md_set_timing(md_system *s, int enable);
 
