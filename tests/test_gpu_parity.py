@@ -733,6 +733,25 @@ def test_inhomogeneous_system_takes_coarser_cells(monkeypatch):
     assert np.abs(pa + ia * sysm.box - (pb + ib * sysm.box)).max() < 2e-5
 
 
+def test_timing_brackets_one_force_launch_per_step_graph():
+    """md_set_timing on the fused path: in the 8-step graphs only the first step's force
+    kernel is bracketed by events, every singly launched step is too, and
+    timed_force_evals counts exactly the bracketed launches (100 steps: 12 graphs of 8 and
+    4 single steps, 16 timed), so force_ms / timed_force_evals is a mean launch time."""
+    sysm = liquid(14)
+    s = make(sysm)
+    s.forces()
+    s.set_timing(True)
+    i0 = s.info()
+    s.step(100)
+    i1 = s.info()
+    s.set_timing(False)
+    assert i1["force_evals"] - i0["force_evals"] == 100
+    timed = i1["timed_force_evals"] - i0["timed_force_evals"]
+    assert 0 < timed < 100
+    assert i1["force_ms"] > 0.0
+
+
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_small_box_full_list_even_cell_count(precision):
     """Sec. II.A: full lists need no colour classes and take 6 cells per side where 6 fit and
