@@ -439,7 +439,7 @@ def comparisons(args, sysm, M, stream, value, list_len_hom, hom=None):
         s.set_state(inh.pos, inh.vel, inh.species)
         s.forces()
         torch.cuda.synchronize()
-        s.set_timing(True)  # as in the homogeneous run: events around every force launch
+        s.set_timing(True)  # as in the homogeneous run: events around one force launch per graph
         info0 = s.info()
         steps_inh = 500
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
