@@ -63,8 +63,10 @@ class Batch:
         self.__del__()
 
     def set_state(self, pos, vel, species=None):
-        (pp, dev), (vp, _), (sp, _) = _m._ptr(pos), _m._ptr(vel), _m._ptr(species)
-        self._check(_lib.md_batch_set_state(self.handle, pp, vp, sp, int(bool(dev))))
+        args = (_m._ptr(pos, np.float64, 3 * self.ntot, "pos"), _m._ptr(vel, np.float64, 3 * self.ntot, "vel"),
+                _m._ptr(species, np.int32, self.ntot, "species"))
+        dev = _m._same_side(*args)
+        self._check(_lib.md_batch_set_state(self.handle, args[0][0], args[1][0], args[2][0], int(bool(dev))))
 
     def step(self, n_steps):
         self._check(_lib.md_batch_step(self.handle, int(n_steps)))
@@ -72,7 +74,7 @@ class Batch:
     def forces(self, out=None):
         if out is None:
             out = np.empty((self.ntot, 3))
-        fp, dev = _m._ptr(out)
+        fp, dev = _m._ptr(out, np.float64, 3 * self.ntot, "out")
         self._check(_lib.md_batch_forces(self.handle, fp, int(bool(dev))))
         return out
 

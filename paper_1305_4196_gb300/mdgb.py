@@ -106,19 +106,46 @@ def _load():
 _lib = _load()
 
 
-def _ptr(a):
-    """(pointer, is_device) of a numpy array or torch tensor (None -> NULL)."""
+def _ptr(a, dtype=None, count=None, name="array"):
+    """(pointer, is_device) of a numpy array or torch tensor (None -> NULL).
+
+    The C calls read or write a fixed number of elements of one type through the pointer,
+    so the array must be contiguous, of element type `dtype` (a numpy dtype, when given)
+    and hold at least `count` elements (when given); anything else raises before the call.
+    """
     if a is None:
         return None, None
     if isinstance(a, np.ndarray):
         if not a.flags["C_CONTIGUOUS"]:
-            raise ValueError("arrays must be C-contiguous")
-        return a.ctypes.data, False
-    if hasattr(a, "data_ptr"):
+            raise ValueError(f"{name} must be C-contiguous")
+        kind, size, dev = a.dtype.name, a.size, False
+        ptr = a.ctypes.data
+    elif hasattr(a, "data_ptr"):
         if not a.is_contiguous():
-            raise ValueError("tensors must be contiguous")
-        return a.data_ptr(), bool(a.is_cuda)
-    raise TypeError(f"unsupported array type {type(a)}")
+            raise ValueError(f"{name} must be contiguous")
+        kind, size, dev = str(a.dtype).replace("torch.", ""), a.numel(), bool(a.is_cuda)
+        ptr = a.data_ptr()
+    else:
+        raise TypeError(f"unsupported array type {type(a)}")
+    if dtype is not None and kind != np.dtype(dtype).name:
+        raise TypeError(f"{name} must be {np.dtype(dtype).name}, not {kind}")
+    if count is not None and size < count:
+        raise ValueError(f"{name} holds {size} elements, the call uses {count}")
+    return ptr, dev
+
+
+def _same_side(*ptrs):
+    """The one host/device flag of a call's arrays (None if all are NULL); a mix raises."""
+    devs = {d for _, d in ptrs if d is not None}
+    if len(devs) > 1:
+        raise ValueError("mix of host and device arrays")
+    return devs.pop() if devs else None
+
+
+def _n_atoms(handle) -> int:
+    info = md_info()
+    _check(handle, _lib.md_get_info(handle, C.byref(info)))
+    return int(info.n)
 
 
 def _check(handle, code):
@@ -140,6 +167,12 @@ def md_create(n, box, r_cut, skin, eps, sigma, mass, dt, precision=MD_MIXED, lis
     mass = np.ascontiguousarray(np.atleast_1d(mass), dtype=np.float64)
     rc = None if rcut is None else np.ascontiguousarray(np.atleast_2d(rcut), dtype=np.float64)
     box = np.ascontiguousarray(box, dtype=np.float64)
+    if box.shape != (3,):
+        raise ValueError("box must hold the 3 sides")
+    nsp = int(mass.shape[0])
+    for name, table in (("eps", eps), ("sigma", sigma), ("rcut", rc)):
+        if table is not None and table.size != nsp * nsp:
+            raise ValueError(f"{name} must be an n_species x n_species table ({nsp} species)")
     dp = C.POINTER(C.c_double)
     p = md_params(int(mass.shape[0]), eps.ctypes.data_as(dp), sigma.ctypes.data_as(dp),
                   rc.ctypes.data_as(dp) if rc is not None else None, mass.ctypes.data_as(dp), float(dt),
@@ -153,8 +186,11 @@ def md_create(n, box, r_cut, skin, eps, sigma, mass, dt, precision=MD_MIXED, lis
 
 
 def md_set_state(handle, pos, vel, species=None):
-    (pp, dev), (vp, _), (sp, _) = _ptr(pos), _ptr(vel), _ptr(species)
-    _check(handle, _lib.md_set_state(handle, pp, vp, sp, int(bool(dev))))
+    n = _n_atoms(handle)
+    args = (_ptr(pos, np.float64, 3 * n, "pos"), _ptr(vel, np.float64, 3 * n, "vel"),
+            _ptr(species, np.int32, n, "species"))
+    dev = _same_side(*args)
+    _check(handle, _lib.md_set_state(handle, args[0][0], args[1][0], args[2][0], int(bool(dev))))
 
 
 def md_bin_cells(handle):
@@ -166,7 +202,7 @@ def md_build_neighbors(handle):
 
 
 def md_forces(handle, f_out=None):
-    fp, dev = _ptr(f_out)
+    fp, dev = _ptr(f_out, np.float64, 3 * _n_atoms(handle) if f_out is not None else None, "f_out")
     _check(handle, _lib.md_forces(handle, fp, int(bool(dev))))
 
 
@@ -182,11 +218,11 @@ def md_energy_virial(handle):
 
 
 def md_get_state(handle, pos=None, vel=None, image=None):
-    (pp, d1), (vp, d2), (ip, d3) = _ptr(pos), _ptr(vel), _ptr(image)
-    devs = {d for d in (d1, d2, d3) if d is not None}
-    if len(devs) > 1:
-        raise ValueError("mix of host and device outputs")
-    _check(handle, _lib.md_get_state(handle, pp, vp, ip, int(devs == {True})))
+    n = _n_atoms(handle)
+    args = (_ptr(pos, np.float64, 3 * n, "pos"), _ptr(vel, np.float64, 3 * n, "vel"),
+            _ptr(image, np.int32, 3 * n, "image"))
+    dev = _same_side(*args)
+    _check(handle, _lib.md_get_state(handle, args[0][0], args[1][0], args[2][0], int(bool(dev))))
 
 
 def md_get_neighbors(handle):
@@ -222,17 +258,23 @@ def md_kinetic_energy_noalloc(n, vel, species, mass, ke_out, stream=None):
     """Kinetic energy of device velocities into the device scalar ke_out, with no device
     allocation (see include/mdgb.h); returns the C status code."""
     mass = np.ascontiguousarray(np.atleast_1d(mass), dtype=np.float64)
-    vp, _ = _ptr(vel)
-    sp, _ = _ptr(species)
-    op, _ = _ptr(ke_out)
+    n = int(n)
+    m = n if 0 < n <= 1 << 30 else None  # outside that range the call reads nothing
+    vp, _ = _ptr(vel, np.float64, 3 * m if m else None, "vel")
+    sp, _ = _ptr(species, np.int32, m, "species")
+    op, _ = _ptr(ke_out, np.float64, 1, "ke_out")
     return _lib.md_kinetic_energy_noalloc(int(n), vp, sp, mass.ctypes.data_as(C.POINTER(C.c_double)),
                                           int(mass.shape[0]), op, C.c_void_p(stream) if stream else None)
 
 
-def md_set_params(handle, eps, sigma, rcut=None):
+def md_set_params(handle, eps, sigma, rcut=None, nsp=None):
+    """New pair tables (n_species x n_species); nsp, when given, is checked against their size."""
     eps = np.ascontiguousarray(np.atleast_2d(eps), dtype=np.float64)
     sigma = np.ascontiguousarray(np.atleast_2d(sigma), dtype=np.float64)
     rc = None if rcut is None else np.ascontiguousarray(np.atleast_2d(rcut), dtype=np.float64)
+    for name, table in (("eps", eps), ("sigma", sigma), ("rcut", rc)):
+        if nsp is not None and table is not None and table.size != nsp * nsp:
+            raise ValueError(f"{name} must be an n_species x n_species table ({nsp} species)")
     _check(handle, _lib.md_set_params(handle, eps.ctypes.data, sigma.ctypes.data,
                                       rc.ctypes.data if rc is not None else None))
 
@@ -244,7 +286,8 @@ def md_set_tbsma(handle, A, xi, p, q, r0, r_cut):
 def md_forces_backward(handle, grad_f, grad_pos, nsp):
     """dL/dx into grad_pos (same kind of array as grad_f: numpy or CUDA tensor, N x 3) and
     (dL/deps, dL/dsigma) returned as nsp x nsp numpy tables."""
-    (gp, dev), (op, dev2) = _ptr(grad_f), _ptr(grad_pos)
+    n = _n_atoms(handle)
+    (gp, dev), (op, dev2) = _ptr(grad_f, np.float64, 3 * n, "grad_f"), _ptr(grad_pos, np.float64, 3 * n, "grad_pos")
     if grad_pos is not None and bool(dev) != bool(dev2):
         raise ValueError("grad_f and grad_pos must both be host or both be device arrays")
     ge = np.zeros((nsp, nsp))
@@ -323,7 +366,7 @@ class System:
         md_set_timing(self.handle, enable)
 
     def set_params(self, eps, sigma, rcut=None):
-        md_set_params(self.handle, eps, sigma, rcut)
+        md_set_params(self.handle, eps, sigma, rcut, self.nsp)
 
     def colour_conflicts(self, n_phases=8):
         """Atoms claimed by two blocks of one phase (md_colour_conflicts): 0 for the 8 colours."""

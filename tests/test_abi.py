@@ -244,3 +244,85 @@ def test_linear_block_numbering(lib, nc):
     odd = np.array([5, 6, 6], dtype=np.int32)
     out = np.zeros(1, dtype=np.int32)
     assert L.mdgb_num_blocks(odd.ctypes.data, out.ctypes.data) == lib.MD_ERR_ARG
+
+
+def test_binding_checks_arrays_before_the_call(lib):
+    """The C calls read a fixed number of elements of one type through each pointer, so the
+    binding refuses, before any call, arrays of another element type, too few elements,
+    non-contiguous arrays, a mix of host and device arrays in one call, and md_create
+    tables that do not match the species count."""
+    import torch
+    M = lib
+    pos = np.zeros((10, 3))
+    assert M._ptr(pos, np.float64, 30, "pos") == (pos.ctypes.data, False)
+    with pytest.raises(TypeError):
+        M._ptr(pos.astype(np.float32), np.float64, 30, "pos")
+    with pytest.raises(ValueError):
+        M._ptr(pos, np.float64, 33, "pos")
+    with pytest.raises(ValueError):
+        M._ptr(np.zeros((3, 10)).T, np.float64, 30, "pos")
+    t = torch.zeros(10, dtype=torch.int32)
+    assert M._ptr(t, np.int32, 10, "species") == (t.data_ptr(), False)
+    with pytest.raises(TypeError):
+        M._ptr(t.to(torch.int64), np.int32, 10, "species")
+    with pytest.raises(ValueError):
+        M._ptr(t, np.int32, 11, "species")
+    assert M._ptr(None, np.int32, 10, "species") == (None, None)
+    assert M._same_side((1, False), (None, None), (2, False)) is False
+    assert M._same_side((None, None)) is None
+    with pytest.raises(ValueError):
+        M._same_side((1, False), (2, True))
+    kw = dict(r_cut=2.5, skin=0.3, dt=0.005)
+    with pytest.raises(ValueError):
+        M.md_create(10, [40, 40], eps=1.0, sigma=1.0, mass=1.0, **kw)
+    with pytest.raises(ValueError):
+        M.md_create(10, [40, 40, 40], eps=1.0, sigma=np.ones((2, 2)), mass=[1.0, 1.0], **kw)
+
+
+def test_binding_marshals_valid_arrays(lib, monkeypatch):
+    """With valid arrays every marshalling function reaches its C call with the arrays'
+    pointers and one host/device flag (a recording stand-in for the library, no GPU)."""
+    import torch
+    M = lib
+    n = 7
+    calls = {}
+
+    class Fake:
+        def md_get_info(self, handle, info):
+            C.cast(info, C.POINTER(M.md_info)).contents.n = n
+            return M.MD_OK
+
+        def __getattr__(self, name):
+            def call(*args):
+                calls[name] = args
+                return M.MD_OK
+            return call
+
+    monkeypatch.setattr(M, "_lib", Fake())
+    pos, vel = np.zeros((n, 3)), np.zeros((n, 3))
+    sp, img = np.zeros(n, dtype=np.int32), np.zeros((n, 3), dtype=np.int32)
+    M.md_set_state("h", pos, vel, sp)
+    assert calls["md_set_state"] == ("h", pos.ctypes.data, vel.ctypes.data, sp.ctypes.data, 0)
+    M.md_set_state("h", pos, None)
+    assert calls["md_set_state"] == ("h", pos.ctypes.data, None, None, 0)
+    M.md_get_state("h", pos, vel, img)
+    assert calls["md_get_state"] == ("h", pos.ctypes.data, vel.ctypes.data, img.ctypes.data, 0)
+    M.md_forces("h", None)
+    assert calls["md_forces"] == ("h", None, 0)
+    M.md_forces("h", pos)
+    assert calls["md_forces"] == ("h", pos.ctypes.data, 0)
+    M.md_forces_backward("h", pos, vel, 1)
+    assert calls["md_forces_backward"][:4] == ("h", pos.ctypes.data, 0, vel.ctypes.data)
+    t = torch.zeros((n, 3), dtype=torch.float64)
+    M.md_set_state("h", t, t)
+    assert calls["md_set_state"] == ("h", t.data_ptr(), t.data_ptr(), None, 0)
+    with pytest.raises(ValueError):
+        M.md_set_state("h", np.zeros((n - 1, 3)), vel)
+    with pytest.raises(TypeError):
+        M.md_get_state("h", pos, vel, np.zeros((n, 3), dtype=np.int64))
+    with pytest.raises(TypeError):
+        M.md_set_state("h", pos, vel, np.zeros(n, dtype=np.int64))
+    with pytest.raises(ValueError):
+        M.md_set_params("h", np.ones((2, 2)), np.ones((2, 2)), None, nsp=1)
+    M.md_set_params("h", 1.0, 1.0, None, nsp=1)
+    assert "md_set_params" in calls

@@ -733,6 +733,49 @@ def test_inhomogeneous_system_takes_coarser_cells(monkeypatch):
     assert np.abs(pa + ia * sysm.box - (pb + ib * sysm.box)).max() < 2e-5
 
 
+def test_coarser_cells_per_side_in_a_non_cubic_mixture():
+    """Sec. II.A, cells at least r_list wide, on a non-cubic box: a binary mixture with
+    per-pair cutoffs (r_c = 2.5 sigma_ab) on 41 x 34 x 24 fcc cells at rho* = 0.8442
+    (133,824 atoms, box 68.9 x 57.1 x 40.3 sigma).  The r_list fit gives 24 x 20 x 12 cells;
+    the homogeneous rule's width (224 / (8 rho))^(1/3) = 3.213 sigma asks for 22 x 18 x 14,
+    capped at the fit: 22 x 18 x 12, two sides that are not multiples of 4 (linear block
+    numbering).  Pair set bit-exact, forces, energy and virial against the oracle, a
+    20-step trajectory against the oracle's velocity Verlet; a second md_set_state keeps
+    the grid and its forces match the oracle again."""
+    a = W.lattice_constant(0.8442)
+    lat, box = W.fcc_lattice(41, 34, 24, a)
+    sig = np.array([[1.0, 0.8], [0.8, 0.88]])
+    P = O.LJParams([[1.0, 1.5], [1.5, 0.5]], sig, 2.5 * sig, [1.0, 1.0])
+
+    def config(seed):
+        pos = W.gaussian_jitter(lat, box, 0.05, seed=seed)
+        sp = W.species_shuffle(len(pos), 0.2, seed=seed)
+        vel = W.thermal_velocities(np.ones(len(pos)), 0.72, seed)
+        return W.System(pos, vel, sp, box)
+
+    sysm = config(12)
+    s = make(sysm, params=P)
+    F = s.forces()
+    assert s.info()["ncell"] == [22, 18, 12]
+    assert np.array_equal(s.neighbors(), O.neighbor_pairs(sysm.pos, box, RC + SKIN))
+    Fref, pe_ref, vir_ref = O.lj_forces(sysm.pos, box, P, species=sysm.species)
+    assert force_error(F, Fref) <= TOL["mixed"]
+    pe, _, vir = s.energy_virial()
+    assert abs(pe - pe_ref) <= 1e-6 * abs(pe_ref)
+    assert np.abs(vir - vir_ref).max() <= 1e-6 * np.abs(vir_ref[:3]).max()
+    s.step(20)
+    pos, _, img = s.get_state()
+    ref = O.run_nve(sysm.pos, sysm.vel, box, P, DT, SKIN, 20, species=sysm.species)
+    # forces within ~1e-6 of F per step, carried by 20 steps of the jittered lattice to a
+    # few 1e-6 sigma over 133,824 atoms
+    assert np.abs(pos + img * box - (ref["pos"] + ref["image"] * box)).max() < 2e-5
+    other = config(13)
+    s.set_state(other.pos, other.vel, other.species)
+    F = s.forces()
+    assert s.info()["ncell"] == [22, 18, 12]
+    assert force_error(F, O.lj_forces(other.pos, box, P, species=other.species)[0]) <= TOL["mixed"]
+
+
 def test_timing_brackets_one_force_launch_per_step_graph():
     """md_set_timing on the fused path: in the 8-step graphs only the first step's force
     kernel is bracketed by events, every singly launched step is too, and
