@@ -766,9 +766,18 @@ def test_coarser_cells_per_side_in_a_non_cubic_mixture():
     s.step(20)
     pos, _, img = s.get_state()
     ref = O.run_nve(sysm.pos, sysm.vel, box, P, DT, SKIN, 20, species=sysm.species)
-    # forces within ~1e-6 of F per step, carried by 20 steps of the jittered lattice to a
-    # few 1e-6 sigma over 133,824 atoms
-    assert np.abs(pos + img * box - (ref["pos"] + ref["image"] * box)).max() < 2e-5
+    d = np.abs(pos + img * box - (ref["pos"] + ref["image"] * box)).max(axis=1)
+    # FP32 pair forces keep nearly every atom within 1e-6 sigma of the FP64 run.  The
+    # potential is cut unshifted at r_c (Sec. I: no interaction beyond r_c), so its force
+    # steps there, by up to 24 * 1.5 / 2.0 * |2 * 0.4^12 - 0.4^6| = 0.073 eps/sigma (the AB
+    # pair).  A pair within the runs' ~1e-8 sigma difference of r_c (about two such
+    # crossings in 20 steps of 133,824 atoms) is cut in one run a step before the other:
+    # its atoms' velocities then differ by 0.073 dt and their positions by at most
+    # 0.073 dt * 20 dt = 3.7e-5 sigma at the end, and their neighbours by less.  Two runs of
+    # the oracle itself from positions 1e-9 sigma apart show the same: 2.7e-5 sigma at two
+    # atoms, 3.7e-9 sigma at the 99.9th percentile.
+    assert np.quantile(d, 0.999) < 1e-6
+    assert d.max() < 2 * 0.0732 * DT * 20 * DT
     other = config(13)
     s.set_state(other.pos, other.vel, other.species)
     F = s.forces()
