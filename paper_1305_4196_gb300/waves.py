@@ -24,6 +24,14 @@ def _check(v):
     return v
 
 
+def _cells3(n):
+    """The cell counts as 3 int32 values (the C calls read exactly three)."""
+    n = np.ascontiguousarray(n, dtype=np.int32)
+    if n.shape != (3,):
+        raise ValueError("n must hold the cell counts of the 3 dimensions")
+    return n
+
+
 def sets_1d(D, periodic, spacing=3, start=0):
     """Set number of every cell of one dimension (0-based cells); returns (set_of_cell, n_sets)."""
     out = np.empty(int(D), dtype=np.int32)
@@ -33,7 +41,7 @@ def sets_1d(D, periodic, spacing=3, start=0):
 
 def waves(n, periodic, overlap=27):
     """Wave of every cell (x fastest), shape n[2] x n[1] x n[0] flattened; returns (wave_of_cell, n_waves)."""
-    n = np.ascontiguousarray(n, dtype=np.int32)
+    n = _cells3(n)
     p = np.ascontiguousarray(np.broadcast_to(np.asarray(periodic, dtype=np.int32), (3,)))
     out = np.empty(int(np.prod(n)), dtype=np.int32)
     k = _check(_lib.md_waves(n.ctypes.data, p.ctypes.data, int(overlap), out.ctypes.data))
@@ -42,7 +50,7 @@ def waves(n, periodic, overlap=27):
 
 def schedule(n, periodic, overlap=27, backward=False):
     """(task_cell, n_pred, succ_start, succ) of the forward or backward wave method."""
-    n = np.ascontiguousarray(n, dtype=np.int32)
+    n = _cells3(n)
     p = np.ascontiguousarray(np.broadcast_to(np.asarray(periodic, dtype=np.int32), (3,)))
     T = int(np.prod(n))
     tc = np.empty(T, dtype=np.int32)

@@ -120,3 +120,10 @@ def test_critical_path_is_at_most_the_wave_count():
     _, k = WV.waves(n, periodic)
     tc, npred, start, succ = WV.schedule(n, periodic)
     assert WV.critical_path(npred, start, succ) <= k
+
+
+def test_cell_counts_must_have_three_entries():
+    with pytest.raises(ValueError):
+        WV.waves([4, 4], True)
+    with pytest.raises(ValueError):
+        WV.schedule([4, 4, 4, 4], True)
