@@ -46,6 +46,21 @@ def test_every_declared_symbol_is_exported(lib):
         assert n in names
 
 
+@pytest.mark.parametrize("compiler", [["gcc", "-std=c99"], ["g++", "-std=c++17", "-x", "c++"]])
+def test_headers_compile_as_strict_c_and_cxx(compiler):
+    """Every public header, alone and all together, is valid pedantic C99 and C++17 with no
+    warning: a C caller needs no CUDA or C++ header to use the library."""
+    import tempfile
+    headers = sorted(h for h in os.listdir(INCLUDE) if h.endswith(".h"))
+    with tempfile.TemporaryDirectory() as d:
+        for name, body in [(h, f'#include "{h}"\n') for h in headers] + \
+                [("all", "".join(f'#include "{h}"\n' for h in headers))]:
+            src = os.path.join(d, name.replace(".h", "") + ".c")
+            open(src, "w").write(body)
+            subprocess.run(compiler + ["-Wall", "-Wextra", "-Werror", "-pedantic", "-fsyntax-only", "-I", INCLUDE,
+                                       src], check=True)
+
+
 def test_struct_layout_matches_binding(lib):
     src = r'''
 #include <stdio.h>
