@@ -61,6 +61,40 @@ def test_headers_compile_as_strict_c_and_cxx(compiler):
                                        src], check=True)
 
 
+def test_plain_c_caller(lib):
+    """A C program links libmdgb.so with no Python in between: it gets an argument error from
+    md_create (before any CUDA call, so no GPU is needed) and computes the wave count of an
+    8 x 8 x 8 periodic grid with the host tool md_waves, which must equal the binding's."""
+    import tempfile
+    from paper_1305_4196_gb300 import waves as WV
+    src = r'''
+#include <stdio.h>
+#include <stdlib.h>
+#include "mdgb.h"
+#include "mdgb_waves.h"
+int main(void) {
+  double box[3] = {40.0, 40.0, 40.0}, eps = 1.0, sig = 1.0, mass = 1.0;
+  md_params p = {1, &eps, &sig, NULL, &mass, 0.005, MD_MIXED, MD_LIST_FULL, MD_REBUILD_SKIN_HALF, 10, NULL};
+  md_system *s = (md_system *)&p;
+  int code = md_create(-1, box, 2.5, 0.3, &p, &s);
+  int32_t n[3] = {8, 8, 8}, per[3] = {1, 1, 1};
+  int32_t *w = malloc(sizeof(int32_t) * 512);
+  int waves = md_waves(n, per, 27, w);
+  printf("%d %d %d\n", code, s == NULL, waves);
+  free(w);
+  return 0;
+}'''
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "caller.c")
+        open(c, "w").write(src)
+        exe = os.path.join(d, "caller")
+        libdir = os.path.dirname(B.LIB)
+        subprocess.run(["gcc", "-std=c99", "-Wall", "-Werror", "-I", INCLUDE, c, "-o", exe, "-L", libdir, "-lmdgb",
+                        "-Wl,-rpath," + libdir], check=True)
+        got = [int(v) for v in subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()]
+    assert got == [lib.MD_ERR_ARG, 1, WV.waves([8, 8, 8], True)[1]]
+
+
 def test_struct_layout_matches_binding(lib):
     src = r'''
 #include <stdio.h>
